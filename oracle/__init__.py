@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for space-variant elliptical box-spline filtering.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never calls it and shares no code with it.
+
+Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
+"Fast space-variant elliptical filtering using box splines":
+
+* ``beta4`` / ``beta4_lines``: the four-directional radially-uniform box spline
+  of Eq. (const) (Sec. 2.2.1), evaluated exactly in two independent ways.
+* ``direct4``: the plain definition fbar[n] = sum_k f[k] beta_{a(n)}(n-k)
+  (Eq. SVF_2D with the Dirac-comb image used to derive Eq. keyeqn).
+* ``preint4_i64`` / ``preint4_f64``: Algorithm 1 step 2 (Sec. 3.1, RS1-RS4).
+* ``stencil4``: Algorithm 1 step 3 (Table 1, Eq. final_eqn, App. F).
+* ``map4``: the optimal scale vector of Sec. 3.2.2, steps (i)-(iii).
+* ``U_bound``: the elongation bound of Prop. 3.1.
+
+The C source is ``bsf_oracle.c``; it is compiled with gcc on first use (or by
+``__graft_entry__.build()``) into ``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bsf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libbsf_oracle.so")
+
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle C source into a shared library (gcc, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.bo_beta4.restype = ctypes.c_double
+        lib.bo_beta4.argtypes = [_dp, ctypes.c_double, ctypes.c_double]
+        lib.bo_beta4_lines.restype = ctypes.c_double
+        lib.bo_beta4_lines.argtypes = [_dp, ctypes.c_double, ctypes.c_double]
+        lib.bo_direct4.restype = None
+        lib.bo_direct4.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i64p, ctypes.c_int64, _dp]
+        lib.bo_preint4_i64.restype = None
+        lib.bo_preint4_i64.argtypes = [_i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p]
+        lib.bo_preint4_f64.restype = None
+        lib.bo_preint4_f64.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        lib.bo_stencil4.restype = ctypes.c_int64
+        lib.bo_stencil4.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _i64p,
+                                    ctypes.c_int64, _dp]
+        lib.bo_map4.restype = ctypes.c_int
+        lib.bo_map4.argtypes = [_dp, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                _dp, _u8p]
+        lib.bo_U_bound.restype = ctypes.c_double
+        lib.bo_U_bound.argtypes = [ctypes.c_double]
+        _lib = lib
+    return _lib
+
+
+def _d(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _ptr(x, t):
+    return x.ctypes.data_as(t)
+
+
+SQRT2 = np.sqrt(2.0)
+ZP_SCALES = np.array([1.0, SQRT2, 1.0, SQRT2])  # b of Sec. 3.1 (Zwart-Powell element)
+
+KIND_SCALES, KIND_COV, KIND_SRT = 0, 1, 2
+FLAG_CLAMPED, FLAG_INFEASIBLE, FLAG_INVALID = 1, 2, 4
+
+
+def beta4(a, x1, x2) -> float:
+    """beta^4_a(x1, x2), area form (exact up to rounding)."""
+    a = _d(a)
+    return _load().bo_beta4(_ptr(a, _dp), float(x1), float(x2))
+
+
+def beta4_lines(a, x1, x2) -> float:
+    """beta^4_a(x1, x2), line-integral recursion form (independent evaluation)."""
+    a = _d(a)
+    return _load().bo_beta4_lines(_ptr(a, _dp), float(x1), float(x2))
+
+
+def beta4_grid(a, X1, X2) -> np.ndarray:
+    """beta4 at every point of broadcastable arrays X1, X2."""
+    X1, X2 = np.broadcast_arrays(np.asarray(X1, float), np.asarray(X2, float))
+    lib = _load()
+    a = _d(a)
+    pa = _ptr(a, _dp)
+    out = np.empty(X1.shape)
+    for i, (u, v) in enumerate(zip(X1.ravel(), X2.ravel())):
+        out.flat[i] = lib.bo_beta4(pa, float(u), float(v))
+    return out
+
+
+def _idx(idx, HW):
+    if idx is None:
+        return None, -1
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    if idx.size and (idx.min() < 0 or idx.max() >= HW):
+        raise ValueError("pixel index out of range")
+    return idx, idx.size
+
+
+def direct4(f, a, idx=None) -> np.ndarray:
+    """O-direct: fbar[n] = sum_k f[k] beta_{a(n)}(n - k), zero outside the image.
+
+    f: (H, W) array; a: (4, H, W) scale planes; idx: optional flat pixel indices.
+    Returns (H, W) (idx None) or the values at idx.
+    """
+    f = _d(f)
+    H, W = f.shape
+    a = _d(a)
+    assert a.shape == (4, H, W)
+    ii, n = _idx(idx, H * W)
+    out = np.empty(H * W if n < 0 else n)
+    _load().bo_direct4(_ptr(f, _dp), H, W, _ptr(a, _dp),
+                       _ptr(ii, _i64p) if ii is not None else None, n, _ptr(out, _dp))
+    return out.reshape(H, W) if n < 0 else out
+
+
+def preint4_i64(f_int, P: int) -> np.ndarray:
+    """Algorithm 1 step 2 in integers (sqrt2 factors taken out, g_b = 2 G), mod 2^64.
+
+    f_int: (H, W) integer image.  Returns G of shape (H+2P, W+2P), int64.
+    """
+    f = np.ascontiguousarray(f_int, dtype=np.int64)
+    H, W = f.shape
+    G = np.empty((H + 2 * P, W + 2 * P), dtype=np.int64)
+    _load().bo_preint4_i64(_ptr(f, _i64p), H, W, int(P), _ptr(G, _i64p))
+    return G
+
+
+def preint4_f64(f, P: int) -> np.ndarray:
+    """Algorithm 1 step 2 in FP64, literally (with the sqrt2 factors): returns g_b."""
+    f = _d(f)
+    H, W = f.shape
+    gb = np.empty((H + 2 * P, W + 2 * P))
+    _load().bo_preint4_f64(_ptr(f, _dp), H, W, int(P), _ptr(gb, _dp))
+    return gb
+
+
+def stencil4(gb, H: int, W: int, P: int, a, idx=None):
+    """Algorithm 1 step 3: 16-tap FD mesh of Table 1 on the ZP-interpolated g_b.
+
+    Returns (out, n_outside); pixels whose taps leave the buffer get NaN.
+    """
+    gb = _d(gb)
+    assert gb.shape == (H + 2 * P, W + 2 * P)
+    a = _d(a)
+    assert a.shape == (4, H, W)
+    ii, n = _idx(idx, H * W)
+    out = np.empty(H * W if n < 0 else n)
+    bad = _load().bo_stencil4(_ptr(gb, _dp), H, W, int(P), _ptr(a, _dp),
+                              _ptr(ii, _i64p) if ii is not None else None, n, _ptr(out, _dp))
+    return (out.reshape(H, W) if n < 0 else out), int(bad)
+
+
+def alg1_filter4(f, a, P: int, integer: bool, idx=None):
+    """Algorithm 1 end to end (O-alg): pre-integration then the local FD step."""
+    f = np.asarray(f)
+    H, W = f.shape
+    if integer:
+        G = preint4_i64(f, P)
+        gb = 2.0 * G.astype(np.float64)
+    else:
+        gb = preint4_f64(f, P)
+    return stencil4(gb, H, W, P, a, idx)
+
+
+def map4(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
+    """O-map: covariance (kind 1) or (sigma, rho, theta) (kind 2) -> scales.
+
+    params: (3, ...) planes.  Returns (a of shape (4, ...), flags uint8 of shape (...)).
+    """
+    params = _d(params)
+    shp = params.shape[1:]
+    npix = int(np.prod(shp)) if shp else 1
+    a = np.empty((4,) + shp)
+    flags = np.empty(shp, dtype=np.uint8)
+    _load().bo_map4(_ptr(params, _dp), int(kind), npix, float(eps), float(eta), _ptr(a, _dp),
+                    _ptr(flags, _u8p))
+    return a, flags
+
+
+def U_bound(phi: float) -> float:
+    """Prop. 3.1: supremum of the elongation at orientation phi in [0, pi)."""
+    return _load().bo_U_bound(float(phi))
+
+
+def covariance4(a) -> np.ndarray:
+    """Eq. covariance_ZP: C_a = (1/24) [[2a1^2+a2^2+a4^2, a2^2-a4^2], [., 2a3^2+a2^2+a4^2]]."""
+    a = np.asarray(a, float)
+    p = a * a
+    return np.array([[2 * p[0] + p[1] + p[3], p[1] - p[3]],
+                     [p[1] - p[3], 2 * p[2] + p[1] + p[3]]]) / 24.0
+
+
+def kurtosis4_norm2(p) -> float:
+    """||K||^2 up to the factor (mu4 - 3 mu2^2)^2 (App. E): sum p^4 + (p1^2+p3^2)(p2^2+p4^2), p = a^2."""
+    p = np.asarray(p, float)
+    return float(np.sum(p ** 4) + (p[0] ** 2 + p[2] ** 2) * (p[1] ** 2 + p[3] ** 2))

@@ -1,0 +1,135 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds only random-number generation and reshaping: none of the
+filter's arithmetic.  Both the CUDA path (bench, tests) and the oracle side of
+the tests draw their inputs from here, so both see identical bytes.
+
+Recipe (numpy PCG64, one sub-seed per field):
+  * images: uniform f32 in [0, 1), or uniform u8 in {0..255}; the batched N=6
+    workload adds three seeded sinusoidal gratings of amplitude 0.25 and
+    spatial frequency |k| in [1/64, 1/8] cycles/px;
+  * smooth fields: white noise on a grid 16x coarser than the image, blurred
+    (std 1 coarse px), upsampled with a cubic spline to full size, then
+    rank-normalised to U[0, 1] and mapped affinely to the requested range;
+  * orientation from a vector field: theta = atan2(v, u) mod pi of two
+    independent smooth fields centred at zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+try:  # scipy is on both machines; keep the import local to the generators
+    from scipy import ndimage as _ndi
+except Exception:  # pragma: no cover
+    _ndi = None
+
+
+def _rng(seed: int, sub: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([int(seed), int(sub)]))
+
+
+def image(H: int, W: int, seed: int, dtype: str = "f32", sub: int = 0) -> np.ndarray:
+    """Uniform image: 'f32' in [0,1) or 'u8' in {0..255}."""
+    g = _rng(seed, 100 + sub)
+    if dtype == "u8":
+        return g.integers(0, 256, size=(H, W), dtype=np.uint8)
+    return g.random((H, W), dtype=np.float32)
+
+
+def gratings_image(H: int, W: int, seed: int, sub: int = 0) -> np.ndarray:
+    """U[0,1) plus three sinusoidal gratings (amplitude 0.25 each), f32."""
+    g = _rng(seed, 200 + sub)
+    f = g.random((H, W)).astype(np.float64)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    for _ in range(3):
+        fr = g.uniform(1 / 64, 1 / 8)
+        ang = g.uniform(0, np.pi)
+        ph = g.uniform(0, 2 * np.pi)
+        f += 0.25 * np.sin(2 * np.pi * fr * (np.cos(ang) * x + np.sin(ang) * y) + ph)
+    return f.astype(np.float32)
+
+
+def _smooth_noise(H: int, W: int, g: np.random.Generator) -> np.ndarray:
+    cs = 16
+    hc, wc = H // cs + 6, W // cs + 6
+    z = g.standard_normal((hc, wc))
+    if _ndi is not None:
+        z = _ndi.gaussian_filter(z, 1.0, mode="wrap")
+        up = _ndi.zoom(z, cs, order=3)
+    else:  # plain nearest fallback (never used where scipy exists)
+        up = np.kron(z, np.ones((cs, cs)))
+    return up[3 * cs // 2:3 * cs // 2 + H, 3 * cs // 2:3 * cs // 2 + W]
+
+
+def smooth_field(H: int, W: int, seed: int, sub: int, lo: float, hi: float) -> np.ndarray:
+    """Smooth random field, rank-normalised to U[0,1], mapped to [lo, hi] (f64)."""
+    z = _smooth_noise(H, W, _rng(seed, sub))
+    r = np.empty(z.size)
+    r[np.argsort(z, axis=None, kind="stable")] = (np.arange(z.size) + 0.5) / z.size
+    return lo + (hi - lo) * r.reshape(H, W)
+
+
+def orientation_field(H: int, W: int, seed: int, sub: int) -> np.ndarray:
+    """theta = atan2(v, u) mod pi of a smooth zero-mean vector field."""
+    g = _rng(seed, sub)
+    u = _smooth_noise(H, W, g)
+    v = _smooth_noise(H, W, g)
+    return np.mod(np.arctan2(v, u), np.pi)
+
+
+def srt_field(H: int, W: int, seed: int, sigma=(2.0, 8.0), rho=(1.0, 4.0), theta: str = "uniform",
+              sigma_log: bool = False) -> np.ndarray:
+    """(sigma, rho, theta) planes, shape (3, H, W), float32.
+
+    sigma: major-axis std in px; rho: elongation lambda_max / lambda_min;
+    theta: 'uniform' (smooth field mapped to [0, pi)) or 'vector' (from a
+    smooth vector field).
+    """
+    if sigma_log:
+        s = np.exp(smooth_field(H, W, seed, 1, np.log(sigma[0]), np.log(sigma[1])))
+    else:
+        s = smooth_field(H, W, seed, 1, sigma[0], sigma[1])
+    r = smooth_field(H, W, seed, 2, rho[0], rho[1])
+    if theta == "vector":
+        t = orientation_field(H, W, seed, 3)
+    else:
+        t = smooth_field(H, W, seed, 3, 0.0, np.pi)
+    t = np.minimum(t, np.nextafter(np.pi, 0))
+    return np.stack([s, r, t]).astype(np.float32)
+
+
+def constant_srt(H: int, W: int, sigma: float, rho: float, theta: float) -> np.ndarray:
+    """A constant (sigma, rho, theta) field, shape (3, H, W), float32."""
+    out = np.empty((3, H, W), dtype=np.float32)
+    out[0], out[1], out[2] = sigma, rho, theta
+    return out
+
+
+# Workloads: shapes and parameter ranges of the paper-shaped configurations.
+WORKLOADS = {
+    # 256x256 f32 U[0,1), N=4, smooth (sigma 2-8, rho 1-4, theta uniform)
+    "u256_f32_n4": dict(B=1, C=1, H=256, W=256, dtype="f32", N=4, sigma=(2.0, 8.0), rho=(1.0, 4.0),
+                        theta="uniform"),
+    # 2048x2048 u8 U{0..255}, N=4, sigma 1-32, rho 1-8, theta from a smooth vector field
+    "u2048_u8_n4": dict(B=1, C=1, H=2048, W=2048, dtype="u8", N=4, sigma=(1.0, 32.0), rho=(1.0, 8.0),
+                        theta="vector"),
+    # same image as f32
+    "u2048_f32_n4": dict(B=1, C=1, H=2048, W=2048, dtype="f32", N=4, sigma=(1.0, 32.0), rho=(1.0, 8.0),
+                         theta="vector"),
+}
+
+
+def workload_inputs(name: str, seed: int = 0, H: int | None = None, W: int | None = None):
+    """Image (H, W) and (sigma, rho, theta) planes (3, H, W) for a named workload.
+
+    H, W override the size (same distributions) for reduced parity cases.
+    """
+    cfg = WORKLOADS[name]
+    H = H or cfg["H"]
+    W = W or cfg["W"]
+    if cfg["dtype"] == "u8":
+        f = image(H, W, seed, "u8")
+    else:
+        f = image(H, W, seed, "f32")
+    p = srt_field(H, W, seed, cfg["sigma"], cfg["rho"], cfg["theta"])
+    return f, p
