@@ -1,0 +1,167 @@
+/*
+ * bsf.h -- C ABI of the GB300 space-variant elliptical box-spline filter.
+ *
+ * The library computes, for an image f[n] and a per-pixel scale vector a(n),
+ *
+ *     fbar[n] = sum_k f[k] beta^N_{a(n)}(n - k)                      (1)
+ *
+ * where beta^N_a is the radially-uniform box spline of Chaudhury,
+ * Munoz-Barrutia and Unser, "Fast space-variant elliptical filtering using
+ * box splines", Sec. 2.2.1, Eq. (const): the convolution of N box
+ * distributions of widths a_k along theta_k = (k-1) pi / N.  (1) is
+ * Eq. (SVF_2D) with the Dirac-comb image used to derive Eq. (keyeqn).  The
+ * path is Algorithm 1 of Sec. 3.1: pre-integration by four running sums
+ * (RS1-RS4), then a 16-tap finite difference (Table 1, Eq. final_eqn) of the
+ * Zwart-Powell interpolant of the pre-integrated image (App. F).  Scale
+ * vectors may be given directly, or derived per pixel from a covariance by
+ * the optimal-scale algorithm of Sec. 3.2.2.
+ *
+ * Conventions shared by every entry point:
+ *   - Points n = (n1, n2): n1 is the column, n2 the row (rows grow downward in
+ *     memory).  theta is measured from +n1 towards +n2, so the four
+ *     directions are (1,0), (1,1)/sqrt2, (0,1), (-1,1)/sqrt2.
+ *   - Images are dense row-major arrays of B*C*H*W elements (batch, channel,
+ *     row, column), dtype BSF_U8 (uint8) or BSF_F32 (float32).  f is zero
+ *     outside the image (reading 1 of the paper's unspecified boundary).
+ *   - Parameter fields are dense float32 planes, one set per image of the
+ *     batch and shared by its C channels: B*K*H*W floats, plane k of image b
+ *     at params + (b*K + k)*H*W.  K = N for BSF_PARAM_SCALES (a_1..a_N in px,
+ *     the widths of Eq. const), K = 3 for BSF_PARAM_COV (C11, C12, C22 in
+ *     px^2, descriptor D3 of Sec. 3.2.1) and for BSF_PARAM_SRT (sigma, rho,
+ *     theta: sigma = sqrt(lambda_max) in px, rho = lambda_max/lambda_min,
+ *     theta in radians, the major-axis orientation).
+ *   - All data pointers are DEVICE pointers owned by the caller; the library
+ *     never frees them.  Scratch memory (pre-integrated buffers, scan
+ *     carries) is owned by the context and reused across calls.
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream) unless stated otherwise.
+ *   - Argument errors return synchronously.  Errors detected on the device
+ *     (a tap outside the pre-integrated buffer, an invalid scale) are OR-ed
+ *     into a device status word read by bsf_get_device_status; the affected
+ *     output pixels are NaN.
+ *   - Only N = 4 is implemented; other N return BSF_EUNSUPPORTED.
+ */
+#ifndef BSF_H
+#define BSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int bsf_status;
+#define BSF_OK 0
+#define BSF_EINVAL 1          /* bad argument (null pointer, size, kind, dtype) */
+#define BSF_EUNSUPPORTED 2    /* N other than 4 */
+#define BSF_ENOMEM 3          /* device allocation of scratch failed */
+#define BSF_ECUDA 4           /* a CUDA runtime call failed */
+#define BSF_EHALO 5           /* device: a tap fell outside the pre-integrated buffer */
+#define BSF_EINFEASIBLE 6     /* strict mode: a covariance needed the elongation clamp */
+#define BSF_EBADSCALE 7       /* device: a scale or covariance was not finite/positive */
+#define BSF_ERANGE 8          /* device: a kernel too large for the exact integer form */
+
+/* image element types */
+#define BSF_U8 0
+#define BSF_F32 1
+
+/* parameter kinds */
+#define BSF_PARAM_SCALES 0
+#define BSF_PARAM_COV 1
+#define BSF_PARAM_SRT 2
+
+/* arithmetic forms of the path */
+#define BSF_PREC_EXACT 0  /* integer pre-integration (int64 for u8; 128-bit fixed point with 32
+                             fractional bits for f32) and an exact integer finite difference at
+                             scales rounded to a per-pixel dyadic grid; one final FP32 rounding */
+#define BSF_PREC_FP64 1   /* all-FP64: Algorithm 1 computed literally in double precision */
+
+typedef struct bsf_ctx bsf_ctx;
+
+typedef struct {
+    int precision;    /* BSF_PREC_EXACT (default) or BSF_PREC_FP64 */
+    float eps;        /* lower bound on a_k^2, px^2 (Sec. 3.2.2 constraint p >= eps); default 1e-3 */
+    float eta;        /* covariances with rho > (1-eta) U(theta) (Prop. 3.1) are lowered to that
+                         elongation, keeping size s and orientation theta; default 1e-3 */
+    int strict;       /* 0 (default): clamp and continue; 1: bsf_filter returns BSF_EINFEASIBLE
+                         (after a stream synchronisation) when any pixel needed the clamp */
+    int halo;         /* padding P of the pre-integrated buffer in px; 0 = derive it:
+                         from max_scale if > 0, else from a device reduction over the field
+                         (one stream synchronisation) */
+    float max_scale;  /* optional bound on the largest footprint: for SCALES the largest a_k,
+                         for COV/SRT the largest sqrt(lambda_max) (px); 0 = unknown */
+} bsf_opts;
+
+/* Fill *opts with the defaults listed above. */
+void bsf_default_opts(bsf_opts* opts);
+
+/* Create a context bound to CUDA device `device` (the device is made current
+ * on the calling thread).  *ctx receives the handle. */
+bsf_status bsf_create(bsf_ctx** ctx, int device);
+
+/* Release a context and all scratch memory it owns (synchronises the device). */
+bsf_status bsf_destroy(bsf_ctx* ctx);
+
+/* Whole path: fbar of (1) for every pixel of every channel of every image.
+ * image: B*C*H*W elements of `dtype`; params: B*K*H*W floats of `kind`;
+ * out: B*C*H*W floats.  Runs the scale map (Sec. 3.2.2, for COV/SRT), the
+ * pre-integration (Algorithm 1 step 2) and the finite difference with ZP
+ * interpolation (Algorithm 1 step 3).  opts may be NULL (defaults). */
+bsf_status bsf_filter(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
+                      int64_t W, int N, const float* params, int kind, const bsf_opts* opts,
+                      float* out, void* stream);
+
+/* Step (b), Sec. 3.2.2: covariance (COV) or (sigma, rho, theta) (SRT) planes
+ * (3*npix floats) -> scale planes a_1..a_4 (4*npix floats, Eq. const widths).
+ * flags (nullable, npix bytes): bit0 elongation clamped (Prop. 3.1), bit1
+ * p >= eps infeasible (p raised to eps), bit2 invalid input (scales NaN). */
+bsf_status bsf_scales_from_cov(bsf_ctx* ctx, const float* params, int kind, int64_t npix, int N,
+                               const bsf_opts* opts, float* scales, uint8_t* flags, void* stream);
+
+/* Bytes of the caller-owned pre-integrated buffer for one H x W image with
+ * halo P in the given precision form (the buffer holds (H+2P)*(W+2P)
+ * elements: int64 for u8/EXACT, 16-byte fixed point for f32/EXACT, double
+ * for FP64). */
+bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, int precision,
+                            size_t* bytes);
+
+/* Step (a), Algorithm 1 step 2 (RS1-RS4 of Sec. 3.1) for ONE H x W image:
+ * writes the pre-integrated buffer (zero padding P on every side, every
+ * running sum started from zero at the buffer edge; the two sqrt2 factors
+ * are taken out, so g_b = 2 * buffer).  Integer forms wrap modulo 2^64
+ * (u8) or 2^128 (f32 fixed point), which the exact finite difference
+ * tolerates.  buffer: caller-owned device memory of bsf_buffer_bytes. */
+bsf_status bsf_preintegrate(bsf_ctx* ctx, const void* image, int dtype, int64_t H, int64_t W, int N,
+                            int halo, int precision, void* buffer, void* stream);
+
+/* Step (c), Algorithm 1 step 3 for ONE image: reads a buffer written by
+ * bsf_preintegrate with the same dtype/H/W/halo/precision, and the K*H*W
+ * params of `kind` (COV/SRT are mapped per pixel on the fly); writes H*W
+ * floats to out. */
+bsf_status bsf_apply(bsf_ctx* ctx, const void* buffer, int dtype, int64_t H, int64_t W, int N,
+                     int halo, const float* params, int kind, const bsf_opts* opts, float* out,
+                     void* stream);
+
+/* Synchronise `stream`, then return (and clear) the device status word in
+ * *status: 0 or the OR of (1 << BSF_EHALO), (1 << BSF_EBADSCALE),
+ * (1 << BSF_ERANGE), (1 << BSF_EINFEASIBLE) raised since the last call. */
+bsf_status bsf_get_device_status(bsf_ctx* ctx, void* stream, int* status);
+
+/* Measurement hook.  Between bsf_profile_begin and bsf_profile_end every
+ * bsf_filter call records CUDA events on its own stream before the
+ * pre-integration, between it and the finite difference, and after the
+ * finite difference.  bsf_profile_end synchronises on those events and
+ * returns the summed milliseconds of the two steps and the number of
+ * launches of each (any pointer may be NULL). */
+bsf_status bsf_profile_begin(bsf_ctx* ctx);
+bsf_status bsf_profile_end(bsf_ctx* ctx, double* ms_preintegrate, double* ms_stencil, int* nlaunch);
+
+/* Static description of a status code. */
+const char* bsf_status_string(bsf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSF_H */

@@ -1,0 +1,156 @@
+"""Torch-facing calls of the filter: device memory and streams come from
+PyTorch, every step runs in libbsf (CUDA).
+
+    out = filter(image, params, kind="srt")          # (B,C,H,W) -> (B,C,H,W) float32
+
+image: uint8 or float32 CUDA tensor of shape (H,W), (C,H,W) with B=1, or
+(B,C,H,W).  params: float32 CUDA tensor of the parameter planes of each
+batch entry, shape (K,H,W) or (B,K,H,W): K=4 scale vectors a (kind
+"scales"), or K=3 covariances (C11,C12,C22) (kind "cov"), or (sigma, rho,
+theta) (kind "srt").
+"""
+from __future__ import annotations
+
+import threading
+
+import torch
+
+from . import _lib as L
+
+_KINDS = {"scales": L.BSF_PARAM_SCALES, "cov": L.BSF_PARAM_COV, "srt": L.BSF_PARAM_SRT}
+_PREC = {"exact": L.BSF_PREC_EXACT, "fp64": L.BSF_PREC_FP64}
+_ctx: dict[int, int] = {}
+_ctx_lock = threading.Lock()
+
+
+def context(device: int | torch.device | None = None) -> int:
+    """The library context bound to a CUDA device (created on first use)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    idx = device.index if isinstance(device, torch.device) else int(device)
+    with _ctx_lock:
+        if idx not in _ctx:
+            with torch.cuda.device(idx):
+                _ctx[idx] = L.bsf_create(idx)
+        return _ctx[idx]
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False) -> L.bsf_opts:
+    o = L.default_opts()
+    o.precision = _PREC[precision]
+    o.halo = int(halo)
+    o.max_scale = float(max_scale)
+    o.eps = float(eps)
+    o.eta = float(eta)
+    o.strict = 1 if strict else 0
+    return o
+
+
+def _as4d(image: torch.Tensor) -> torch.Tensor:
+    if image.dim() == 2:
+        return image[None, None]
+    if image.dim() == 3:
+        return image[None]
+    if image.dim() == 4:
+        return image
+    raise ValueError("image must be (H,W), (C,H,W) or (B,C,H,W)")
+
+
+def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int = 4, precision: str = "exact",
+           halo: int = 0, max_scale: float = 0.0, eps: float = 1e-3, eta: float = 1e-3, strict: bool = False,
+           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k)."""
+    img = _as4d(image)
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dtype not in (torch.uint8, torch.float32):
+        raise ValueError("image dtype must be uint8 or float32")
+    img = img.contiguous()
+    B, C, H, W = img.shape
+    prm = params if params.dim() == 4 else params[None]
+    if prm.dtype != torch.float32 or not prm.is_cuda:
+        raise ValueError("params must be a float32 CUDA tensor")
+    prm = prm.contiguous()
+    K = 4 if kind == "scales" else 3
+    if tuple(prm.shape) != (B, K, H, W):
+        raise ValueError(f"params shape {tuple(prm.shape)} != {(B, K, H, W)}")
+    if out is None:
+        out = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device)
+    dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
+    opts = make_opts(precision, halo, max_scale, eps, eta, strict)
+    rc = L.bsf_filter(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), _KINDS[kind],
+                      opts, out.data_ptr(), _stream_ptr(stream))
+    L.check(rc, "bsf_filter")
+    return out.reshape(image.shape) if image.dim() < 4 else out
+
+
+def scales_from_cov(params: torch.Tensor, kind: str = "srt", N: int = 4, eps: float = 1e-3, eta: float = 1e-3,
+                    stream=None):
+    """Per-pixel optimal scale vectors (Sec. 3.2.2): (3, ...) planes -> ((4, ...), flags uint8)."""
+    prm = params.contiguous()
+    if prm.dtype != torch.float32 or not prm.is_cuda or prm.shape[0] != 3:
+        raise ValueError("params must be a float32 CUDA tensor of shape (3, ...)")
+    npix = prm[0].numel()
+    scales = torch.empty((4,) + tuple(prm.shape[1:]), dtype=torch.float32, device=prm.device)
+    flags = torch.empty(tuple(prm.shape[1:]), dtype=torch.uint8, device=prm.device)
+    opts = make_opts(eps=eps, eta=eta)
+    rc = L.bsf_scales_from_cov(context(prm.device), prm.data_ptr(), _KINDS[kind], npix, N, opts,
+                               scales.data_ptr(), flags.data_ptr(), _stream_ptr(stream))
+    L.check(rc, "bsf_scales_from_cov")
+    return scales, flags
+
+
+def preintegrate(image: torch.Tensor, halo: int, precision: str = "exact", N: int = 4, stream=None) -> torch.Tensor:
+    """Algorithm 1 step 2 for one (H,W) image: the pre-integrated buffer as a
+    tensor of shape (H+2P, W+2P) (int64 / 16-byte pairs as int64 (...,2) / float64)."""
+    if image.dim() != 2 or not image.is_cuda:
+        raise ValueError("image must be a 2-D CUDA tensor")
+    img = image.contiguous()
+    H, W = img.shape
+    dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
+    prec = _PREC[precision]
+    nbytes = L.bsf_buffer_bytes(dtype, H, W, N, halo, prec)
+    Hp, Wp = H + 2 * halo, W + 2 * halo
+    if prec == L.BSF_PREC_FP64:
+        buf = torch.empty((Hp, Wp), dtype=torch.float64, device=img.device)
+    elif dtype == L.BSF_U8:
+        buf = torch.empty((Hp, Wp), dtype=torch.int64, device=img.device)
+    else:
+        buf = torch.empty((Hp, Wp, 2), dtype=torch.int64, device=img.device)
+    assert buf.numel() * buf.element_size() == nbytes
+    rc = L.bsf_preintegrate(context(img.device), img.data_ptr(), dtype, H, W, N, halo, prec, buf.data_ptr(),
+                            _stream_ptr(stream))
+    L.check(rc, "bsf_preintegrate")
+    return buf
+
+
+def apply(buffer: torch.Tensor, image_dtype: torch.dtype, H: int, W: int, halo: int, params: torch.Tensor,
+          kind: str = "scales", precision: str = "exact", N: int = 4, eps: float = 1e-3, eta: float = 1e-3,
+          stream=None) -> torch.Tensor:
+    """Algorithm 1 step 3 on a buffer from preintegrate(): (H, W) float32."""
+    dtype = L.BSF_U8 if image_dtype == torch.uint8 else L.BSF_F32
+    prm = params.contiguous()
+    out = torch.empty((H, W), dtype=torch.float32, device=buffer.device)
+    opts = make_opts(precision, halo=halo, eps=eps, eta=eta)
+    rc = L.bsf_apply(context(buffer.device), buffer.data_ptr(), dtype, H, W, N, halo, prm.data_ptr(), _KINDS[kind],
+                     opts, out.data_ptr(), _stream_ptr(stream))
+    L.check(rc, "bsf_apply")
+    return out
+
+
+def device_status(device=None, stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status bits."""
+    return L.bsf_get_device_status(context(device), _stream_ptr(stream))
+
+
+def halo_for(max_scale: float, kind: str = "srt") -> int:
+    """Padding that covers every tap for fields whose largest footprint is bounded by max_scale
+    (the same rule the library applies for opts.max_scale)."""
+    import math
+    ext = (2.41422 if kind == "scales" else 8.3640) * max_scale
+    return int(math.ceil(0.5 * ext)) + 4

@@ -1,0 +1,379 @@
+// C ABI of the GB300 box-spline filter (see include/bsf.h).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <mutex>
+#include <vector>
+
+#include "bsf_common.cuh"
+#include "bsf_internal.h"
+
+struct bsf_ctx {
+    int device;
+    unsigned* d_status;      // device status word
+    unsigned* d_ext;         // scratch word for the extent reduction
+    void* buf;               // pre-integrated buffers (library-owned)
+    size_t buf_bytes;
+    void* work;              // scan carry workspace
+    size_t work_bytes;
+    std::mutex mu;
+    bool profiling;
+    size_t prof_used;                                // event triples recorded since begin
+    std::vector<std::array<cudaEvent_t, 3>> prof;    // pool of event triples
+};
+
+static cudaError_t prof_mark(bsf_ctx* c, int which, cudaStream_t st) {
+    if (!c->profiling) return cudaSuccess;
+    if (which == 0) {
+        if (c->prof_used == c->prof.size()) {
+            std::array<cudaEvent_t, 3> t;
+            for (int i = 0; i < 3; ++i) {
+                cudaError_t e = cudaEventCreate(&t[i]);
+                if (e != cudaSuccess) return e;
+            }
+            c->prof.push_back(t);
+        }
+        ++c->prof_used;
+    }
+    return cudaEventRecord(c->prof[c->prof_used - 1][which], st);
+}
+
+static bsf_status map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return BSF_OK;
+    if (e == cudaErrorMemoryAllocation) return BSF_ENOMEM;
+    return BSF_ECUDA;
+}
+
+#define BSF_TRY(expr)                          \
+    do {                                       \
+        cudaError_t e_ = (expr);               \
+        if (e_ != cudaSuccess) return map_cuda(e_); \
+    } while (0)
+
+static cudaError_t grow(void** p, size_t* cur, size_t need) {
+    if (*cur >= need && *p != nullptr) return cudaSuccess;
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        *p = nullptr;
+        *cur = 0;
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    *cur = need;
+    return cudaSuccess;
+}
+
+static int mode_of(int dtype, int precision) {
+    if (precision == BSF_PREC_FP64) return MODE_F64;
+    return dtype == BSF_U8 ? MODE_U64 : MODE_U128;
+}
+
+static size_t elem_bytes(int mode) { return mode == MODE_U128 ? 16 : 8; }
+
+extern "C" {
+
+void bsf_default_opts(bsf_opts* o) {
+    if (!o) return;
+    o->precision = BSF_PREC_EXACT;
+    o->eps = 1e-3f;
+    o->eta = 1e-3f;
+    o->strict = 0;
+    o->halo = 0;
+    o->max_scale = 0.f;
+}
+
+const char* bsf_status_string(bsf_status s) {
+    switch (s) {
+        case BSF_OK: return "ok";
+        case BSF_EINVAL: return "invalid argument";
+        case BSF_EUNSUPPORTED: return "unsupported N (only N = 4 is implemented)";
+        case BSF_ENOMEM: return "device allocation failed";
+        case BSF_ECUDA: return "CUDA runtime error";
+        case BSF_EHALO: return "a finite-difference tap left the pre-integrated buffer (halo too small)";
+        case BSF_EINFEASIBLE: return "a covariance needed the elongation clamp (strict mode)";
+        case BSF_EBADSCALE: return "a scale or covariance was not finite and positive";
+        case BSF_ERANGE: return "a kernel too large for the exact integer form";
+        default: return "unknown status";
+    }
+}
+
+bsf_status bsf_create(bsf_ctx** ctx, int device) {
+    if (!ctx) return BSF_EINVAL;
+    *ctx = nullptr;
+    int n = 0;
+    BSF_TRY(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return BSF_EINVAL;
+    BSF_TRY(cudaSetDevice(device));
+    bsf_ctx* c = new bsf_ctx();
+    c->device = device;
+    c->d_status = nullptr;
+    c->d_ext = nullptr;
+    c->buf = nullptr;
+    c->buf_bytes = 0;
+    c->work = nullptr;
+    c->work_bytes = 0;
+    c->profiling = false;
+    c->prof_used = 0;
+    cudaError_t e = cudaMalloc((void**)&c->d_status, 2 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        delete c;
+        return map_cuda(e);
+    }
+    c->d_ext = c->d_status + 1;
+    e = cudaMemset(c->d_status, 0, 2 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return map_cuda(e);
+    }
+    *ctx = c;
+    return BSF_OK;
+}
+
+bsf_status bsf_destroy(bsf_ctx* c) {
+    if (!c) return BSF_EINVAL;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->buf) cudaFree(c->buf);
+    if (c->work) cudaFree(c->work);
+    if (c->d_status) cudaFree(c->d_status);
+    for (auto& t : c->prof)
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(t[i]);
+    delete c;
+    return BSF_OK;
+}
+
+bsf_status bsf_profile_begin(bsf_ctx* c) {
+    if (!c) return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    c->profiling = true;
+    c->prof_used = 0;
+    return BSF_OK;
+}
+
+bsf_status bsf_profile_end(bsf_ctx* c, double* ms_pre, double* ms_st, int* nlaunch) {
+    if (!c) return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    double a = 0, b = 0;
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        BSF_TRY(cudaEventSynchronize(c->prof[i][2]));
+        float t0 = 0, t1 = 0;
+        BSF_TRY(cudaEventElapsedTime(&t0, c->prof[i][0], c->prof[i][1]));
+        BSF_TRY(cudaEventElapsedTime(&t1, c->prof[i][1], c->prof[i][2]));
+        a += t0;
+        b += t1;
+    }
+    if (ms_pre) *ms_pre = a;
+    if (ms_st) *ms_st = b;
+    if (nlaunch) *nlaunch = (int)c->prof_used;
+    c->profiling = false;
+    c->prof_used = 0;
+    return BSF_OK;
+}
+
+bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, int precision, size_t* bytes) {
+    if (!bytes || H <= 0 || W <= 0 || halo < 2) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (precision != BSF_PREC_EXACT && precision != BSF_PREC_FP64) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    const int64_t Hp = H + 2 * (int64_t)halo, Wp = W + 2 * (int64_t)halo;
+    *bytes = (size_t)(Hp * Wp) * elem_bytes(mode_of(dtype, precision));
+    return BSF_OK;
+}
+
+bsf_status bsf_get_device_status(bsf_ctx* c, void* stream, int* status) {
+    if (!c || !status) return BSF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    BSF_TRY(cudaStreamSynchronize(st));
+    BSF_TRY(cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    BSF_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
+    BSF_TRY(cudaStreamSynchronize(st));
+    *status = (int)h;
+    return BSF_OK;
+}
+
+bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_t npix, int N, const bsf_opts* opts,
+                               float* scales, uint8_t* flags, void* stream) {
+    if (!c || !params || !scales || npix < 0) return BSF_EINVAL;
+    if (kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    BSF_TRY(cudaSetDevice(c->device));
+    BSF_TRY(launch_map4(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
+    return BSF_OK;
+}
+
+// halo from opts or from a device reduction over the parameter fields
+static bsf_status resolve_halo(bsf_ctx* c, const float* params, int kind, int64_t nfield, int64_t HW, const bsf_opts& o,
+                               cudaStream_t st, int* P) {
+    if (o.halo > 0) {
+        *P = o.halo;
+        return BSF_OK;
+    }
+    float ext;
+    if (o.max_scale > 0.f) {
+        // SCALES: a1 + (a2 + a4)/sqrt2 <= (1 + sqrt2) max a.  COV/SRT: a1 <= sqrt(12 C11),
+        // a2' + a4' <= sqrt(p2 + p4) <= sqrt(24 C11), C11 <= lambda_max (same along y).
+        ext = (kind == BSF_PARAM_SCALES) ? 2.41422f * o.max_scale : 8.3640f * o.max_scale;
+    } else {
+        const int K = (kind == BSF_PARAM_SCALES) ? 4 : 3;
+        unsigned h = 0;
+        BSF_TRY(cudaMemsetAsync(c->d_ext, 0, sizeof(unsigned), st));
+        for (int64_t b = 0; b < nfield; ++b)
+            BSF_TRY(launch_extent4(params + (size_t)b * K * HW, kind, (long long)HW, o.eps, o.eta, c->d_ext, st));
+        BSF_TRY(cudaMemcpyAsync(&h, c->d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        BSF_TRY(cudaStreamSynchronize(st));
+        memcpy(&ext, &h, sizeof(float));
+    }
+    if (!(ext >= 0.f) || ext > 1e6f) return BSF_EINVAL;
+    *P = (int)ceilf(0.5f * ext) + 4;
+    return BSF_OK;
+}
+
+static cudaError_t run_scan(int mode, int dtype, const void* img, long long img_stride, int nimg, int H, int W, int P,
+                            void* G, long long G_stride, int pitch, void* work, cudaStream_t st) {
+    if (mode == MODE_U64)
+        return launch_scan4<MODE_U64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
+                                               work, st);
+    if (mode == MODE_U128)
+        return launch_scan4<MODE_U128, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
+                                              work, st);
+    if (dtype == BSF_U8)
+        return launch_scan4<MODE_F64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
+                                               work, st);
+    return launch_scan4<MODE_F64, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch, work, st);
+}
+
+static bool dims_ok(int64_t H, int64_t W) {
+    return H > 0 && W > 0 && H <= (1 << 20) && W <= (1 << 20);
+}
+
+bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
+                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
+    if (!c || !image || !params || !out) return BSF_EINVAL;
+    if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != BSF_PREC_EXACT && o.precision != BSF_PREC_FP64) return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t HW = H * W;
+    int P = 0;
+    bsf_status s = resolve_halo(c, params, kind, B, HW, o, st, &P);
+    if (s != BSF_OK) return s;
+    const int mode = mode_of(dtype, o.precision);
+    const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P, pitch = Wp;
+    const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
+    // images per launch: whole batch entries, bounded by a 16 GiB buffer budget
+    const size_t budget = (size_t)16 << 30;
+    int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / (per_img * (size_t)C)));
+    bchunk = std::min<int64_t>(bchunk, B);
+    const int K = (kind == BSF_PARAM_SCALES) ? 4 : 3;
+    const size_t esz = (dtype == BSF_U8) ? 1 : 4;
+    for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
+        const int64_t nbat = std::min<int64_t>(bchunk, B - b0);
+        const int nimg = (int)(nbat * C);
+        const scan_plan plan = make_scan_plan(Hp, Wp, nimg, elem_bytes(mode));
+        BSF_TRY(grow(&c->buf, &c->buf_bytes, per_img * nimg));
+        BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
+        const char* img0 = (const char*)image + (size_t)(b0 * C) * HW * esz;
+        BSF_TRY(prof_mark(c, 0, st));
+        BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf,
+                         (long long)Hp * pitch, pitch, c->work, st));
+        stencil_args a;
+        a.buf = c->buf;
+        a.buf_stride = (long long)Hp * pitch;
+        a.Hp = Hp;
+        a.Wp = Wp;
+        a.pitch = pitch;
+        a.P = P;
+        a.H = (int)H;
+        a.W = (int)W;
+        a.C = (int)C;
+        a.nimg = nimg;
+        a.params = params + (size_t)b0 * K * HW;
+        a.kind = kind;
+        a.eps = o.eps;
+        a.eta = o.eta;
+        a.out = out + (size_t)(b0 * C) * HW;
+        a.status = c->d_status;
+        BSF_TRY(prof_mark(c, 1, st));
+        BSF_TRY(launch_stencil4(mode, a, st));
+        BSF_TRY(prof_mark(c, 2, st));
+    }
+    if (o.strict) {
+        unsigned h = 0;
+        BSF_TRY(cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        BSF_TRY(cudaStreamSynchronize(st));
+        if (h & (1u << BSF_EINFEASIBLE)) return BSF_EINFEASIBLE;
+    }
+    return BSF_OK;
+}
+
+bsf_status bsf_preintegrate(bsf_ctx* c, const void* image, int dtype, int64_t H, int64_t W, int N, int halo,
+                            int precision, void* buffer, void* stream) {
+    if (!c || !image || !buffer || !dims_ok(H, W) || halo < 2) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (precision != BSF_PREC_EXACT && precision != BSF_PREC_FP64) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    const int mode = mode_of(dtype, precision);
+    const int Hp = (int)H + 2 * halo, Wp = (int)W + 2 * halo;
+    const scan_plan plan = make_scan_plan(Hp, Wp, 1, elem_bytes(mode));
+    BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
+    BSF_TRY(run_scan(mode, dtype, image, (long long)H * W, 1, (int)H, (int)W, halo, buffer, (long long)Hp * Wp, Wp,
+                     c->work, (cudaStream_t)stream));
+    return BSF_OK;
+}
+
+bsf_status bsf_apply(bsf_ctx* c, const void* buffer, int dtype, int64_t H, int64_t W, int N, int halo,
+                     const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
+    if (!c || !buffer || !params || !out || !dims_ok(H, W) || halo < 2) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != BSF_PREC_EXACT && o.precision != BSF_PREC_FP64) return BSF_EINVAL;
+    BSF_TRY(cudaSetDevice(c->device));
+    const int mode = mode_of(dtype, o.precision);
+    stencil_args a;
+    a.buf = buffer;
+    a.buf_stride = 0;
+    a.Hp = (int)H + 2 * halo;
+    a.Wp = (int)W + 2 * halo;
+    a.pitch = a.Wp;
+    a.P = halo;
+    a.H = (int)H;
+    a.W = (int)W;
+    a.C = 1;
+    a.nimg = 1;
+    a.params = params;
+    a.kind = kind;
+    a.eps = o.eps;
+    a.eta = o.eta;
+    a.out = out;
+    a.status = c->d_status;
+    BSF_TRY(launch_stencil4(mode, a, (cudaStream_t)stream));
+    return BSF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Shared device-side definitions of the GB300 box-spline filter library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bsf.h"
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// Arithmetic forms of the pre-integrated buffer.
+//   MODE_U64  : uint8 image, exact integer running sums modulo 2^64
+//   MODE_U128 : float32 image in fixed point (32 fractional bits), sums modulo 2^128
+//   MODE_F64  : all-FP64 form (Algorithm 1 computed literally in double)
+enum { MODE_U64 = 0, MODE_U128 = 1, MODE_F64 = 2 };
+
+template <int MODE> struct mode_traits;
+template <> struct mode_traits<MODE_U64> {
+    typedef unsigned long long T;
+    static constexpr int ACC_BITS = 64;
+    static constexpr int VAL_BITS = 8;    // |f| < 2^8
+    static constexpr int FRAC_BITS = 0;
+};
+template <> struct mode_traits<MODE_U128> {
+    typedef u128 T;
+    static constexpr int ACC_BITS = 128;
+    static constexpr int VAL_BITS = 63;   // |f * 2^32| < 2^63
+    static constexpr int FRAC_BITS = 32;
+};
+template <> struct mode_traits<MODE_F64> {
+    typedef double T;
+    static constexpr int ACC_BITS = 0;
+    static constexpr int VAL_BITS = 0;
+    static constexpr int FRAC_BITS = 0;
+};
+
+// Image sample -> accumulator element.
+__device__ __forceinline__ unsigned long long to_acc_u64(uint8_t v) { return (unsigned long long)v; }
+__device__ __forceinline__ u128 to_acc_u128(float v) {
+    // round(v * 2^32) as a signed 64-bit integer, sign-extended to 128 bits
+    long long q = __double2ll_rn((double)v * 4294967296.0);
+    return (u128)(i128)q;
+}
+
+template <int MODE, class InT> __device__ __forceinline__ typename mode_traits<MODE>::T load_sample(InT v);
+template <> __device__ __forceinline__ unsigned long long load_sample<MODE_U64, uint8_t>(uint8_t v) {
+    return to_acc_u64(v);
+}
+template <> __device__ __forceinline__ u128 load_sample<MODE_U128, float>(float v) { return to_acc_u128(v); }
+template <> __device__ __forceinline__ double load_sample<MODE_F64, uint8_t>(uint8_t v) { return (double)v; }
+template <> __device__ __forceinline__ double load_sample<MODE_F64, float>(float v) { return (double)v; }
+
+// Warp shuffles of 64/128-bit values, split into 32-bit words.
+template <class T> __device__ __forceinline__ T shfl_up_T(T v, int d) {
+    static_assert(sizeof(T) % 4 == 0, "word size");
+    union { T t; unsigned w[sizeof(T) / 4]; } u;
+    u.t = v;
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) u.w[i] = __shfl_up_sync(0xffffffffu, u.w[i], d);
+    return u.t;
+}
+template <class T> __device__ __forceinline__ T shfl_down_T(T v, int d) {
+    union { T t; unsigned w[sizeof(T) / 4]; } u;
+    u.t = v;
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) u.w[i] = __shfl_down_sync(0xffffffffu, u.w[i], d);
+    return u.t;
+}
+
+// Device status word bits (1 << BSF_E*).
+__device__ __forceinline__ void raise_status(unsigned* status, int code) {
+    if (status) atomicOr(status, 1u << code);
+}
+
+// 128-bit two's-complement integer -> float (round to nearest of the top 64 bits).
+__device__ __forceinline__ float i128_to_float(u128 v) {
+    bool neg = (long long)(unsigned long long)(v >> 64) < 0;
+    u128 m = neg ? (u128)(-(i128)v) : v;
+    unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
+    float r;
+    if (hi == 0) {
+        r = __ull2float_rn(lo);
+    } else {
+        int lz = __clzll(hi);               // 0..63
+        int sh = 64 - lz;                   // bits to drop so the value fits 64 bits
+        u128 t = m >> sh;
+        // sticky bit keeps round-to-nearest honest for the dropped part
+        unsigned long long top = (unsigned long long)t | (((m & ((((u128)1) << sh) - 1)) != 0) ? 1ull : 0ull);
+        r = ldexpf(__ull2float_rn(top), sh);
+    }
+    return neg ? -r : r;
+}
+
+__host__ __device__ __forceinline__ int ceil_div_i(int a, int b) { return (a + b - 1) / b; }

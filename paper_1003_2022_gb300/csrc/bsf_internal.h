@@ -1,0 +1,43 @@
+// Host-side declarations shared by the translation units of libbsf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+struct scan_plan {
+    int band_h;         // rows per band
+    int nb;             // bands per image
+    int cpt;            // columns per thread in the band kernel
+    int threads;        // threads per band CTA
+    size_t work_bytes;  // carry workspace for all images of one launch
+    size_t smem;        // dynamic shared memory of the band kernel (g2 state)
+    bool ok;            // false: the row is too wide for one CTA
+};
+
+scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes);
+
+// Pre-integration (RS1-RS4) of nimg images of H x W (stride img_stride
+// elements) into buffers of Hp x pitch elements (stride G_stride elements).
+template <int MODE, class InT>
+cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
+                         long long G_stride, int pitch, void* work, cudaStream_t st);
+
+struct stencil_args {
+    const void* buf;
+    long long buf_stride;  // elements between consecutive images' buffers
+    int Hp, Wp, pitch, P, H, W;
+    int C;                 // channels sharing one parameter field
+    int nimg;              // images in this launch (a multiple of C)
+    const float* params;   // parameter planes of the first image's field
+    int kind;
+    float eps, eta;
+    float* out;
+    unsigned* status;
+};
+
+cudaError_t launch_stencil4(int mode, const stencil_args& a, cudaStream_t st);
+cudaError_t launch_map4(const float* params, int kind, long long npix, float eps, float eta, float* scales,
+                        uint8_t* flags, cudaStream_t st);
+cudaError_t launch_extent4(const float* params, int kind, long long npix, float eps, float eta, unsigned* ext_bits,
+                           cudaStream_t st);

@@ -1,0 +1,331 @@
+// Local finite difference with Zwart-Powell interpolation (Algorithm 1
+// step 3; Table 1; Eq. final_eqn; App. F), four-directional box spline.
+//
+// For every pixel n with scale vector a = a(n):
+//   fbar[n] = (1/(a1 a2 a3 a4)) sum_{i=0}^{15} (-1)^{|q|} F(n + tau - x_i),
+//   F(y)    = sum_m g_b[m] beta_b(y - m),   g_b = 2 G,
+// with x_i = q1 a1 (1,0) + q2 a2' (1,1) + q3 a3 (0,1) + q4 a4' (-1,1),
+// a'_k = a_k / sqrt2, tau = ((a1 + a2' - a4' - 1)/2, (a2' + a3 + a4' - 3)/2).
+// So fbar = (1/(a1 a2' a3 a4')) sum_i s_i sum_m G[m] beta_b(y_i - m).
+//
+// ZP interpolation.  With m0 = round(y) and phi = y - m0 in [-1/2, 1/2)^2,
+// the cell around m0 is cut by its two diagonals into four triangles; the
+// element is D4-symmetric, so each triangle is rotated onto the canonical one
+// (phi_x >= |phi_y|), where exactly seven lattice points carry weight and
+// each weight is one quadratic in phi.  Collecting those quadratics by
+// monomial gives (derived from the box-spline definition, Eq. const at
+// a = b = (1, sqrt2, 1, sqrt2)):
+//   8 F = K1 + Kx x + Ky y + Kxx x^2 + Kxy x y + Kyy y^2
+//   K1  = 4 g00 + gW + gE + gS + gN,   Kx = 4 (gE - gW),  Ky = 4 (gN - gS),
+//   Kxx = 4 (gW - g00) - 2 (gS + gN) + 2 (gSE + gNE),
+//   Kxy = 4 (gS - gN - gSE + gNE),
+//   Kyy = -4 (g00 + gE) + 2 (gS + gN) + 2 (gSE + gNE),
+// where gW/gE/gS/gN/gSE/gNE are G at m0 + (-1,0)/(1,0)/(0,-1)/(0,1)/(1,-1)/(1,1)
+// in the rotated frame.
+//
+// Exact integer form (MODE_U64 / MODE_U128).  a'_k is rounded to A_k 2^-q
+// with a per-pixel q; then every tap position lies on the 2^-(q+1) grid, the
+// mesh of Table 1 is exact for the rounded scales, and
+//   S = 2^(2q+4) sum_i s_i F(y_i)
+// is an integer combination of G.  It is evaluated modulo 2^64 / 2^128: the
+// true S is bounded by 2^(2q+4) * max|f| * prod(a') * (lattice mass), and q
+// is chosen per pixel so that this bound stays below 2^(ACC-2); then the
+// wrapped result IS S, whatever the size of G.  The only rounding is the
+// final conversion fbar = S 2^(2q-4-frac) / prod(A) in FP32.
+//
+// All-FP64 form (MODE_F64): the same formulas in double, positions and
+// weights unrounded (Algorithm 1 computed literally).
+#include "bsf_common.cuh"
+#include "bsf_internal.h"
+#include "map4.cuh"
+
+namespace {
+
+__device__ __forceinline__ int ilog2_ceil(float v) {
+    // smallest integer e with 2^e >= v, for v > 0
+    int e;
+    const float m = frexpf(v, &e);  // v = m 2^e, m in [0.5, 1)
+    return (m == 0.5f) ? e - 1 : e;
+}
+
+template <class T> __device__ __forceinline__ T mul_s32(T v, int s) { return v * (T)(long long)s; }
+
+template <int MODE> struct pixel_acc;
+
+template <int MODE>
+__device__ __forceinline__ void load_scales(int kind, const float* __restrict__ pr, size_t HW, size_t p, float eps,
+                                            float eta, float& a1, float& a2, float& a3, float& a4, int& mflag) {
+    mflag = 0;
+    if (kind == BSF_PARAM_SCALES) {
+        a1 = pr[p];
+        a2 = pr[HW + p];
+        a3 = pr[2 * HW + p];
+        a4 = pr[3 * HW + p];
+    } else {
+        const map4_result R = map4_solve(kind, pr[p], pr[HW + p], pr[2 * HW + p], eps, eta);
+        a1 = R.a[0];
+        a2 = R.a[1];
+        a3 = R.a[2];
+        a4 = R.a[3];
+        mflag = R.flag;
+    }
+}
+
+// canonical-frame strides for the four triangles
+__device__ __forceinline__ void tri_frame(int fx, int fy, int pitch, int& X, int& Y, int& se, int& sf) {
+    const int d1 = fx - fy, d2 = fx + fy;
+    if (d2 >= 0) {
+        if (d1 >= 0) { X = fx;  Y = fy;  se = 1;      sf = pitch; }   // x >= |y|
+        else         { X = fy;  Y = -fx; se = pitch;  sf = -1;    }   // y >= |x|
+    } else {
+        if (d1 >= 0) { X = -fy; Y = fx;  se = -pitch; sf = 1;     }   // -y >= |x|
+        else         { X = -fx; Y = -fy; se = -1;     sf = -pitch; }  // -x >= |y|
+    }
+}
+
+template <int MODE, int KIND>
+__global__ void __launch_bounds__(256) k_stencil4_exact(const void* __restrict__ buf, long long buf_stride, int Hp,
+                                                         int Wp, int pitch, int P, int H, int W, int C,
+                                                         const float* __restrict__ params, float eps, float eta,
+                                                         float* __restrict__ out, unsigned* status) {
+    typedef typename mode_traits<MODE>::T T;
+    constexpr int ACC = mode_traits<MODE>::ACC_BITS;
+    constexpr int VAL = mode_traits<MODE>::VAL_BITS;
+    constexpr int FRAC = mode_traits<MODE>::FRAC_BITS;
+    const int n1 = blockIdx.x * 32 + threadIdx.x;
+    const int n2 = blockIdx.y * 8 + threadIdx.y;
+    const int im = blockIdx.z;
+    if (n1 >= W || n2 >= H) return;
+    const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
+    const int K = (KIND == BSF_PARAM_SCALES) ? 4 : 3;
+    const float* pr = params + (size_t)(im / C) * K * HW;
+    float a1, a2, a3, a4;
+    int mflag;
+    load_scales<MODE>(KIND, pr, HW, p, eps, eta, a1, a2, a3, a4, mflag);
+    float* o = out + (size_t)im * HW + p;
+    if (mflag & 1) raise_status(status, BSF_EINFEASIBLE);
+    if (!(a1 > 0.f && a2 > 0.f && a3 > 0.f && a4 > 0.f) || !(a1 < 1e30f && a2 < 1e30f && a3 < 1e30f && a4 < 1e30f)) {
+        raise_status(status, BSF_EBADSCALE);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const float a2p = a2 * 0.70710678118654752f, a4p = a4 * 0.70710678118654752f;
+    // bound on prod(a') * lattice mass
+    const float Bm = fminf((a1 + 1.f) * (a3 + 1.f) * a2p * a4p, 0.5f * a1 * a3 * (2.f * a2p + 1.f) * (a4p + 1.f));
+    int q = (ACC - 6 - VAL - ilog2_ceil(Bm)) >> 1;
+    q = min(q, 24);
+    q = min(q, 30 - ilog2_ceil(a1 + a2p + a3 + a4p + 3.f));
+    if (q < 0) {
+        raise_status(status, BSF_ERANGE);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const float sc = ldexpf(1.f, q);
+    const int A1 = __float2int_rn(a1 * sc), A2 = __float2int_rn(a2p * sc);
+    const int A3 = __float2int_rn(a3 * sc), A4 = __float2int_rn(a4p * sc);
+    if (A1 < 1 || A2 < 1 || A3 < 1 || A4 < 1) {
+        raise_status(status, BSF_ERANGE);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int one = 1 << q;
+    const int sh1 = q + 1;
+    const T* G = (const T*)buf + (size_t)im * buf_stride;
+    const int bx = n1 + P, by = n2 + P;
+    T S = T(0);
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int sg1 = (i & 1) ? -1 : 1, sg2 = (i & 2) ? -1 : 1, sg3 = (i & 4) ? -1 : 1, sg4 = (i & 8) ? -1 : 1;
+        // tau - x_i in units of 2^-(q+1)
+        const int Ox = sg1 * A1 + sg2 * A2 - sg4 * A4 - one;
+        const int Oy = sg2 * A2 + sg3 * A3 + sg4 * A4 - 3 * one;
+        const int mx = (Ox + one) >> sh1, my = (Oy + one) >> sh1;
+        const int fx = Ox - (mx << sh1), fy = Oy - (my << sh1);
+        const int cx = bx + mx, cy = by + my;
+        if (cx < 1 || cx > Wp - 2 || cy < 1 || cy > Hp - 2) {
+            bad = true;
+            continue;
+        }
+        int X, Y, se, sf;
+        tri_frame(fx, fy, pitch, X, Y, se, sf);
+        const T* c = G + (size_t)cy * pitch + cx;
+        const T g00 = c[0], gW = c[-se], gE = c[se], gS = c[-sf], gN = c[sf], gSE = c[se - sf], gNE = c[se + sf];
+        const T u = gS + gN, t = gSE + gNE;
+        const T K1 = (g00 << 2) + gW + gE + u;
+        const T kx = gE - gW, ky = gN - gS;
+        const T kxx = ((gW - g00) << 1) - u + t;
+        const T kxy = gS - gN - gSE + gNE;
+        const T kyy = t + u - ((g00 + gE) << 1);
+        const T hx = (kx << (q + 2)) + mul_s32(kxx, X) + mul_s32(kxy << 1, Y);
+        const T hy = (ky << (q + 2)) + mul_s32(kyy, Y);
+        const T F = (K1 << (2 * q + 1)) + mul_s32(hx, X) + mul_s32(hy, Y);
+        if ((sg1 * sg2 * sg3 * sg4) > 0) S += F; else S -= F;
+    }
+    if (bad) {
+        raise_status(status, BSF_EHALO);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const float prodA = ((float)A1 * (float)A2) * ((float)A3 * (float)A4);
+    float sf;
+    if constexpr (MODE == MODE_U64) sf = __ll2float_rn((long long)S);
+    else sf = i128_to_float(S);
+    *o = ldexpf(sf / prodA, 2 * q - 4 - FRAC);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_stencil4_f64(const double* __restrict__ buf, long long buf_stride, int Hp,
+                                                       int Wp, int pitch, int P, int H, int W, int C,
+                                                       const float* __restrict__ params, float eps, float eta,
+                                                       float* __restrict__ out, unsigned* status) {
+    const int n1 = blockIdx.x * 32 + threadIdx.x;
+    const int n2 = blockIdx.y * 8 + threadIdx.y;
+    const int im = blockIdx.z;
+    if (n1 >= W || n2 >= H) return;
+    const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
+    const int K = (KIND == BSF_PARAM_SCALES) ? 4 : 3;
+    const float* pr = params + (size_t)(im / C) * K * HW;
+    float fa1, fa2, fa3, fa4;
+    int mflag;
+    load_scales<MODE_F64>(KIND, pr, HW, p, eps, eta, fa1, fa2, fa3, fa4, mflag);
+    float* o = out + (size_t)im * HW + p;
+    if (mflag & 1) raise_status(status, BSF_EINFEASIBLE);
+    if (!(fa1 > 0.f && fa2 > 0.f && fa3 > 0.f && fa4 > 0.f) ||
+        !(fa1 < 1e30f && fa2 < 1e30f && fa3 < 1e30f && fa4 < 1e30f)) {
+        raise_status(status, BSF_EBADSCALE);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const double a1 = fa1, a3 = fa3;
+    const double a2p = (double)fa2 * 0.70710678118654752440, a4p = (double)fa4 * 0.70710678118654752440;
+    const double* G = buf + (size_t)im * buf_stride;
+    const int bx = n1 + P, by = n2 + P;
+    double S = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const double sg1 = (i & 1) ? -1.0 : 1.0, sg2 = (i & 2) ? -1.0 : 1.0;
+        const double sg3 = (i & 4) ? -1.0 : 1.0, sg4 = (i & 8) ? -1.0 : 1.0;
+        const double Ox = 0.5 * (sg1 * a1 + sg2 * a2p - sg4 * a4p - 1.0);
+        const double Oy = 0.5 * (sg2 * a2p + sg3 * a3 + sg4 * a4p - 3.0);
+        const double mxd = floor(Ox + 0.5), myd = floor(Oy + 0.5);
+        const double fx = Ox - mxd, fy = Oy - myd;
+        const int cx = bx + (int)mxd, cy = by + (int)myd;
+        if (cx < 1 || cx > Wp - 2 || cy < 1 || cy > Hp - 2) {
+            bad = true;
+            continue;
+        }
+        double X, Y;
+        int se, sf;
+        {
+            const double d1 = fx - fy, d2 = fx + fy;
+            if (d2 >= 0) {
+                if (d1 >= 0) { X = fx;  Y = fy;  se = 1;      sf = pitch; }
+                else         { X = fy;  Y = -fx; se = pitch;  sf = -1;    }
+            } else {
+                if (d1 >= 0) { X = -fy; Y = fx;  se = -pitch; sf = 1;     }
+                else         { X = -fx; Y = -fy; se = -1;     sf = -pitch; }
+            }
+        }
+        const double* c = G + (size_t)cy * pitch + cx;
+        const double g00 = c[0], gW = c[-se], gE = c[se], gS = c[-sf], gN = c[sf], gSE = c[se - sf],
+                     gNE = c[se + sf];
+        const double u = gS + gN, t = gSE + gNE;
+        const double K1 = 4.0 * g00 + gW + gE + u;
+        const double kx = gE - gW, ky = gN - gS;
+        const double kxx = 2.0 * (gW - g00) - u + t;
+        const double kxy = gS - gN - gSE + gNE;
+        const double kyy = t + u - 2.0 * (g00 + gE);
+        const double F = 0.125 * K1 + 0.5 * (kx * X + ky * Y) + 0.25 * ((kxx * X + 2.0 * kxy * Y) * X + kyy * Y * Y);
+        S += (sg1 * sg2 * sg3 * sg4) * F;
+    }
+    if (bad) {
+        raise_status(status, BSF_EHALO);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    *o = (float)(S / (a1 * a2p * a3 * a4p));
+}
+
+__global__ void k_map4(const float* __restrict__ params, int kind, long long npix, float eps, float eta,
+                       float* __restrict__ scales, uint8_t* __restrict__ flags) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const map4_result R = map4_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scales[k * npix + p] = R.a[k];
+    if (flags) flags[p] = (uint8_t)R.flag;
+}
+
+// largest footprint extent max(a1 + a2' + a4', a2' + a3 + a4') over a field
+__global__ void k_extent4(const float* __restrict__ params, int kind, long long npix, float eps, float eta,
+                          unsigned* __restrict__ ext_bits) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (p < npix) {
+        float a[4];
+        if (kind == BSF_PARAM_SCALES) {
+            for (int k = 0; k < 4; ++k) a[k] = params[k * npix + p];
+        } else {
+            const map4_result R = map4_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta);
+            for (int k = 0; k < 4; ++k) a[k] = R.a[k];
+        }
+        const float a2p = a[1] * 0.70710678f, a4p = a[3] * 0.70710678f;
+        e = fmaxf(a[0] + a2p + a4p, a2p + a[2] + a4p);
+        if (!(e < 1e30f)) e = 0.f;  // invalid pixels are reported by the filter itself
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, d));
+    if ((threadIdx.x & 31) == 0 && e > 0.f) atomicMax(ext_bits, __float_as_uint(e));
+}
+
+}  // namespace
+
+template <int MODE, int KIND>
+static void launch_exact(const stencil_args& a, cudaStream_t st) {
+    dim3 blk(32, 8), grd((a.W + 31) / 32, (a.H + 7) / 8, a.nimg);
+    k_stencil4_exact<MODE, KIND><<<grd, blk, 0, st>>>(a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H, a.W, a.C,
+                                                      a.params, a.eps, a.eta, a.out, a.status);
+}
+
+template <int KIND>
+static void launch_f64(const stencil_args& a, cudaStream_t st) {
+    dim3 blk(32, 8), grd((a.W + 31) / 32, (a.H + 7) / 8, a.nimg);
+    k_stencil4_f64<KIND><<<grd, blk, 0, st>>>((const double*)a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H,
+                                              a.W, a.C, a.params, a.eps, a.eta, a.out, a.status);
+}
+
+template <int MODE>
+static void launch_mode(const stencil_args& a, cudaStream_t st) {
+    if constexpr (MODE == MODE_F64) {
+        if (a.kind == BSF_PARAM_SCALES) launch_f64<BSF_PARAM_SCALES>(a, st);
+        else if (a.kind == BSF_PARAM_COV) launch_f64<BSF_PARAM_COV>(a, st);
+        else launch_f64<BSF_PARAM_SRT>(a, st);
+    } else {
+        if (a.kind == BSF_PARAM_SCALES) launch_exact<MODE, BSF_PARAM_SCALES>(a, st);
+        else if (a.kind == BSF_PARAM_COV) launch_exact<MODE, BSF_PARAM_COV>(a, st);
+        else launch_exact<MODE, BSF_PARAM_SRT>(a, st);
+    }
+}
+
+cudaError_t launch_stencil4(int mode, const stencil_args& a, cudaStream_t st) {
+    if (mode == MODE_U64) launch_mode<MODE_U64>(a, st);
+    else if (mode == MODE_U128) launch_mode<MODE_U128>(a, st);
+    else launch_mode<MODE_F64>(a, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map4(const float* params, int kind, long long npix, float eps, float eta, float* scales,
+                        uint8_t* flags, cudaStream_t st) {
+    if (npix <= 0) return cudaSuccess;
+    k_map4<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(params, kind, npix, eps, eta, scales, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extent4(const float* params, int kind, long long npix, float eps, float eta, unsigned* ext_bits,
+                           cudaStream_t st) {
+    if (npix <= 0) return cudaSuccess;
+    k_extent4<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(params, kind, npix, eps, eta, ext_bits);
+    return cudaGetLastError();
+}

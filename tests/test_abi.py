@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point of include/bsf.h.
+
+CPU only: no compute call is made; host-only entry points (defaults,
+buffer sizes, status strings, argument validation) are exercised.
+"""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bsf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsf_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1003_2022_gb300 import build
+    build.build()
+    from paper_1003_2022_gb300 import _lib
+    return _lib
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = lib.load()
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(so, n), n
+    assert sorted(lib.EXPORTS) == names
+
+
+def test_host_only_calls(lib):
+    o = lib.default_opts()
+    assert o.precision == lib.BSF_PREC_EXACT and abs(o.eps - 1e-3) < 1e-9 and o.halo == 0
+    assert lib.bsf_buffer_bytes(lib.BSF_U8, 10, 20, 4, 3, lib.BSF_PREC_EXACT) == 16 * 26 * 8
+    assert lib.bsf_buffer_bytes(lib.BSF_F32, 10, 20, 4, 3, lib.BSF_PREC_EXACT) == 16 * 26 * 16
+    assert lib.bsf_buffer_bytes(lib.BSF_F32, 10, 20, 4, 3, lib.BSF_PREC_FP64) == 16 * 26 * 8
+    with pytest.raises(lib.BsfError) as e:
+        lib.bsf_buffer_bytes(lib.BSF_U8, 10, 20, 6, 3, lib.BSF_PREC_EXACT)
+    assert e.value.code == lib.BSF_EUNSUPPORTED
+    with pytest.raises(lib.BsfError):
+        lib.bsf_buffer_bytes(lib.BSF_U8, 0, 20, 4, 3, lib.BSF_PREC_EXACT)
+    for code in range(0, 9):
+        assert lib.status_string(code) not in ("", "unknown status")
+    # null context and null pointers are rejected before any CUDA call
+    assert lib.bsf_filter(None, 0, 0, 1, 1, 8, 8, 4, 0, 0, None, 0, 0) == lib.BSF_EINVAL
+    assert lib.bsf_scales_from_cov(None, 0, 2, 10, 4, None, 0, 0, 0) == lib.BSF_EINVAL
+
+
+def test_python_binding_refuses_to_run_without_library(tmp_path, lib):
+    import importlib
+    mod = importlib.import_module("paper_1003_2022_gb300._lib")
+    saved = mod._lib
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError):
+            mod.load(str(tmp_path / "missing.so"))
+    finally:
+        mod._lib = saved

@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: the filter output must match the oracle's plain definition
+fbar[n] = sum_k f[k] beta_{a(n)}(n-k) within 1e-5 normwise
+(max |gpu - ref| / max |ref|), the bar of the workload statement.  The
+pre-integration of integer images must be bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1003_2022_gb300 import _lib as L  # noqa: E402
+from paper_1003_2022_gb300 import api, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+DEV = "cuda:0"
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device(DEV)
+
+
+def _nerr(got, ref):
+    return float(np.abs(np.asarray(got, np.float64) - ref).max() / np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ pre-integration
+@pytest.mark.parametrize("H,W,P", [(1, 1, 2), (5, 7, 3), (37, 53, 9), (64, 64, 12), (100, 333, 20),
+                                   (257, 130, 40), (700, 900, 60), (1900, 2100, 120)])
+def test_preintegrate_u8_bitexact(H, W, P):
+    dev = _cuda()
+    f = synth.image(H, W, seed=H * 1000 + W, dtype="u8")
+    buf = api.preintegrate(torch.from_numpy(f).to(dev), halo=P)
+    ref = O.preint4_i64(f.astype(np.int64), P)
+    assert np.array_equal(buf.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("H,W,P", [(5, 7, 3), (64, 48, 10), (300, 410, 25)])
+def test_preintegrate_f32_fixed_point_bitexact(H, W, P):
+    """f32 -> round(f 2^32): the low 64 bits of the 128-bit sums equal the
+    oracle's integer recursion modulo 2^64."""
+    dev = _cuda()
+    f = synth.image(H, W, seed=11, dtype="f32")
+    buf = api.preintegrate(torch.from_numpy(f).to(dev), halo=P).cpu().numpy()  # (Hp, Wp, 2) lo, hi
+    fi = np.rint(f.astype(np.float64) * 2.0 ** 32).astype(np.int64)
+    ref = O.preint4_i64(fi, P)
+    assert np.array_equal(buf[..., 0], ref)
+    if H * W <= 64:  # small enough that the sums fit 63 bits: the high word is the sign extension
+        assert np.array_equal(buf[..., 1], np.where(ref < 0, -1, 0))
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_preintegrate_fp64_form(dtype):
+    dev = _cuda()
+    H, W, P = 90, 120, 15
+    f = synth.image(H, W, seed=5, dtype=dtype)
+    buf = api.preintegrate(torch.from_numpy(f).to(dev), halo=P, precision="fp64").cpu().numpy()
+    gb = O.preint4_f64(f.astype(np.float64), P)
+    assert np.allclose(2.0 * buf, gb, rtol=1e-12, atol=1e-12 * np.abs(gb).max())
+
+
+# ------------------------------------------------------------------ scale map
+@pytest.mark.parametrize("kind", ["srt", "cov"])
+def test_scales_from_cov_parity(kind):
+    dev = _cuda()
+    H, W = 96, 128
+    p = synth.srt_field(H, W, seed=3, sigma=(1.0, 32.0), rho=(1.0, 8.0), theta="vector")
+    if kind == "cov":
+        s, r, t = p.astype(np.float64)
+        lmax, lmin = s * s, s * s / r
+        c, sn = np.cos(t), np.sin(t)
+        p = np.stack([lmax * c * c + lmin * sn * sn, (lmax - lmin) * sn * c, lmin * c * c + lmax * sn * sn]
+                     ).astype(np.float32)
+    a_gpu, fl_gpu = api.scales_from_cov(torch.from_numpy(p).to(dev), kind=kind)
+    a_gpu = a_gpu.cpu().numpy().astype(np.float64)
+    a_ref, fl_ref = O.map4(p.astype(np.float64), O.KIND_SRT if kind == "srt" else O.KIND_COV)
+    ok = fl_ref == fl_gpu.cpu().numpy()
+    assert ok.mean() > 0.99
+    # scale error relative to the largest scale of the pixel (the filter depends on a_k to
+    # within its own footprint; see the end-to-end tests for the output bar)
+    rel = np.abs(a_gpu - a_ref).max(axis=0) / a_ref.max(axis=0)
+    assert np.percentile(rel[ok], 99.9) < 2e-5, np.percentile(rel[ok], 99.9)
+    # the covariance of the GPU scales reproduces the target where no clamp applied
+    sel = ok & (fl_ref == 0)
+    pg = a_gpu[:, sel] ** 2
+    c11 = (2 * pg[0] + pg[1] + pg[3]) / 24
+    c11r = (2 * a_ref[0, sel] ** 2 + a_ref[1, sel] ** 2 + a_ref[3, sel] ** 2) / 24
+    assert np.abs(c11 / c11r - 1).max() < 1e-5
+
+
+# ------------------------------------------------------------------ whole path
+def _run(f, params, kind, **kw):
+    dev = _cuda()
+    out = api.filter(torch.from_numpy(f).to(dev), torch.from_numpy(params).to(dev), kind=kind, **kw)
+    st = api.device_status(dev)
+    return out.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("H,W", [(64, 80), (45, 67)])
+def test_filter_scales_parity(dtype, H, W):
+    """Identical scale fields on both sides: the only GPU error is the
+    per-pixel dyadic rounding of a and the final FP32 rounding."""
+    f = synth.image(H, W, seed=21, dtype=dtype)
+    rng = np.random.default_rng(4)
+    a = rng.uniform(0.3, 9.0, size=(4, H, W)).astype(np.float32)
+    out, st = _run(f, a, "scales", max_scale=9.0)
+    assert st == 0
+    ref = O.direct4(f.astype(np.float64), a.astype(np.float64))
+    assert _nerr(out, ref) < TOL
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_filter_srt_parity_small_workload(dtype):
+    """256x256-shaped workload at a reduced size: sigma 2-8, rho 1-4, smooth fields."""
+    H, W = 96, 112
+    f = synth.image(H, W, seed=1, dtype=dtype)
+    p = synth.srt_field(H, W, seed=1, sigma=(2.0, 8.0), rho=(1.0, 4.0))
+    out, st = _run(f, p, "srt", max_scale=8.0)
+    assert st == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    idx = np.random.default_rng(0).choice(H * W, size=600, replace=False)
+    ref = O.direct4(f.astype(np.float64), a, idx)
+    assert _nerr(out.ravel()[idx], ref) < TOL
+
+
+def test_filter_u2048_full_size_sampled():
+    """The 2048x2048 u8 workload at full size (sigma 1-32, rho 1-8 clamped by
+    Prop. 3.1, orientation from a vector field), in the launch configuration
+    the benchmark times; checked on sampled pixels including the borders."""
+    f, p = synth.workload_inputs("u2048_u8_n4")
+    out, st = _run(f, p, "srt", max_scale=32.0)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    H, W = f.shape
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    rng = np.random.default_rng(9)
+    idx = np.concatenate([rng.choice(H * W, size=150, replace=False),
+                          np.array([0, W - 1, (H - 1) * W, H * W - 1, W // 2, (H // 2) * W])])
+    ref = O.direct4(f.astype(np.float64), a, idx)
+    assert _nerr(out.ravel()[idx], ref) < TOL
+
+
+def test_filter_fp64_form_runs_and_reports_error():
+    """The all-FP64 form (Algorithm 1 literally in double) on a small image:
+    close to the oracle, but not held to the bar (its cancellation error
+    grows like the fourth power of the buffer size)."""
+    H, W = 64, 64
+    f = synth.image(H, W, seed=2, dtype="u8")
+    p = synth.srt_field(H, W, seed=2, sigma=(2.0, 6.0), rho=(1.0, 3.0))
+    out, st = _run(f, p, "srt", max_scale=6.0, precision="fp64")
+    assert st == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    ref = O.direct4(f.astype(np.float64), a)
+    assert _nerr(out, ref) < 1e-3
+
+
+# ------------------------------------------------------------------ edge cases
+def test_batch_channels_share_params():
+    dev = _cuda()
+    B, C, H, W = 2, 3, 40, 50
+    f = np.stack([np.stack([synth.image(H, W, seed=10 * b + c, dtype="f32") for c in range(C)]) for b in range(B)])
+    p = np.stack([synth.srt_field(H, W, seed=b, sigma=(1.0, 5.0), rho=(1.0, 3.0)) for b in range(B)])
+    out = api.filter(torch.from_numpy(f).to(dev), torch.from_numpy(p).to(dev), kind="srt", max_scale=5.0)
+    for b in range(B):
+        for c in range(C):
+            single = api.filter(torch.from_numpy(f[b, c]).to(dev), torch.from_numpy(p[b]).to(dev), kind="srt",
+                                max_scale=5.0)
+            assert torch.equal(out[b, c], single)
+
+
+def test_tiny_image_large_kernel_zero_boundary():
+    """1x1 and 1xN images with footprints far beyond the image."""
+    for H, W in [(1, 1), (1, 9), (7, 1)]:
+        f = synth.image(H, W, seed=H + W, dtype="u8")
+        a = np.full((4, H, W), 6.5, dtype=np.float32)
+        out, st = _run(f, a, "scales", max_scale=6.5)
+        assert st == 0
+        ref = O.direct4(f.astype(np.float64), a.astype(np.float64))
+        assert _nerr(out, ref) < TOL
+
+
+def test_zp_scales_reproduce_interpolation():
+    """a = b = (1, sqrt2, 1, sqrt2): the filter is the ZP element itself; on a
+    constant image every interior output is the lattice mass = 1."""
+    H, W = 20, 24
+    f = np.full((H, W), 7, dtype=np.uint8)
+    a = np.empty((4, H, W), dtype=np.float32)
+    a[0], a[1], a[2], a[3] = 1.0, np.sqrt(2), 1.0, np.sqrt(2)
+    out, st = _run(f, a, "scales", max_scale=2.0)
+    assert st == 0
+    assert np.abs(out[3:-3, 3:-3] - 7.0).max() < 1e-4
+
+
+def test_constant_image_integer_scales_exact_mass():
+    H, W = 30, 30
+    f = np.full((H, W), 200, dtype=np.uint8)
+    a = np.empty((4, H, W), dtype=np.float32)
+    a[0], a[1], a[2], a[3] = 3.0, 2.3, 2.0, 1.7   # a1, a3 integers: lattice mass exactly 1
+    out, st = _run(f, a, "scales", max_scale=3.0)
+    assert st == 0
+    assert np.abs(out[8:-8, 8:-8] - 200.0).max() < 200.0 * 1e-6
+
+
+def test_invalid_scale_gives_nan_and_status():
+    H, W = 8, 8
+    f = synth.image(H, W, seed=1, dtype="u8")
+    a = np.full((4, H, W), 2.0, dtype=np.float32)
+    a[1, 3, 4] = -1.0
+    a[2, 5, 5] = np.nan
+    out, st = _run(f, a, "scales", halo=8)
+    assert st & (1 << L.BSF_EBADSCALE)
+    assert np.isnan(out[3, 4]) and np.isnan(out[5, 5])
+    assert np.isfinite(np.delete(out.ravel(), [3 * W + 4, 5 * W + 5])).all()
+
+
+def test_halo_too_small_is_reported_not_read():
+    """A halo smaller than the footprint: the kernel's bounds check skips the
+    reads, writes NaN and raises BSF_EHALO."""
+    H, W = 16, 16
+    f = synth.image(H, W, seed=1, dtype="u8")
+    a = np.full((4, H, W), 12.0, dtype=np.float32)
+    out, st = _run(f, a, "scales", halo=3)
+    assert st & (1 << L.BSF_EHALO)
+    assert np.isnan(out).any()
+
+
+def test_strict_mode_reports_clamp():
+    dev = _cuda()
+    H, W = 8, 8
+    f = torch.from_numpy(synth.image(H, W, seed=1, dtype="u8")).to(dev)
+    p = torch.from_numpy(synth.constant_srt(H, W, 2.0, 20.0, np.pi / 8)).to(dev)
+    with pytest.raises(L.BsfError) as e:
+        api.filter(f, p, kind="srt", max_scale=2.0, strict=True)
+    assert e.value.code == L.BSF_EINFEASIBLE
+    api.device_status(dev)
+
+
+def test_unsupported_n_and_bad_args():
+    dev = _cuda()
+    f = torch.zeros((8, 8), dtype=torch.uint8, device=dev)
+    p = torch.ones((3, 8, 8), dtype=torch.float32, device=dev)
+    with pytest.raises(L.BsfError) as e:
+        api.filter(f, p, kind="srt", N=6, halo=8)
+    assert e.value.code == L.BSF_EUNSUPPORTED
+    rc = L.bsf_filter(api.context(dev), 0, L.BSF_U8, 1, 1, 8, 8, 4, p.data_ptr(), L.BSF_PARAM_SRT, None,
+                      p.data_ptr(), 0)
+    assert rc == L.BSF_EINVAL
