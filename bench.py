@@ -122,9 +122,9 @@ def alu_peak_tops():
     return 152 * 128 * 2.070e9 / 1e12
 
 
-def _inputs():
+def _inputs(size=None):
     from paper_1003_2022_gb300 import synth
-    return synth.workload_inputs(WORKLOAD, seed=0)
+    return synth.workload_inputs(WORKLOAD, seed=0, H=size, W=size)
 
 
 def cpu_baseline_run(f, p, crop=192, seed=0):
@@ -189,7 +189,7 @@ def run_ours(args):
     from paper_1003_2022_gb300 import _lib as L
     from paper_1003_2022_gb300 import api
 
-    f_np, p_np = _inputs()
+    f_np, p_np = _inputs(args.size)
     H, W = f_np.shape
     f = torch.from_numpy(f_np).to(dev)
     p = torch.from_numpy(p_np).to(dev)
@@ -288,7 +288,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "int64" if args.precision == "exact" else "f64", "data": "synthetic",
-        "config": {"workload": "2048x2048 u8 image (uniform 0-255), N=4, per-pixel (sigma 1-32 px, rho 1-8 "
+        "config": {"workload": f"{H}x{W} u8 image (uniform 0-255), N=4, per-pixel (sigma 1-32 px, rho 1-8 "
                                "clamped to Prop. 3.1, theta from a smooth vector field), exact int64 path",
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--precision", default="exact", choices=["exact", "fp64"])
     ap.add_argument("--cpu-crop", type=int, default=640)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/bsf.h"
 
@@ -51,22 +52,21 @@ template <> __device__ __forceinline__ u128 load_sample<MODE_U128, float>(float 
 template <> __device__ __forceinline__ double load_sample<MODE_F64, uint8_t>(uint8_t v) { return (double)v; }
 template <> __device__ __forceinline__ double load_sample<MODE_F64, float>(float v) { return (double)v; }
 
-// Warp shuffles of 64/128-bit values, split into 32-bit words.
-template <class T> __device__ __forceinline__ T shfl_up_T(T v, int d) {
-    static_assert(sizeof(T) % 4 == 0, "word size");
-    union { T t; unsigned w[sizeof(T) / 4]; } u;
-    u.t = v;
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) u.w[i] = __shfl_up_sync(0xffffffffu, u.w[i], d);
-    return u.t;
-}
-template <class T> __device__ __forceinline__ T shfl_down_T(T v, int d) {
-    union { T t; unsigned w[sizeof(T) / 4]; } u;
-    u.t = v;
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) u.w[i] = __shfl_down_sync(0xffffffffu, u.w[i], d);
-    return u.t;
-}
+// Warp shuffles of 64/128-bit (and small aggregate) values, split into 32-bit words.
+#define BSF_SHFL_T(NAME, CALL)                                                   \
+    template <class T> __device__ __forceinline__ T NAME(T v, int d) {           \
+        static_assert(sizeof(T) % 4 == 0, "word size");                          \
+        unsigned w[sizeof(T) / 4];                                               \
+        memcpy(w, &v, sizeof(T));                                                \
+        _Pragma("unroll") for (int i = 0; i < (int)(sizeof(T) / 4); ++i) w[i] = CALL; \
+        T r;                                                                     \
+        memcpy(&r, w, sizeof(T));                                                \
+        return r;                                                                \
+    }
+BSF_SHFL_T(shfl_up_T, __shfl_up_sync(0xffffffffu, w[i], d))
+BSF_SHFL_T(shfl_down_T, __shfl_down_sync(0xffffffffu, w[i], d))
+BSF_SHFL_T(shfl_idx_T, __shfl_sync(0xffffffffu, w[i], d))
+#undef BSF_SHFL_T
 
 // Device status word bits (1 << BSF_E*).
 __device__ __forceinline__ void raise_status(unsigned* status, int code) {

@@ -5,19 +5,25 @@
 // c = 24 (C11, C12, C22) (Eq. covariance_ZP), minimising the kurtosis norm
 // ||K||^2 ~ sum p_k^4 + (p1^2 + p3^2)(p2^2 + p4^2) (Eq. opt1, App. E).
 // The solutions of M p = c form a line; here it is parameterised
-// symmetrically by u = p2 + p4:
-//   p1 = (c1 - u)/2, p3 = (c3 - u)/2, p2 = (u + c2)/2, p4 = (u - c2)/2,
-// feasible for |c2| + 2 eps <= u <= min(c1, c3) - 2 eps.  The objective is a
-// quartic in u whose second derivative 4 sum p^2 - 2 (p1+p3)(p2+p4) is
-// positive, so its minimiser on the interval is unique: an end point if the
-// derivative does not change sign there, else the root found by a bracketed
-// Newton iteration.  (The paper pivots p4 = 1 and enumerates the real roots
-// of the cubic derivative; both give the same minimiser.)
+// symmetrically by w = (p2 + p4)/2:
+//   p1 = a - w, p3 = c - w, p2 = w + d, p4 = w - d,   a = c1/2, c = c3/2, d = c2/2.
+// Along the line the objective's derivative is, up to a factor 8, the cubic
+//   g(w) = 8 w^3 - 6 s1 w^2 + (4 s2 + 8 d^2) w - (s3 + s1 d^2),
+//   s1 = a + c, s2 = a^2 + c^2, s3 = a^3 + c^3.
+// With w = z + s1/4 it becomes z^3 + P z + Q = 0,
+//   P = ((5/2)(a^2 + c^2) - 3 a c + 8 d^2) / 8 > 0,
+//   Q = s1 (d^2 - (a - c)^2 / 4) / 8,
+// whose single real root (P > 0) is z = -Q / (A^2 + P/3 + B^2),
+// A = cbrt(|Q|/2 + sqrt(Q^2/4 + P^3/27)), B = P / (3A): Cardano's formula
+// written without cancellation.  The objective is convex, so the constrained
+// minimiser is that root clamped to the feasible interval
+// |d| + eps <= w <= min(a, c) - eps.  (The paper pivots p4 = 1 and enumerates
+// the real roots of its cubic zeta'(t); both give the same minimiser.)
 //
 // Elongations beyond Prop. 3.1's bound U(theta) = (1 + |sin 2t| + |cos 2t|)^2
 // / (2 |sin 2t| |cos 2t|) are lowered to (1 - eta) U keeping the size
 // s = lambda_max + lambda_min and the orientation (flag bit 0).  If p >= eps
-// is still infeasible, u is the interval midpoint and p is raised to eps
+// is still infeasible, w is the interval midpoint and p is raised to eps
 // (flag bit 1).  Non-finite or non-positive-definite input: NaN scales,
 // flag bit 2.
 #pragma once
@@ -29,12 +35,6 @@ struct map4_result {
     int flag;
 };
 
-__device__ __forceinline__ float map4_dzeta(float p1, float p2, float p3, float p4) {
-    const float s13 = p1 + p3, s24 = p2 + p4;
-    const float q13 = p1 * p1 + p3 * p3, q24 = p2 * p2 + p4 * p4;
-    return 2.f * (p2 * p2 * p2 + p4 * p4 * p4 - p1 * p1 * p1 - p3 * p3 * p3) + q13 * s24 - s13 * q24;
-}
-
 // kind: BSF_PARAM_COV (v0,v1,v2) = (C11, C12, C22) or BSF_PARAM_SRT (sigma, rho, theta)
 __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, float v2, float eps, float eta) {
     map4_result R;
@@ -42,7 +42,7 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
     float lmax, lmin, th;
     if (kind == BSF_PARAM_SRT) {
         lmax = v0 * v0;
-        lmin = lmax / v1;
+        lmin = __fdividef(lmax, v1);
         th = v2;
     } else {
         const float tr = v0 + v2;
@@ -57,18 +57,26 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
         R.flag = 4;
         return R;
     }
+    // sin, cos of 2 theta via the hardware approximation on [-pi, pi)
+    // (absolute error ~2^-21): theta is taken modulo pi first
     float s2, c2;
-    sincosf(2.f * th, &s2, &c2);
+    {
+        float t2 = 2.f * th;
+        t2 -= 6.28318530717958648f * floorf(t2 * 0.159154943091895336f);  // [0, 2 pi)
+        __sincosf(t2 - 3.14159265358979324f, &s2, &c2);                    // shifted by pi
+        s2 = -s2;
+        c2 = -c2;
+    }
     const float as = fabsf(s2), ac = fabsf(c2);
     const float rho = lmax / lmin;
     bool clamp = false;
     if (as * ac > 1e-12f) {
-        const float U = (1.f + as + ac) * (1.f + as + ac) / (2.f * as * ac);
+        const float U = __fdividef((1.f + as + ac) * (1.f + as + ac), 2.f * as * ac);
         const float rc = (1.f - eta) * U;
         if (rho > rc) {
             const float s = lmax + lmin;
-            lmax = s * rc / (1.f + rc);
-            lmin = s / (1.f + rc);
+            lmin = __fdividef(s, 1.f + rc);
+            lmax = s - lmin;
             clamp = true;
             R.flag |= 1;
         }
@@ -85,63 +93,47 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
         c2v = 24.f * (d * s2);
         c3 = 24.f * (m - d * c2);
     }
-    const float ac2 = fabsf(c2v);
-    const float lo = ac2 + 2.f * eps;
-    const float cmin = fminf(c1, c3);
-    const float hi = cmin - 2.f * eps;
+    const float ha = 0.5f * c1, hc = 0.5f * c3, hd = 0.5f * c2v, ahd = fabsf(hd);
+    const float lo = ahd + eps;
+    const float cmin = fminf(ha, hc);
+    const float hi = cmin - eps;
     float p1, p2, p3, p4;
     if (!(lo <= hi)) {
-        const float u = 0.5f * (lo + hi);
-        p1 = fmaxf(0.5f * (c1 - u), eps);
-        p3 = fmaxf(0.5f * (c3 - u), eps);
-        p2 = fmaxf(0.5f * (u + c2v), eps);
-        p4 = fmaxf(0.5f * (u - c2v), eps);
+        const float w = 0.5f * (lo + hi);
+        p1 = fmaxf(ha - w, eps);
+        p3 = fmaxf(hc - w, eps);
+        p2 = fmaxf(w + hd, eps);
+        p4 = fmaxf(w - hd, eps);
         R.flag |= 2;
     } else {
-        // the four components as functions of u, written from the nearer end of
-        // the interval to keep small components accurate
-        auto comps = [&](float u, float& q1, float& q2, float& q3, float& q4) {
-            if (u - lo <= hi - u) {
-                const float v = u - lo;  // >= 0
-                q2 = 0.5f * (ac2 + c2v) + eps + 0.5f * v;
-                q4 = 0.5f * (ac2 - c2v) + eps + 0.5f * v;
-                q1 = 0.5f * (c1 - u);
-                q3 = 0.5f * (c3 - u);
-            } else {
-                const float w = hi - u;  // >= 0
-                q1 = 0.5f * (c1 - cmin) + eps + 0.5f * w;
-                q3 = 0.5f * (c3 - cmin) + eps + 0.5f * w;
-                q2 = 0.5f * (u + c2v);
-                q4 = 0.5f * (u - c2v);
-            }
-        };
-        float u;
-        comps(lo, p1, p2, p3, p4);
-        const float dlo = map4_dzeta(p1, p2, p3, p4);
-        float q1, q2, q3, q4;
-        comps(hi, q1, q2, q3, q4);
-        const float dhi = map4_dzeta(q1, q2, q3, q4);
-        if (dlo >= 0.f) {
-            u = lo;
-        } else if (dhi <= 0.f) {
-            u = hi;
-            p1 = q1; p2 = q2; p3 = q3; p4 = q4;
+        // normalised cubic (scale-free, avoids FP32 overflow of P^3)
+        const float sc = ha + hc + ahd;
+        const float isc = __frcp_rn(sc);
+        const float an = ha * isc, cn = hc * isc, dn = hd * isc;
+        const float P = (2.5f * (an * an + cn * cn) - 3.f * an * cn + 8.f * dn * dn) * 0.125f;
+        const float amc = an - cn;
+        const float Q = (an + cn) * (dn * dn - 0.25f * amc * amc) * 0.125f;
+        const float rr = sqrtf(0.25f * Q * Q + P * P * P * (1.f / 27.f));
+        const float A = cbrtf(0.5f * fabsf(Q) + rr);
+        const float B = __fdividef(P, 3.f * A);
+        float z = -__fdividef(Q, A * A + P * (1.f / 3.f) + B * B);
+        z -= __fdividef(z * z * z + P * z + Q, 3.f * z * z + P);  // one Newton step against rounding
+        float w = sc * (z + 0.25f * (an + cn));
+        w = fminf(fmaxf(w, lo), hi);
+        // each component from the nearer end of the interval, so that small
+        // components keep their relative accuracy
+        if (w - lo <= hi - w) {
+            const float v = w - lo;
+            p2 = (ahd + hd) + eps + v;
+            p4 = (ahd - hd) + eps + v;
+            p1 = ha - w;
+            p3 = hc - w;
         } else {
-            float a = lo, b = hi;
-            u = 0.5f * (lo + hi);
-#pragma unroll 1
-            for (int it = 0; it < 40; ++it) {
-                comps(u, p1, p2, p3, p4);
-                const float g = map4_dzeta(p1, p2, p3, p4);
-                if (g > 0.f) b = u; else a = u;
-                const float s13 = p1 + p3, s24 = p2 + p4;
-                const float h2 = 4.f * (p1 * p1 + p2 * p2 + p3 * p3 + p4 * p4) - 2.f * s13 * s24;
-                float un = u - g / h2;
-                if (!(un > a && un < b)) un = 0.5f * (a + b);
-                if (un == u || b - a <= 0.f) break;
-                u = un;
-            }
-            comps(u, p1, p2, p3, p4);
+            const float v = hi - w;
+            p1 = (ha - cmin) + eps + v;
+            p3 = (hc - cmin) + eps + v;
+            p2 = w + hd;
+            p4 = w - hd;
         }
     }
     R.a[0] = sqrtf(fmaxf(p1, 0.f));

@@ -40,10 +40,16 @@ template <class T> __device__ __forceinline__ T warp_incl_scan(T v, int lane) {
     return v;
 }
 
-template <int MODE> struct band_bounds { static constexpr int MAXT = (MODE == MODE_U128) ? 512 : 1024; };
+// Threads per band CTA for each (form, columns per thread): the register
+// state grows with both, so wider rows trade threads for registers.
+__host__ __device__ constexpr int band_maxt(bool wide, int cpt) {
+    return wide ? (cpt <= 1 ? 1024 : cpt == 2 ? 768 : cpt == 4 ? 512 : 384)
+                : (cpt <= 2 ? 1024 : cpt == 4 ? 768 : 512);
+}
+template <int MODE, int CPT> struct band_bounds { static constexpr int MAXT = band_maxt(MODE == MODE_U128, CPT); };
 
 template <int MODE, class InT, int CPT>
-__global__ void __launch_bounds__(band_bounds<MODE>::MAXT) k_band(const InT* __restrict__ img, long long img_stride, int H, int W,
+__global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT* __restrict__ img, long long img_stride, int H, int W,
                                                int P, int Hp, int Wp, int pitch, int band_h, int nb,
                                                const typename mode_traits<MODE>::T* __restrict__ carry,
                                                typename mode_traits<MODE>::T* __restrict__ local,
@@ -53,8 +59,7 @@ __global__ void __launch_bounds__(band_bounds<MODE>::MAXT) k_band(const InT* __r
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int c0 = tid * CPT;
     const int y0 = b * band_h, y1 = min(Hp, y0 + band_h);
-    __shared__ T s_tot[32];
-    __shared__ T s_off[32];
+    __shared__ T s_tot[2][32];
     __shared__ T s_eg1[2][32];
     __shared__ T s_eG[2][32];
     // the vertical sum g2 is column-local: it lives in shared memory, one
@@ -78,8 +83,8 @@ __global__ void __launch_bounds__(band_bounds<MODE>::MAXT) k_band(const InT* __r
     }
 
     const InT* f = img + (size_t)im * img_stride;
-    // prefetch of the next row's samples
-    InT nxt[CPT];
+    // samples of the next D rows are kept in flight in a register ring
+    constexpr int D = 4;
     auto fetch = [&](int y, InT* dst) {
         const int iy = y - P;
 #pragma unroll
@@ -88,56 +93,62 @@ __global__ void __launch_bounds__(band_bounds<MODE>::MAXT) k_band(const InT* __r
             dst[j] = (y < y1 && iy >= 0 && iy < H && ic >= 0 && ic < W) ? f[(size_t)iy * W + ic] : InT(0);
         }
     };
-    fetch(y0, nxt);
-    for (int y = y0; y < y1; ++y) {
-        T v[CPT];
+    InT pre[D][CPT];
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) v[j] = load_sample<MODE, InT>(nxt[j]);
-        fetch(y + 1, nxt);
+    for (int k = 0; k < D; ++k) fetch(y0 + k, pre[k]);
+    for (int yb = y0; yb < y1; yb += D) {
 #pragma unroll
-        for (int j = 1; j < CPT; ++j) v[j] += v[j - 1];
-        const T tot = v[CPT - 1];
-        const T inc = warp_incl_scan(tot, lane);
-        const int par = y & 1;
-        if (lane == 31) {
-            s_tot[warp] = inc;
-            s_eg1[par][warp] = g1[CPT - 1];
-        }
-        if (lane == 0) s_eG[par][warp] = gG[0];
-        const T g1_from_left = shfl_up_T(g1[CPT - 1], 1);
-        const T gG_from_right = shfl_down_T(gG[0], 1);
-        __syncthreads();
-        if (warp == 0) {
-            const T t = lane < nw ? s_tot[lane] : T(0);
-            const T ti = warp_incl_scan(t, lane);
-            s_off[lane] = ti - t;
-        }
-        __syncthreads();
-        const T off = s_off[warp] + (inc - tot);
-        const T left = lane > 0 ? g1_from_left : (warp > 0 ? s_eg1[par][warp - 1] : T(0));
-        const T right = lane < 31 ? gG_from_right : (warp + 1 < nw ? s_eG[par][warp + 1] : T(0));
-        T ng1[CPT];
+        for (int k = 0; k < D; ++k) {
+            const int y = yb + k;
+            if (y >= y1) break;  // uniform over the CTA
+            T v[CPT];
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) ng1[j] = (v[j] + off) + (j == 0 ? left : g1[j - 1]);
+            for (int j = 0; j < CPT; ++j) v[j] = load_sample<MODE, InT>(pre[k][j]);
+            fetch(y + D, pre[k]);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) g2[j] += ng1[j];
-        T ngG[CPT];
+            for (int j = 1; j < CPT; ++j) v[j] += v[j - 1];
+            const T tot = v[CPT - 1];
+            const T inc = warp_incl_scan(tot, lane);
+            const int par = y & 1;
+            if (lane == 31) {
+                s_tot[par][warp] = inc;
+                s_eg1[par][warp] = g1[CPT - 1];
+            }
+            if (lane == 0) s_eG[par][warp] = gG[0];
+            const T g1_from_left = shfl_up_T(g1[CPT - 1], 1);
+            const T gG_from_right = shfl_down_T(gG[0], 1);
+            // one barrier per row: every warp sums the totals of the warps before it
+            // (buffers alternate by row parity, so the next row cannot overwrite them early)
+            __syncthreads();
+            T before = lane < warp ? s_tot[par][lane] : T(0);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            T nb_ = (j + 1 < CPT) ? gG[j + 1] : right;
-            if (c0 + j + 1 >= Wp) nb_ = T(0);
-            ngG[j] = g2[j] + nb_;
-        }
+            for (int d = 16; d > 0; d >>= 1) before += shfl_down_T(before, d);
+            const T off = shfl_idx_T(before, 0) + (inc - tot);
+            const T left = lane > 0 ? g1_from_left : (warp > 0 ? s_eg1[par][warp - 1] : T(0));
+            const T right = lane < 31 ? gG_from_right : (warp + 1 < nw ? s_eG[par][warp + 1] : T(0));
+            T ng1[CPT];
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            g1[j] = ng1[j];
-            gG[j] = ngG[j];
-        }
-        if (G != nullptr) {
-            T* row = G + (size_t)im * G_stride + (size_t)y * pitch;
+            for (int j = 0; j < CPT; ++j) ng1[j] = (v[j] + off) + (j == 0 ? left : g1[j - 1]);
 #pragma unroll
-            for (int j = 0; j < CPT; ++j)
-                if (c0 + j < Wp) row[c0 + j] = gG[j];
+            for (int j = 0; j < CPT; ++j) g2[j] += ng1[j];
+            T ngG[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                T nb_ = (j + 1 < CPT) ? gG[j + 1] : right;
+                if (c0 + j + 1 >= Wp) nb_ = T(0);
+                ngG[j] = g2[j] + nb_;
+            }
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                g1[j] = ng1[j];
+                gG[j] = ngG[j];
+            }
+            if (G != nullptr) {
+                T* row = G + (size_t)im * G_stride + (size_t)y * pitch;
+#pragma unroll
+                for (int j = 0; j < CPT; ++j)
+                    if (c0 + j < Wp) row[c0 + j] = gG[j];
+            }
         }
     }
     if (local != nullptr) {
@@ -156,133 +167,183 @@ __global__ void __launch_bounds__(band_bounds<MODE>::MAXT) k_band(const InT* __r
 
 __device__ __forceinline__ int band_last_row(int b, int band_h, int Hp) { return min((b + 1) * band_h, Hp) - 1; }
 
-// Phase 2a: S1_b[x] = L1_b[x] + S1_{b-1}[x - h_b]  (diagonal lines)
-template <class T>
-__global__ void k_carry_s1(const T* __restrict__ L, T* __restrict__ S, int Hp, int Wp, int band_h, int nb) {
-    const int im = blockIdx.y;
-    const int Ylast = Hp - 1, Y0 = band_last_row(0, band_h, Hp);
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    if (X >= Wp + (Ylast - Y0)) return;
-    T run = T(0);
-    for (int b = 0; b < nb; ++b) {
-        const int x = X - (Ylast - band_last_row(b, band_h, Hp));
-        if (x >= Wp) break;
-        if (x < 0) continue;
-        const size_t base = ((size_t)im * nb + b) * 3 * (size_t)Wp;
-        const T val = L[base + x] + run;
-        S[base + x] = val;
-        run = val;
-    }
-}
-
 template <class T> __device__ __forceinline__ T at0(const T* a, int i) { return i >= 0 ? a[i] : T(0); }
 
-// Phase 2c: S2_b[x] = L2_b[x] + S2_{b-1}[x] + sum_{j=1..h_b} S1_{b-1}[x-j]  (columns)
-template <class T>
-__global__ void k_carry_s2(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1, int Hp, int Wp,
-                           int band_h, int nb) {
-    const int im = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= Wp) return;
-    T run = T(0);
-    for (int b = 0; b < nb; ++b) {
-        const size_t base = ((size_t)im * nb + b) * 3 * (size_t)Wp;
-        T val = L[base + Wp + x] + run;
-        if (b > 0) {
-            const int h = band_last_row(b, band_h, Hp) - band_last_row(b - 1, band_h, Hp);
-            const T* p1 = P1 + ((size_t)im * nb + (b - 1)) * (size_t)Wp;
-            val += at0(p1, x - 1) - at0(p1, x - h - 1);
-        }
-        S[base + Wp + x] = val;
-        run = val;
+// Phase 2 line scans.  Along every line of a family, the true band-end
+// states obey S_b = v_b + S_{b-1} over the contiguous range of bands where
+// the line lies inside the buffer, with v_b the band's local state plus the
+// closed-form response to the previous band's lower-order states.  One warp
+// owns one line; its lanes take 32 consecutive bands at a time and a warp
+// prefix scan carries the running sum across the chunk.
+template <class T, class GetV, class Put>
+__device__ __forceinline__ void warp_band_scan(int b_lo, int b_hi, GetV getv, Put put) {
+    const int lane = threadIdx.x & 31;
+    T carry = T(0);
+    for (int base = b_lo; base <= b_hi; base += 32) {
+        const int b = base + lane;
+        const bool ok = b <= b_hi;
+        const T v = ok ? getv(b) : T(0);
+        const T inc = warp_incl_scan(v, lane);
+        if (ok) put(b, carry + inc);
+        carry += shfl_idx_T(inc, 31);
     }
 }
 
-// Phase 2e: SG_b[x] = LG_b[x] + [x+h <= Wp-1] SG_{b-1}[x+h]
-//          + sum_{j=j0..h} ( S2_{b-1}[x+h-j] + sum_{k=1..j} S1_{b-1}[x+h-j-k] ),
-//   j0 = max(1, x+h-Wp+1)  (RS4 truncated at the right buffer edge)   (anti-diagonal lines)
+// Phase 2a: diagonal lines, x_b = X - (Ylast - Y_b):  S1_b[x_b] = L1_b[x_b] + S1_{b-1}[x_{b-1}]
 template <class T>
-__global__ void k_carry_sg(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1,
-                           const T* __restrict__ PP1, const T* __restrict__ Q1, const T* __restrict__ P2, int Hp,
-                           int Wp, int band_h, int nb) {
+__global__ void k_scan_s1(const T* __restrict__ L, T* __restrict__ S, int Hp, int Wp, int band_h, int nb) {
     const int im = blockIdx.y;
     const int Ylast = Hp - 1, Y0 = band_last_row(0, band_h, Hp);
-    const int X = (int)(blockIdx.x * blockDim.x + threadIdx.x) - (Ylast - Y0);
-    if (X >= Wp) return;
-    T run = T(0);
-    for (int b = 0; b < nb; ++b) {
-        const int x = X + (Ylast - band_last_row(b, band_h, Hp));
-        if (x < 0) break;
-        if (x >= Wp) {
-            run = T(0);
-            continue;
-        }
-        const size_t base = ((size_t)im * nb + b) * 3 * (size_t)Wp;
-        T val = L[base + 2 * Wp + x];
-        if (b > 0) {
-            const int h = band_last_row(b, band_h, Hp) - band_last_row(b - 1, band_h, Hp);
-            const size_t pb = ((size_t)im * nb + (b - 1)) * (size_t)Wp;
-            const int j0 = max(1, x + h - Wp + 1);
-            if (x + h <= Wp - 1) val += run;
-            val += at0(P2 + pb, x + h - j0) - at0(P2 + pb, x - 1);
-            val += at0(PP1 + pb, x + h - 1 - j0) - at0(PP1 + pb, x - 2);
-            val -= at0(Q1 + pb, x + h - 1 - 2 * j0) - at0(Q1 + pb, x - h - 3);
-        }
-        S[base + 2 * Wp + x] = val;
-        run = val;
-    }
+    const int X = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (X >= Wp + (Ylast - Y0)) return;
+    // valid bands: 0 <= X - (Ylast - Y_b) < Wp, x increasing in b
+    int b_lo = max(0, (Ylast - X + 1) / band_h - 1), b_hi = min(nb - 1, (Ylast - X + Wp) / band_h + 1);
+    while (b_lo < nb && X - (Ylast - band_last_row(b_lo, band_h, Hp)) < 0) ++b_lo;
+    while (b_hi >= b_lo && X - (Ylast - band_last_row(b_hi, band_h, Hp)) >= Wp) --b_hi;
+    warp_band_scan<T>(b_lo, b_hi,
+        [&](int b) {
+            const int x = X - (Ylast - band_last_row(b, band_h, Hp));
+            return L[((size_t)im * nb + b) * 3 * (size_t)Wp + x];
+        },
+        [&](int b, T v) {
+            const int x = X - (Ylast - band_last_row(b, band_h, Hp));
+            S[((size_t)im * nb + b) * 3 * (size_t)Wp + x] = v;
+        });
 }
 
-// Inclusive prefix of get(i), i < n, along one row, by one CTA.
-template <class T, class Get, class Put>
-__device__ void block_row_scan(int n, Get get, Put put, T* smem /* 33 */) {
+// Phase 2c: columns:  S2_b[x] = L2_b[x] + sum_{j=1..h_b} S1_{b-1}[x-j] + S2_{b-1}[x]
+template <class T>
+__global__ void k_scan_s2(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1, int Hp, int Wp,
+                          int band_h, int nb) {
+    const int im = blockIdx.y;
+    const int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (x >= Wp) return;
+    warp_band_scan<T>(0, nb - 1,
+        [&](int b) {
+            T v = L[((size_t)im * nb + b) * 3 * (size_t)Wp + Wp + x];
+            if (b > 0) {
+                const int h = band_last_row(b, band_h, Hp) - band_last_row(b - 1, band_h, Hp);
+                const T* p1 = P1 + ((size_t)im * nb + (b - 1)) * (size_t)Wp;
+                v += at0(p1, x - 1) - at0(p1, x - h - 1);
+            }
+            return v;
+        },
+        [&](int b, T v) { S[((size_t)im * nb + b) * 3 * (size_t)Wp + Wp + x] = v; });
+}
+
+// Phase 2e: anti-diagonal lines, x_b = X + (Ylast - Y_b):
+//   SG_b[x] = LG_b[x] + [x+h <= Wp-1] SG_{b-1}[x+h]
+//           + sum_{j=j0..h} ( S2_{b-1}[x+h-j] + sum_{k=1..j} S1_{b-1}[x+h-j-k] ),
+//   j0 = max(1, x+h-Wp+1)  (RS4 stops at the right buffer edge)
+template <class T>
+__global__ void k_scan_sg(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1,
+                          const T* __restrict__ PP1, const T* __restrict__ Q1, const T* __restrict__ P2, int Hp,
+                          int Wp, int band_h, int nb) {
+    const int im = blockIdx.y;
+    const int Ylast = Hp - 1, Y0 = band_last_row(0, band_h, Hp);
+    const int X = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) - (Ylast - Y0);
+    if (X >= Wp) return;
+    // valid bands: 0 <= X + (Ylast - Y_b) < Wp, x decreasing in b
+    int b_lo = max(0, (X + Ylast - Wp + 1) / band_h - 1), b_hi = min(nb - 1, (X + Ylast) / band_h + 1);
+    while (b_lo < nb && X + (Ylast - band_last_row(b_lo, band_h, Hp)) >= Wp) ++b_lo;
+    while (b_hi >= b_lo && X + (Ylast - band_last_row(b_hi, band_h, Hp)) < 0) --b_hi;
+    warp_band_scan<T>(b_lo, b_hi,
+        [&](int b) {
+            const int x = X + (Ylast - band_last_row(b, band_h, Hp));
+            T v = L[((size_t)im * nb + b) * 3 * (size_t)Wp + 2 * Wp + x];
+            if (b > 0) {
+                const int h = band_last_row(b, band_h, Hp) - band_last_row(b - 1, band_h, Hp);
+                const size_t pb = ((size_t)im * nb + (b - 1)) * (size_t)Wp;
+                const int j0 = max(1, x + h - Wp + 1);
+                v += at0(P2 + pb, x + h - j0) - at0(P2 + pb, x - 1);
+                v += at0(PP1 + pb, x + h - 1 - j0) - at0(PP1 + pb, x - 2);
+                v -= at0(Q1 + pb, x + h - 1 - 2 * j0) - at0(Q1 + pb, x - h - 3);
+            }
+            return v;
+        },
+        [&](int b, T v) {
+            const int x = X + (Ylast - band_last_row(b, band_h, Hp));
+            S[((size_t)im * nb + b) * 3 * (size_t)Wp + 2 * Wp + x] = v;
+        });
+}
+
+template <class T> struct V3 {
+    T a, b, c;
+    __device__ __forceinline__ V3 operator+(const V3& o) const { return V3{a + o.a, b + o.b, c + o.c}; }
+    __device__ __forceinline__ V3 operator-(const V3& o) const { return V3{a - o.a, b - o.b, c - o.c}; }
+    __device__ __forceinline__ V3& operator+=(const V3& o) { a += o.a; b += o.b; c += o.c; return *this; }
+    __device__ explicit V3(T z = T(0)) : a(z), b(z), c(z) {}
+    __device__ V3(T x, T y, T w) : a(x), b(y), c(w) {}
+};
+
+// Inclusive prefix along one row of n <= blockDim * ITEMS elements by one
+// CTA: each thread scans ITEMS consecutive elements, then a block scan of
+// the thread totals.
+template <class T, int ITEMS, class Get, class Put>
+__device__ void block_row_scan(int n, Get get, Put put, T* smem /* 32 */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T carry = T(0);
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const T v = i < n ? get(i) : T(0);
-        const T inc = warp_incl_scan(v, lane);
-        if (lane == 31) smem[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const T t = lane < nw ? smem[lane] : T(0);
-            const T ti = warp_incl_scan(t, lane);
-            if (lane == nw - 1) smem[32] = ti;
-            smem[lane] = ti - t;
-        }
-        __syncthreads();
-        const T res = carry + smem[warp] + inc;
-        if (i < n) put(i, res);
-        carry += smem[32];
-        __syncthreads();
+    const int i0 = threadIdx.x * ITEMS;
+    T v[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) v[j] = (i0 + j < n) ? get(i0 + j) : T(0);
+#pragma unroll
+    for (int j = 1; j < ITEMS; ++j) v[j] += v[j - 1];
+    const T tot = v[ITEMS - 1];
+    const T inc = warp_incl_scan(tot, lane);
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const T t = lane < nw ? smem[lane] : T(0);
+        const T ti = warp_incl_scan(t, lane);
+        smem[lane] = ti - t;
     }
+    __syncthreads();
+    const T off = smem[warp] + (inc - tot);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+        if (i0 + j < n) put(i0 + j, v[j] + off);
+    __syncthreads();
 }
 
 // Phase 2b: P1 = prefix(S1), PP1 = prefix(P1), Q1[x] = P1[x] + Q1[x-2]
-template <class T>
+template <class T, int ITEMS>
 __global__ void k_prefix1(const T* __restrict__ S, T* __restrict__ P1, T* __restrict__ PP1, T* __restrict__ Q1,
                           int Wp, int nb) {
-    __shared__ T sm[33];
+    __shared__ T sm[32];
     const int b = blockIdx.x, im = blockIdx.y;
     const T* s1 = S + ((size_t)im * nb + b) * 3 * (size_t)Wp;
     const size_t pb = ((size_t)im * nb + b) * (size_t)Wp;
     T* p1 = P1 + pb;
     T* pp1 = PP1 + pb;
     T* q1 = Q1 + pb;
-    block_row_scan<T>(Wp, [&](int i) { return s1[i]; }, [&](int i, T v) { p1[i] = v; }, sm);
-    __syncthreads();
-    block_row_scan<T>(Wp, [&](int i) { return p1[i]; }, [&](int i, T v) { pp1[i] = v; }, sm);
-    block_row_scan<T>((Wp + 1) / 2, [&](int i) { return p1[2 * i]; }, [&](int i, T v) { q1[2 * i] = v; }, sm);
-    block_row_scan<T>(Wp / 2, [&](int i) { return p1[2 * i + 1]; }, [&](int i, T v) { q1[2 * i + 1] = v; }, sm);
+    block_row_scan<T, ITEMS>(Wp, [&](int i) { return s1[i]; }, [&](int i, T v) { p1[i] = v; }, sm);
+    // over pairs i: (P1[2i], P1[2i+1], P1[2i] + P1[2i+1]) -> Q1[2i], Q1[2i+1], PP1[2i+1];
+    // PP1[2i] = PP1[2i+1] - P1[2i+1]
+    __shared__ V3<T> sm3[32];
+    block_row_scan<V3<T>, ITEMS / 2>((Wp + 1) / 2,
+        [&](int i) {
+            const T e = p1[2 * i], o = (2 * i + 1 < Wp) ? p1[2 * i + 1] : T(0);
+            return V3<T>{e, o, e + o};
+        },
+        [&](int i, V3<T> v) {
+            q1[2 * i] = v.a;
+            const T o = (2 * i + 1 < Wp) ? p1[2 * i + 1] : T(0);
+            pp1[2 * i] = v.c - o;
+            if (2 * i + 1 < Wp) {
+                q1[2 * i + 1] = v.b;
+                pp1[2 * i + 1] = v.c;
+            }
+        },
+        sm3);
 }
 
 // Phase 2d: P2 = prefix(S2)
-template <class T> __global__ void k_prefix2(const T* __restrict__ S, T* __restrict__ P2, int Wp, int nb) {
-    __shared__ T sm[33];
+template <class T, int ITEMS> __global__ void k_prefix2(const T* __restrict__ S, T* __restrict__ P2, int Wp, int nb) {
+    __shared__ T sm[32];
     const int b = blockIdx.x, im = blockIdx.y;
     const T* s2 = S + ((size_t)im * nb + b) * 3 * (size_t)Wp + Wp;
     T* p2 = P2 + ((size_t)im * nb + b) * (size_t)Wp;
-    block_row_scan<T>(Wp, [&](int i) { return s2[i]; }, [&](int i, T v) { p2[i] = v; }, sm);
+    block_row_scan<T, ITEMS>(Wp, [&](int i) { return s2[i]; }, [&](int i, T v) { p2[i] = v; }, sm);
 }
 
 }  // namespace
@@ -290,19 +351,19 @@ template <class T> __global__ void k_prefix2(const T* __restrict__ S, T* __restr
 // ---------------------------------------------------------------- host side
 scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes) {
     scan_plan p;
-    // bands: about two CTAs per SM of a 152-SM part over the whole batch
-    int bh = (int)((long long)Hp * nimg / 304);
+    // bands: one wave of band CTAs (one per SM of a 152-SM part) over the whole batch
+    int bh = (int)(((long long)Hp * nimg + 151) / 152);
     if (bh < 8) bh = 8;
     if (bh > 64) bh = 64;
     if (bh > Hp) bh = Hp;
     p.band_h = bh;
     p.nb = (Hp + bh - 1) / bh;
-    const int maxt = elem_bytes > 8 ? 512 : 1024;
+    const bool wide = elem_bytes > 8;
     p.cpt = 1;
-    while (p.cpt < 8 && (Wp + p.cpt - 1) / p.cpt > maxt) p.cpt *= 2;
+    while (p.cpt < 8 && ((Wp + p.cpt - 1) / p.cpt + 31) / 32 * 32 > band_maxt(wide, p.cpt)) p.cpt *= 2;
     p.threads = ((Wp + p.cpt - 1) / p.cpt + 31) / 32 * 32;
     p.smem = (size_t)p.threads * p.cpt * elem_bytes;
-    p.ok = p.threads <= maxt;
+    p.ok = p.threads <= band_maxt(wide, p.cpt);
     const size_t row = (size_t)nimg * p.nb * Wp * elem_bytes;
     p.work_bytes = row * 10;  // L (3), S (3), P1, PP1, Q1, P2
     return p;
@@ -350,19 +411,14 @@ cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, 
     T* Q1 = PP1 + row;
     T* P2 = Q1 + row;
     launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, P, Hp, Wp, pitch, nullptr, L, nullptr, 0, st);
-    {
-        const int n = Wp + (Hp - 1 - min(p.band_h, Hp) + 1);
-        dim3 g((n + 255) / 256, nimg);
-        k_carry_s1<T><<<g, 256, 0, st>>>(L, S, Hp, Wp, p.band_h, p.nb);
-    }
-    k_prefix1<T><<<dim3(p.nb, nimg), 256, 0, st>>>(S, P1, PP1, Q1, Wp, p.nb);
-    k_carry_s2<T><<<dim3((Wp + 255) / 256, nimg), 256, 0, st>>>(L, S, P1, Hp, Wp, p.band_h, p.nb);
-    k_prefix2<T><<<dim3(p.nb, nimg), 256, 0, st>>>(S, P2, Wp, p.nb);
-    {
-        const int n = Wp + (Hp - 1 - min(p.band_h, Hp) + 1);
-        dim3 g((n + 255) / 256, nimg);
-        k_carry_sg<T><<<g, 256, 0, st>>>(L, S, P1, PP1, Q1, P2, Hp, Wp, p.band_h, p.nb);
-    }
+    const int nlines = Wp + (Hp - min(p.band_h, Hp));  // diagonal / anti-diagonal lines crossing the band ends
+    const int wpb = 8;                                 // warps (lines) per 256-thread block
+    k_scan_s1<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, Hp, Wp, p.band_h, p.nb);
+    const int pthreads = min(1024, ((Wp + 7) / 8 + 31) / 32 * 32);
+    k_prefix1<T, 8><<<dim3(p.nb, nimg), pthreads, 0, st>>>(S, P1, PP1, Q1, Wp, p.nb);
+    k_scan_s2<T><<<dim3((Wp + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, Hp, Wp, p.band_h, p.nb);
+    k_prefix2<T, 8><<<dim3(p.nb, nimg), pthreads, 0, st>>>(S, P2, Wp, p.nb);
+    k_scan_sg<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, PP1, Q1, P2, Hp, Wp, p.band_h, p.nb);
     launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, P, Hp, Wp, pitch, S, nullptr, G, G_stride, st);
     return cudaGetLastError();
 }

@@ -8,20 +8,26 @@
 // a'_k = a_k / sqrt2, tau = ((a1 + a2' - a4' - 1)/2, (a2' + a3 + a4' - 3)/2).
 // So fbar = (1/(a1 a2' a3 a4')) sum_i s_i sum_m G[m] beta_b(y_i - m).
 //
-// ZP interpolation.  With m0 = round(y) and phi = y - m0 in [-1/2, 1/2)^2,
-// the cell around m0 is cut by its two diagonals into four triangles; the
-// element is D4-symmetric, so each triangle is rotated onto the canonical one
-// (phi_x >= |phi_y|), where exactly seven lattice points carry weight and
-// each weight is one quadratic in phi.  Collecting those quadratics by
-// monomial gives (derived from the box-spline definition, Eq. const at
-// a = b = (1, sqrt2, 1, sqrt2)):
-//   8 F = K1 + Kx x + Ky y + Kxx x^2 + Kxy x y + Kyy y^2
-//   K1  = 4 g00 + gW + gE + gS + gN,   Kx = 4 (gE - gW),  Ky = 4 (gN - gS),
-//   Kxx = 4 (gW - g00) - 2 (gS + gN) + 2 (gSE + gNE),
-//   Kxy = 4 (gS - gN - gSE + gNE),
-//   Kyy = -4 (g00 + gE) + 2 (gS + gN) + 2 (gSE + gNE),
-// where gW/gE/gS/gN/gSE/gNE are G at m0 + (-1,0)/(1,0)/(0,-1)/(0,1)/(1,-1)/(1,1)
-// in the rotated frame.
+// ZP interpolation.  Let m0 = round(y) and phi = y - m0 in [-1/2, 1/2)^2.
+// On the cell around m0, F is a C1 piecewise quadratic whose only breaks are
+// the cell's two diagonals (the ZP element is Eq. const at a = b =
+// (1, sqrt2, 1, sqrt2); its knot lines are x, y in 1/2 + Z and x +- y in Z).
+// Such a function is one quadratic plus a multiple of each truncated power
+// across the diagonals.  With the 3x3 neighbourhood of m0 named
+//     a b c        (row above)
+//     d e f        (row of m0)
+//     g h i        (row below)
+// and x' = phi_x + 1/2, y' = phi_y + 1/2 in [0, 1) (origin at the cell's
+// upper-left corner), the derivation from the element's polynomial pieces
+// gives
+//   16 F = 4 s + 8 (cx x' + cy y') + 16 (cxx x'^2 + 2 m x'y' + cyy y'^2)
+//          + 16 A ((x' - y')_+)^2 + 16 B ((x' + y' - 1)_+)^2,
+//   s = a + b + d + e,  u1 = d - f,  u2 = h - b,  m = (a - g) + u2,
+//   cxx = (a + g) - (b + h) + 2 (f - e),   cyy = (a + g) + (b + h) - 2 (d + e),
+//   cx = -2 u1 - cxx - m,   cy = 2 u2 - cyy - m,
+//   A = u1 + u2 + (c - g),  B = u1 - u2 + (i - a).
+// The nine loads have fixed offsets from m0, so the 32 lanes of a warp
+// (consecutive pixels, neighbouring taps) read consecutive addresses.
 //
 // Exact integer form (MODE_U64 / MODE_U128).  a'_k is rounded to A_k 2^-q
 // with a per-pixel q; then every tap position lies on the 2^-(q+1) grid, the
@@ -48,7 +54,7 @@ __device__ __forceinline__ int ilog2_ceil(float v) {
     return (m == 0.5f) ? e - 1 : e;
 }
 
-template <class T> __device__ __forceinline__ T mul_s32(T v, int s) { return v * (T)(long long)s; }
+template <class T> __device__ __forceinline__ T mul_u32(T v, unsigned s) { return v * (T)s; }
 
 template <int MODE> struct pixel_acc;
 
@@ -71,20 +77,8 @@ __device__ __forceinline__ void load_scales(int kind, const float* __restrict__ 
     }
 }
 
-// canonical-frame strides for the four triangles
-__device__ __forceinline__ void tri_frame(int fx, int fy, int pitch, int& X, int& Y, int& se, int& sf) {
-    const int d1 = fx - fy, d2 = fx + fy;
-    if (d2 >= 0) {
-        if (d1 >= 0) { X = fx;  Y = fy;  se = 1;      sf = pitch; }   // x >= |y|
-        else         { X = fy;  Y = -fx; se = pitch;  sf = -1;    }   // y >= |x|
-    } else {
-        if (d1 >= 0) { X = -fy; Y = fx;  se = -pitch; sf = 1;     }   // -y >= |x|
-        else         { X = -fx; Y = -fy; se = -1;     sf = -pitch; }  // -x >= |y|
-    }
-}
-
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(256) k_stencil4_exact(const void* __restrict__ buf, long long buf_stride, int Hp,
+__global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restrict__ buf, long long buf_stride, int Hp,
                                                          int Wp, int pitch, int P, int H, int W, int C,
                                                          const float* __restrict__ params, float eps, float eta,
                                                          float* __restrict__ out, unsigned* status) {
@@ -132,36 +126,48 @@ __global__ void __launch_bounds__(256) k_stencil4_exact(const void* __restrict__
     const int sh1 = q + 1;
     const T* G = (const T*)buf + (size_t)im * buf_stride;
     const int bx = n1 + P, by = n2 + P;
-    T S = T(0);
+    // S = 2^(2q+4) sum_i s_i F(y_i) = 2^(2q+2) SK + 2^(q+1) SL + SQ: the terms of
+    // each power of two are summed over the taps first and shifted once
+    T SK = T(0), SL = T(0), SQ = T(0);
     bool bad = false;
+    const int two = one << 1, mask = two - 1;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int sg1 = (i & 1) ? -1 : 1, sg2 = (i & 2) ? -1 : 1, sg3 = (i & 4) ? -1 : 1, sg4 = (i & 8) ? -1 : 1;
-        // tau - x_i in units of 2^-(q+1)
-        const int Ox = sg1 * A1 + sg2 * A2 - sg4 * A4 - one;
-        const int Oy = sg2 * A2 + sg3 * A3 + sg4 * A4 - 3 * one;
-        const int mx = (Ox + one) >> sh1, my = (Oy + one) >> sh1;
-        const int fx = Ox - (mx << sh1), fy = Oy - (my << sh1);
-        const int cx = bx + mx, cy = by + my;
-        if (cx < 1 || cx > Wp - 2 || cy < 1 || cy > Hp - 2) {
-            bad = true;
-            continue;
-        }
-        int X, Y, se, sf;
-        tri_frame(fx, fy, pitch, X, Y, se, sf);
-        const T* c = G + (size_t)cy * pitch + cx;
-        const T g00 = c[0], gW = c[-se], gE = c[se], gS = c[-sf], gN = c[sf], gSE = c[se - sf], gNE = c[se + sf];
-        const T u = gS + gN, t = gSE + gNE;
-        const T K1 = (g00 << 2) + gW + gE + u;
-        const T kx = gE - gW, ky = gN - gS;
-        const T kxx = ((gW - g00) << 1) - u + t;
-        const T kxy = gS - gN - gSE + gNE;
-        const T kyy = t + u - ((g00 + gE) << 1);
-        const T hx = (kx << (q + 2)) + mul_s32(kxx, X) + mul_s32(kxy << 1, Y);
-        const T hy = (ky << (q + 2)) + mul_s32(kyy, Y);
-        const T F = (K1 << (2 * q + 1)) + mul_s32(hx, X) + mul_s32(hy, Y);
-        if ((sg1 * sg2 * sg3 * sg4) > 0) S += F; else S -= F;
+        // tau - x_i + 1/2 in units of 2^-(q+1): cell index and offset from the cell corner
+        const int tx = sg1 * A1 + sg2 * A2 - sg4 * A4;
+        const int ty = sg2 * A2 + sg3 * A3 + sg4 * A4 - two;
+        const int mx = tx >> sh1, my = ty >> sh1;
+        const unsigned X = (unsigned)(tx & mask), Y = (unsigned)(ty & mask);
+        const unsigned T1 = (unsigned)max((int)X - (int)Y, 0), T2 = (unsigned)max((int)(X + Y) - two, 0);
+        int cx = bx + mx, cy = by + my;
+        // taps outside the buffer: flag the pixel, read a safe element instead
+        const bool inside = (cx >= 1) & (cx <= Wp - 2) & (cy >= 1) & (cy <= Hp - 2);
+        bad |= !inside;
+        cx = min(max(cx, 1), Wp - 2);
+        cy = min(max(cy, 1), Hp - 2);
+        const T* r0 = G + ((size_t)(cy - 1) * pitch + cx);
+        const T* r1 = r0 + pitch;
+        const T* r2 = r1 + pitch;
+        const T a = r0[-1], b = r0[0], c = r0[1];
+        const T d = r1[-1], e = r1[0], f = r1[1];
+        const T g = r2[-1], h = r2[0], ii = r2[1];
+        const T u1 = d - f, u2 = h - b;
+        const T Ac = u1 + u2 + (c - g);
+        const T Bc = u1 - u2 + (ii - a);
+        const T m = (a - g) + u2;
+        const T ag = a + g, bh = b + h;
+        const T cxx = ag - bh + ((f - e) << 1);
+        const T cyy = ag + bh - ((d + e) << 1);
+        const T cxl = T(0) - (u1 << 1) - cxx - m;
+        const T cyl = (u2 << 1) - cyy - m;
+        const T sk = a + b + d + e;
+        const T sl = mul_u32(cxl, X) + mul_u32(cyl, Y);
+        const T sq = mul_u32(mul_u32(cxx, X) + mul_u32(m << 1, Y), X) + mul_u32(mul_u32(cyy, Y), Y) +
+                     mul_u32(mul_u32(Ac, T1), T1) + mul_u32(mul_u32(Bc, T2), T2);
+        if ((sg1 * sg2 * sg3 * sg4) > 0) { SK += sk; SL += sl; SQ += sq; } else { SK -= sk; SL -= sl; SQ -= sq; }
     }
+    const T S = (SK << (2 * q + 2)) + (SL << (q + 1)) + SQ;
     if (bad) {
         raise_status(status, BSF_EHALO);
         *o = __int_as_float(0x7fc00000);
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(256) k_stencil4_exact(const void* __restrict__
     float sf;
     if constexpr (MODE == MODE_U64) sf = __ll2float_rn((long long)S);
     else sf = i128_to_float(S);
-    *o = ldexpf(sf / prodA, 2 * q - 4 - FRAC);
+    *o = ldexpf(__fdividef(sf, prodA), 2 * q - 4 - FRAC);
 }
 
 template <int KIND>

@@ -8,9 +8,10 @@ Recipe (numpy PCG64, one sub-seed per field):
   * images: uniform f32 in [0, 1), or uniform u8 in {0..255}; the batched N=6
     workload adds three seeded sinusoidal gratings of amplitude 0.25 and
     spatial frequency |k| in [1/64, 1/8] cycles/px;
-  * smooth fields: white noise on a grid 16x coarser than the image, blurred
-    (std 1 coarse px), upsampled with a cubic spline to full size, then
-    rank-normalised to U[0, 1] and mapped affinely to the requested range;
+  * smooth fields: white noise Gaussian-blurred with std = side/16 px
+    (computed on a grid 16x coarser than the image, blur std = side/256
+    coarse px, periodic, then upsampled with a cubic spline), rank-normalised
+    to U[0, 1] and mapped affinely to the requested range;
   * orientation from a vector field: theta = atan2(v, u) mod pi of two
     independent smooth fields centred at zero.
 """
@@ -53,8 +54,9 @@ def _smooth_noise(H: int, W: int, g: np.random.Generator) -> np.ndarray:
     cs = 16
     hc, wc = H // cs + 6, W // cs + 6
     z = g.standard_normal((hc, wc))
+    blur = max(1.0, max(H, W) / 16.0 / cs)  # std side/16 px, in coarse px
     if _ndi is not None:
-        z = _ndi.gaussian_filter(z, 1.0, mode="wrap")
+        z = _ndi.gaussian_filter(z, blur, mode="wrap")
         up = _ndi.zoom(z, cs, order=3)
     else:  # plain nearest fallback (never used where scipy exists)
         up = np.kron(z, np.ones((cs, cs)))
