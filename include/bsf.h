@@ -61,6 +61,7 @@ typedef int bsf_status;
 #define BSF_EINFEASIBLE 6     /* strict mode: a covariance needed the elongation clamp */
 #define BSF_EBADSCALE 7       /* device: a scale or covariance was not finite/positive */
 #define BSF_ERANGE 8          /* device: a kernel too large for the exact integer form */
+#define BSF_ENOSCRATCH 9      /* bsf_filter_noalloc: the image needs more than its fixed scratch */
 
 /* image element types */
 #define BSF_U8 0
@@ -156,6 +157,28 @@ bsf_status bsf_get_device_status(bsf_ctx* ctx, void* stream, int* status);
  * launches of each (any pointer may be NULL). */
 bsf_status bsf_profile_begin(bsf_ctx* ctx);
 bsf_status bsf_profile_end(bsf_ctx* ctx, double* ms_preintegrate, double* ms_stencil, int* nlaunch);
+
+/* Allocation-free variant of bsf_filter for ONE H x W image (B = C = 1).
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, such as plugins inside a host application
+ * that owns the device memory budget, or latency-critical loops in which
+ * cudaMalloc/cudaFree would synchronise the device.  It needs no context and
+ * calls no allocating routine: its scratch (the pre-integrated buffer and the
+ * scan carries) is a fixed device array of BSF_NOALLOC_SCRATCH_BYTES compiled
+ * into the library and reserved on every GPU that loads it until the process
+ * exits.  Images whose buffer of (H+2P)*(W+2P) elements (8 bytes for u8,
+ * 16 for f32 in the exact form) plus the carries exceed it are rejected with
+ * BSF_ENOSCRATCH before anything runs (u8 images of about 1000 x 1000 px
+ * fit).  opts is required and must give opts->halo or opts->max_scale.
+ * Runs on the current device, asynchronously on `stream`; the first call on a
+ * device looks up the array's device address, so make it before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * There is no device status word: pixels with invalid scales or with taps
+ * outside the buffer are NaN. */
+#define BSF_NOALLOC_SCRATCH_BYTES (32u << 20)
+bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H, int64_t W, int N, const float* params,
+                              int kind, const bsf_opts* opts, float* out, void* stream);
 
 /* Static description of a status code. */
 const char* bsf_status_string(bsf_status s);

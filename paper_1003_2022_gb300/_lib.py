@@ -21,6 +21,8 @@ BSF_EHALO = 5
 BSF_EINFEASIBLE = 6
 BSF_EBADSCALE = 7
 BSF_ERANGE = 8
+BSF_ENOSCRATCH = 9
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 BSF_U8 = 0
 BSF_F32 = 1
@@ -36,7 +38,7 @@ BSF_PREC_FP64 = 1
 EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
-    "bsf_profile_begin", "bsf_profile_end",
+    "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc",
 ]
 
 
@@ -95,6 +97,8 @@ def load(path: str | None = None):
     lib.bsf_profile_end.restype = i32
     lib.bsf_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int)]
+    lib.bsf_filter_noalloc.restype = i32
+    lib.bsf_filter_noalloc.argtypes = [vp, i32, i64, i64, i32, vp, i32, op, vp, vp]
     lib.bsf_status_string.restype = ctypes.c_char_p
     lib.bsf_status_string.argtypes = [i32]
     _lib = lib
@@ -153,6 +157,12 @@ def bsf_preintegrate(ctx, image, dtype, H, W, N, halo, precision, buffer, stream
 def bsf_apply(ctx, buffer, dtype, H, W, N, halo, params, kind, opts, out, stream) -> int:
     return load().bsf_apply(ctx, buffer, dtype, H, W, N, halo, params, kind,
                             ctypes.byref(opts) if opts is not None else None, out, stream)
+
+
+def bsf_filter_noalloc(image, dtype, H, W, N, params, kind, opts, out, stream) -> int:
+    """Allocation-free filter of one image (scratch is a fixed array inside the library)."""
+    return load().bsf_filter_noalloc(image, dtype, H, W, N, params, kind,
+                                     ctypes.byref(opts) if opts is not None else None, out, stream)
 
 
 def bsf_profile_begin(ctx) -> None:

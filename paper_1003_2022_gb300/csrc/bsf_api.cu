@@ -100,6 +100,7 @@ const char* bsf_status_string(bsf_status s) {
         case BSF_EINFEASIBLE: return "a covariance needed the elongation clamp (strict mode)";
         case BSF_EBADSCALE: return "a scale or covariance was not finite and positive";
         case BSF_ERANGE: return "a kernel too large for the exact integer form";
+        case BSF_ENOSCRATCH: return "the image does not fit the fixed scratch of bsf_filter_noalloc";
         default: return "unknown status";
     }
 }
