@@ -144,6 +144,21 @@ bsf_status bsf_apply(bsf_ctx* ctx, const void* buffer, int dtype, int64_t H, int
                      int halo, const float* params, int kind, const bsf_opts* opts, float* out,
                      void* stream);
 
+/* Backward pass (gradients; the paper has none, this is the adjoint of the
+ * forward path).  For a scale-vector field (kind BSF_PARAM_SCALES, B*4*H*W
+ * floats) and grad_out = dL/dfbar (B*C*H*W floats), writes
+ *   grad_image  (nullable, B*C*H*W floats) = sum_n g[n] beta_{a(n)}(n - k),
+ *   grad_scales (nullable, B*4*H*W floats) = sum_c g[n] dfbar[n]/da_k(n)
+ * (channels sharing one field are summed).  The scale gradient is exact for
+ * the per-pixel dyadic scales the forward pass uses (an exact integer
+ * combination of the pre-integrated buffer); the image gradient scatters the
+ * stencil's weights into an FP64 buffer and applies the transposes of RS4,
+ * RS3, RS2, RS1 in that order.  Only the exact form (opts->precision ==
+ * BSF_PREC_EXACT) is supported.  At least one output must be non-NULL. */
+bsf_status bsf_filter_backward(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
+                               int64_t W, int N, const float* scales, const float* grad_out,
+                               float* grad_image, float* grad_scales, const bsf_opts* opts, void* stream);
+
 /* Synchronise `stream`, then return (and clear) the device status word in
  * *status: 0 or the OR of (1 << BSF_EHALO), (1 << BSF_EBADSCALE),
  * (1 << BSF_ERANGE), (1 << BSF_EINFEASIBLE) raised since the last call. */

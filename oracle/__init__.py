@@ -13,6 +13,9 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
   (Eq. SVF_2D with the Dirac-comb image used to derive Eq. keyeqn).
 * ``preint4_i64`` / ``preint4_f64``: Algorithm 1 step 2 (Sec. 3.1, RS1-RS4).
 * ``stencil4``: Algorithm 1 step 3 (Table 1, Eq. final_eqn, App. F).
+* ``adjoint4``: the transpose of the plain definition (gradient with respect
+  to the image); ``direct4_grad_fd``: central differences of ``direct4`` with
+  respect to the scales.
 * ``map4``: the optimal scale vector of Sec. 3.2.2, steps (i)-(iii).
 * ``U_bound``: the elongation bound of Prop. 3.1.
 
@@ -59,6 +62,9 @@ def _load():
         lib.bo_beta4_lines.argtypes = [_dp, ctypes.c_double, ctypes.c_double]
         lib.bo_direct4.restype = None
         lib.bo_direct4.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i64p, ctypes.c_int64, _dp]
+        lib.bo_adjoint4.restype = None
+        lib.bo_adjoint4.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _i64p, ctypes.c_int64,
+                                    _dp]
         lib.bo_preint4_i64.restype = None
         lib.bo_preint4_i64.argtypes = [_i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p]
         lib.bo_preint4_f64.restype = None
@@ -138,6 +144,34 @@ def direct4(f, a, idx=None) -> np.ndarray:
     _load().bo_direct4(_ptr(f, _dp), H, W, _ptr(a, _dp),
                        _ptr(ii, _i64p) if ii is not None else None, n, _ptr(out, _dp))
     return out.reshape(H, W) if n < 0 else out
+
+
+def adjoint4(g, a, idx) -> np.ndarray:
+    """O-adjoint: sum_n g[n] beta_{a(n)}(n - k) at the flat points idx (gradient of
+    sum g * fbar with respect to the image)."""
+    g = _d(g)
+    H, W = g.shape
+    a = _d(a)
+    assert a.shape == (4, H, W)
+    ii, n = _idx(idx, H * W)
+    out = np.empty(n)
+    _load().bo_adjoint4(_ptr(g, _dp), H, W, _ptr(a, _dp), float(np.max(a)), _ptr(ii, _i64p), n, _ptr(out, _dp))
+    return out
+
+
+def direct4_grad_fd(f, a, idx, h: float = 1e-3) -> np.ndarray:
+    """Central finite differences (step h, FP64) of O-direct with respect to each
+    scale a_k at the pixels idx: returns (4, len(idx)).  a(n) enters only fbar[n]."""
+    f = _d(f)
+    a = _d(a)
+    out = np.empty((4, len(idx)))
+    for k in range(4):
+        ap = a.copy()
+        am = a.copy()
+        ap[k].flat[idx] += h
+        am[k].flat[idx] -= h
+        out[k] = (direct4(f, ap, idx) - direct4(f, am, idx)) / (2 * h)
+    return out
 
 
 def preint4_i64(f_int, P: int) -> np.ndarray:

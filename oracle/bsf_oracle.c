@@ -177,6 +177,34 @@ void bo_direct4(const double* f, int H, int W, const double* a, const int64_t* i
 }
 
 /* ------------------------------------------------------------------ */
+/* O-adjoint: the transpose of the plain definition,                   */
+/*   (K^T g)[k] = sum_n g[n] beta^4_{a(n)}(n - k),                      */
+/* the gradient of sum_n g[n] fbar[n] with respect to f[k].  Evaluated   */
+/* for the listed points k by gathering over every pixel n whose support */
+/* can reach k (support half-widths bounded by amax).                    */
+/* ------------------------------------------------------------------ */
+void bo_adjoint4(const double* g, int H, int W, const double* a, double amax, const int64_t* idx, int64_t npts,
+                 double* out) {
+    const int64_t HW = (int64_t)H * W;
+    const int R = (int)ceil(0.5 * (amax + SQRT2 * amax)) + 2;
+    for (int64_t t = 0; t < npts; ++t) {
+        const int k2 = (int)(idx[t] / W), k1 = (int)(idx[t] % W);
+        double s = 0;
+        for (int n2 = k2 - R; n2 <= k2 + R; ++n2) {
+            if (n2 < 0 || n2 >= H) continue;
+            for (int n1 = k1 - R; n1 <= k1 + R; ++n1) {
+                if (n1 < 0 || n1 >= W) continue;
+                const int64_t p = (int64_t)n2 * W + n1;
+                if (g[p] == 0) continue;
+                const double ak[4] = {a[p], a[HW + p], a[2 * HW + p], a[3 * HW + p]};
+                s += g[p] * bo_beta4(ak, (double)(n1 - k1), (double)(n2 - k2));
+            }
+        }
+        out[t] = s;
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* O-alg step 2: the four recursions of Algorithm 1 on a zero-padded   */
 /* buffer of (H+2P) rows x (W+2P) columns holding f at offset (P,P),    */
 /* every recursion started from zero initial values at the buffer edge. */

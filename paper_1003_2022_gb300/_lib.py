@@ -38,7 +38,7 @@ BSF_PREC_FP64 = 1
 EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
-    "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc",
+    "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward",
 ]
 
 
@@ -97,6 +97,8 @@ def load(path: str | None = None):
     lib.bsf_profile_end.restype = i32
     lib.bsf_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int)]
+    lib.bsf_filter_backward.restype = i32
+    lib.bsf_filter_backward.argtypes = [vp, vp, i32, i64, i64, i64, i64, i32, vp, vp, vp, vp, op, vp]
     lib.bsf_filter_noalloc.restype = i32
     lib.bsf_filter_noalloc.argtypes = [vp, i32, i64, i64, i32, vp, i32, op, vp, vp]
     lib.bsf_status_string.restype = ctypes.c_char_p
@@ -157,6 +159,12 @@ def bsf_preintegrate(ctx, image, dtype, H, W, N, halo, precision, buffer, stream
 def bsf_apply(ctx, buffer, dtype, H, W, N, halo, params, kind, opts, out, stream) -> int:
     return load().bsf_apply(ctx, buffer, dtype, H, W, N, halo, params, kind,
                             ctypes.byref(opts) if opts is not None else None, out, stream)
+
+
+def bsf_filter_backward(ctx, image, dtype, B, C, H, W, N, scales, grad_out, grad_image, grad_scales, opts,
+                        stream) -> int:
+    return load().bsf_filter_backward(ctx, image, dtype, B, C, H, W, N, scales, grad_out, grad_image, grad_scales,
+                                      ctypes.byref(opts) if opts is not None else None, stream)
 
 
 def bsf_filter_noalloc(image, dtype, H, W, N, params, kind, opts, out, stream) -> int:

@@ -154,3 +154,55 @@ def halo_for(max_scale: float, kind: str = "srt") -> int:
     import math
     ext = (2.41422 if kind == "scales" else 8.3640) * max_scale
     return int(math.ceil(0.5 * ext)) + 4
+
+
+def filter_backward(image: torch.Tensor, scales: torch.Tensor, grad_out: torch.Tensor, need_image: bool = True,
+                    need_scales: bool = True, N: int = 4, halo: int = 0, max_scale: float = 0.0, stream=None):
+    """Gradients of sum(grad_out * filter(image, scales)) w.r.t. image and scales (kind "scales")."""
+    img = _as4d(image).contiguous()
+    B, C, H, W = img.shape
+    sc = (scales if scales.dim() == 4 else scales[None]).contiguous()
+    if tuple(sc.shape) != (B, 4, H, W) or sc.dtype != torch.float32:
+        raise ValueError("scales must be float32 of shape (B,4,H,W)")
+    g = grad_out.reshape(B, C, H, W).contiguous().to(torch.float32)
+    gi = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device) if need_image else None
+    gs = torch.empty((B, 4, H, W), dtype=torch.float32, device=img.device) if need_scales else None
+    dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
+    opts = make_opts("exact", halo, max_scale)
+    rc = L.bsf_filter_backward(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, sc.data_ptr(),
+                               g.data_ptr(), gi.data_ptr() if gi is not None else None,
+                               gs.data_ptr() if gs is not None else None, opts, _stream_ptr(stream))
+    L.check(rc, "bsf_filter_backward")
+    if gi is not None and image.dim() < 4:
+        gi = gi.reshape(image.shape)
+    if gs is not None and scales.dim() < 4:
+        gs = gs.reshape(scales.shape)
+    return gi, gs
+
+
+class BoxSplineFilter(torch.autograd.Function):
+    """Differentiable space-variant box-spline filter: out = filter(image, scales).
+
+    Gradients flow to the float32 image and to the per-pixel scale vectors
+    (kind "scales"); both come from the CUDA adjoint (bsf_filter_backward).
+    """
+
+    @staticmethod
+    def forward(ctx, image, scales, halo: int = 0, max_scale: float = 0.0):
+        out = filter(image, scales, kind="scales", halo=halo, max_scale=max_scale)
+        ctx.save_for_backward(image, scales)
+        ctx.halo = halo
+        ctx.max_scale = max_scale
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        image, scales = ctx.saved_tensors
+        gi, gs = filter_backward(image, scales, grad_out, need_image=ctx.needs_input_grad[0],
+                                 need_scales=ctx.needs_input_grad[1], halo=ctx.halo, max_scale=ctx.max_scale)
+        return gi, gs, None, None
+
+
+def box_spline_filter(image: torch.Tensor, scales: torch.Tensor, halo: int = 0, max_scale: float = 0.0):
+    """Autograd entry point of the filter with a learnable scale field."""
+    return BoxSplineFilter.apply(image, scales, halo, max_scale)

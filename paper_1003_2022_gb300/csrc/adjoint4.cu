@@ -1,0 +1,265 @@
+// Adjoint of the four-directional filter: gradients of L with respect to the
+// scale field a and to the image f, given g = dL/dfbar.  The paper has no
+// backward pass; it is derived here from the forward path of Algorithm 1.
+//
+// With the exact integer form of the forward pass (stencil4.cu),
+//   fbar[n] = (1/P) sum_i s_i F(y_i),  P = a1 a2' a3 a4',
+//   y_i = n + ((s1 a1 + s2 a2' - s4 a4' - 1)/2, (s2 a2' + s3 a3 + s4 a4' - 3)/2),
+// with s_k = 1 - 2 q_k (Table 1).  Hence
+//   dfbar/da_k = (1/P) sum_i s_i grad F(y_i) . dy_i/da_k - fbar / a_k,
+// dy_i/da1 = (s1/2, 0), dy_i/da2 = (s2, s2)/(2 sqrt2), dy_i/da3 = (0, s3/2),
+// dy_i/da4 = (-s4, s4)/(2 sqrt2).  grad F is the derivative of the cell's
+// quadratic-plus-truncated-powers form, an integer combination of G like F
+// itself, so the four sums are evaluated exactly modulo 2^64 / 2^128 with the
+// same per-pixel dyadic scales as the forward pass: the gradient is that of
+// the function the forward pass computes.
+//
+// dL/df = M^T S^T g: S^T scatters g[n] s_i / P times the nine ZP weights of
+// every tap into an FP64 buffer (the weights are exact integers below 2^53),
+// and M^T is the transpose of the four running sums, applied in the reverse
+// order RS4^T, RS3^T, RS2^T, RS1^T: suffix sums along (-1,1), (0,1), (1,1)
+// and (1,0), each stopping at the buffer edge (the exact transpose of the
+// finite-buffer recursions).  The scattered weights of one pixel form a
+// fourth-order difference of compact support, so the suffix sums stay small
+// and FP64 keeps ~1e-10 relative accuracy.
+#include "bsf_common.cuh"
+#include "bsf_internal.h"
+
+namespace {
+
+__device__ __forceinline__ int ilog2_ceil_g(float v) {
+    int e;
+    const float m = frexpf(v, &e);
+    return (m == 0.5f) ? e - 1 : e;
+}
+
+template <class T> __device__ __forceinline__ T mulu(T v, unsigned s) { return v * (T)s; }
+
+template <int MODE> __device__ __forceinline__ float to_float_s(typename mode_traits<MODE>::T v);
+template <> __device__ __forceinline__ float to_float_s<MODE_U64>(unsigned long long v) {
+    return __ll2float_rn((long long)v);
+}
+template <> __device__ __forceinline__ float to_float_s<MODE_U128>(u128 v) { return i128_to_float(v); }
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) k_stencil4_grad(const void* __restrict__ buf, long long buf_stride, int Hp,
+                                                          int Wp, int pitch, int P, int H, int W, int C,
+                                                          const float* __restrict__ scales,
+                                                          const float* __restrict__ gout,
+                                                          float* __restrict__ gscales, double* __restrict__ hbuf,
+                                                          unsigned* status) {
+    typedef typename mode_traits<MODE>::T T;
+    constexpr int ACC = mode_traits<MODE>::ACC_BITS;
+    constexpr int VAL = mode_traits<MODE>::VAL_BITS;
+    constexpr int FRAC = mode_traits<MODE>::FRAC_BITS;
+    const int n1 = blockIdx.x * 32 + threadIdx.x;
+    const int n2 = blockIdx.y * 8 + threadIdx.y;
+    const int im = blockIdx.z;
+    if (n1 >= W || n2 >= H) return;
+    const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
+    const float* pr = scales + (size_t)(im / C) * 4 * HW;
+    const float a1 = pr[p], a2 = pr[HW + p], a3 = pr[2 * HW + p], a4 = pr[3 * HW + p];
+    const float gv = gout[(size_t)im * HW + p];
+    float* gs = gscales ? gscales + (size_t)(im / C) * 4 * HW + p : nullptr;
+    const float qnan = __int_as_float(0x7fc00000);
+    if (!(a1 > 0.f && a2 > 0.f && a3 > 0.f && a4 > 0.f) || !(a1 < 1e30f && a2 < 1e30f && a3 < 1e30f && a4 < 1e30f)) {
+        raise_status(status, BSF_EBADSCALE);
+        if (gs) for (int k = 0; k < 4; ++k) atomicAdd(gs + k * HW, qnan);
+        return;
+    }
+    // the same per-pixel dyadic scales as the forward pass
+    const float a2p = a2 * 0.70710678118654752f, a4p = a4 * 0.70710678118654752f;
+    const float Bm = fminf((a1 + 1.f) * (a3 + 1.f) * a2p * a4p, 0.5f * a1 * a3 * (2.f * a2p + 1.f) * (a4p + 1.f));
+    int q = (ACC - 6 - VAL - ilog2_ceil_g(Bm)) >> 1;
+    q = min(q, 24);
+    q = min(q, 30 - ilog2_ceil_g(a1 + a2p + a3 + a4p + 3.f));
+    const float sc = ldexpf(1.f, q);
+    const int A1 = __float2int_rn(a1 * sc), A2 = __float2int_rn(a2p * sc);
+    const int A3 = __float2int_rn(a3 * sc), A4 = __float2int_rn(a4p * sc);
+    if (q < 0 || A1 < 1 || A2 < 1 || A3 < 1 || A4 < 1) {
+        raise_status(status, BSF_ERANGE);
+        if (gs) for (int k = 0; k < 4; ++k) atomicAdd(gs + k * HW, qnan);
+        return;
+    }
+    const int sh1 = q + 1, two = 2 << q, mask = two - 1;
+    const T* G = (const T*)buf + (size_t)im * buf_stride;
+    double* hb = hbuf ? hbuf + (size_t)im * ((size_t)Hp * pitch) : nullptr;
+    const double prodA_d = ((double)A1 * (double)A2) * ((double)A3 * (double)A4);
+    // scatter coefficient g / (2^(2q+4) P~) = g 2^(2q-4) / prod(A)
+    const double cg = (double)gv * ldexp(1.0, 2 * q - 4) / prodA_d;
+    const int bx = n1 + P, by = n2 + P;
+    T SK = T(0), SL = T(0), SQ = T(0), E1 = T(0), E2 = T(0), E3 = T(0), E4 = T(0);
+    bool bad = false;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+        const int sg1 = (i & 1) ? -1 : 1, sg2 = (i & 2) ? -1 : 1, sg3 = (i & 4) ? -1 : 1, sg4 = (i & 8) ? -1 : 1;
+        const int sgn = sg1 * sg2 * sg3 * sg4;
+        const int tx = sg1 * A1 + sg2 * A2 - sg4 * A4;
+        const int ty = sg2 * A2 + sg3 * A3 + sg4 * A4 - two;
+        const int mx = tx >> sh1, my = ty >> sh1;
+        const unsigned X = (unsigned)(tx & mask), Y = (unsigned)(ty & mask);
+        const unsigned T1 = (unsigned)max((int)X - (int)Y, 0), T2 = (unsigned)max((int)(X + Y) - two, 0);
+        int cx = bx + mx, cy = by + my;
+        const bool inside = (cx >= 1) & (cx <= Wp - 2) & (cy >= 1) & (cy <= Hp - 2);
+        bad |= !inside;
+        cx = min(max(cx, 1), Wp - 2);
+        cy = min(max(cy, 1), Hp - 2);
+        const size_t i0 = (size_t)(cy - 1) * pitch + cx;
+        const T* r0 = G + i0;
+        const T* r1 = r0 + pitch;
+        const T* r2 = r1 + pitch;
+        const T a = r0[-1], b = r0[0], c = r0[1];
+        const T d = r1[-1], e = r1[0], f = r1[1];
+        const T g = r2[-1], h = r2[0], ii = r2[1];
+        const T u1 = d - f, u2 = h - b;
+        const T Ac = u1 + u2 + (c - g);
+        const T Bc = u1 - u2 + (ii - a);
+        const T m = (a - g) + u2;
+        const T ag = a + g, bh = b + h;
+        const T cxx = ag - bh + ((f - e) << 1);
+        const T cyy = ag + bh - ((d + e) << 1);
+        const T cxl = T(0) - (u1 << 1) - cxx - m;
+        const T cyl = (u2 << 1) - cyy - m;
+        const T sk = a + b + d + e;
+        const T px = mulu(cxx, X) + mulu(m, Y), py = mulu(m, X) + mulu(cyy, Y);
+        const T pa = mulu(Ac, T1), pb = mulu(Bc, T2);
+        const T sl = mulu(cxl, X) + mulu(cyl, Y);
+        const T sq = mulu(px, X) + mulu(py, Y) + mulu(pa, T1) + mulu(pb, T2);
+        // 2^(2q+4) dF/dX and dF/dY, up to the factor 2^(q+3) relating X to phi
+        const T gX = (cxl << sh1) + ((px + pa + pb) << 1);
+        const T gY = (cyl << sh1) + ((py - pa + pb) << 1);
+        if (sgn > 0) { SK += sk; SL += sl; SQ += sq; } else { SK -= sk; SL -= sl; SQ -= sq; }
+        const T dE1 = gX, dE3 = gY, dE2 = gX + gY, dE4 = gY - gX;
+        if (sgn * sg1 > 0) E1 += dE1; else E1 -= dE1;
+        if (sgn * sg2 > 0) E2 += dE2; else E2 -= dE2;
+        if (sgn * sg3 > 0) E3 += dE3; else E3 -= dE3;
+        if (sgn * sg4 > 0) E4 += dE4; else E4 -= dE4;
+        if (hb != nullptr && inside) {
+            // the nine ZP weights (integers < 2^(2q+4)) of this tap
+            const long long t = two, Xl = X, Yl = Y, T1l = T1, T2l = T2;
+            const long long xa = max(t - Xl - Yl, 0ll);
+            const long long w[9] = {
+                xa * xa,                                                            // a (-1,-1)
+                t * t + 2 * t * Xl - 2 * t * Yl - Xl * Xl - 2 * Xl * Yl + Yl * Yl + T2l * T2l - T1l * T1l,  // b
+                T1l * T1l,                                                          // c (1,-1)
+                t * t - 2 * t * Xl + 2 * t * Yl - 2 * Yl * Yl + T1l * T1l + T2l * T2l,  // d (-1,0)
+                t * t + 2 * t * Xl + 2 * t * Yl - 2 * Xl * Xl - 2 * Yl * Yl,         // e (0,0)
+                2 * Xl * Xl - T1l * T1l - T2l * T2l,                                 // f (1,0)
+                (Xl - Yl) * (Xl - Yl) - T1l * T1l,                                   // g (-1,1)
+                -Xl * Xl + 2 * Xl * Yl + Yl * Yl + T1l * T1l - T2l * T2l,            // h (0,1)
+                T2l * T2l};                                                          // i (1,1)
+            const double cs = sgn > 0 ? cg : -cg;
+            double* h0 = hb + i0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if (w[k] == 0) continue;
+                atomicAdd(h0 + (k / 3) * pitch + (k % 3) - 1, cs * (double)w[k]);
+            }
+        }
+    }
+    if (gs == nullptr) return;
+    if (bad) {
+        raise_status(status, BSF_EHALO);
+        for (int k = 0; k < 4; ++k) atomicAdd(gs + k * HW, qnan);
+        return;
+    }
+    const T S = (SK << (2 * q + 2)) + (SL << (q + 1)) + SQ;
+    const float prodA = ((float)A1 * (float)A2) * ((float)A3 * (float)A4);
+    const float fbar = ldexpf(__fdividef(to_float_s<MODE>(S), prodA), 2 * q - 4 - FRAC);
+    // (1/P~) sum_i s_i grad F . dy/da_k = E_k 2^(3q-4-frac) / prod(A)   (times 1/sqrt2 for k = 2, 4)
+    const float ek = ldexpf(1.f, 3 * q - 4 - FRAC) / prodA;
+    const float isq2 = 0.70710678118654752f;
+    const float d1 = to_float_s<MODE>(E1) * ek - fbar * sc / (float)A1;
+    const float d2 = to_float_s<MODE>(E2) * ek * isq2 - fbar * sc * isq2 / (float)A2;
+    const float d3 = to_float_s<MODE>(E3) * ek - fbar * sc / (float)A3;
+    const float d4 = to_float_s<MODE>(E4) * ek * isq2 - fbar * sc * isq2 / (float)A4;
+    atomicAdd(gs, gv * d1);
+    atomicAdd(gs + HW, gv * d2);
+    atomicAdd(gs + 2 * HW, gv * d3);
+    atomicAdd(gs + 3 * HW, gv * d4);
+}
+
+// Suffix sums along direction (dx, dy) in {(-1,1), (0,1), (1,1), (1,0)} of
+// nimg FP64 buffers (Hp x pitch), one warp per line.  When crop is set (the
+// last, row-direction pass) the image window [P, P+H) x [P, P+W) of the
+// result is also written to out as float.
+__global__ void k_line_suffix(double* __restrict__ X, long long stride, int Hp, int Wp, int pitch, int dx, int dy,
+                              float* __restrict__ out, int P, int H, int W) {
+    const int im = blockIdx.y;
+    const int line = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    // line start points: the cells whose predecessor (start - d) is outside the buffer
+    int x0, y0;
+    if (dy == 0) {             // rows
+        if (line >= Hp) return;
+        x0 = 0; y0 = line;
+    } else if (dx == 0) {      // columns
+        if (line >= Wp) return;
+        x0 = line; y0 = 0;
+    } else if (dx == 1) {      // (1,1): starts on the top row and the left column
+        if (line >= Wp + Hp - 1) return;
+        if (line < Wp) { x0 = line; y0 = 0; } else { x0 = 0; y0 = line - Wp + 1; }
+    } else {                   // (-1,1): starts on the top row and the right column
+        if (line >= Wp + Hp - 1) return;
+        if (line < Wp) { x0 = line; y0 = 0; } else { x0 = Wp - 1; y0 = line - Wp + 1; }
+    }
+    int len;
+    {
+        const int lx = dx > 0 ? Wp - x0 : (dx < 0 ? x0 + 1 : 1 << 30);
+        const int ly = dy > 0 ? Hp - y0 : 1 << 30;
+        len = min(lx, ly);
+    }
+    double* base = X + (size_t)im * stride;
+    double carry = 0.0;
+    for (int end = len; end > 0; end -= 32) {
+        const int t = end - 32 + lane;
+        const bool ok = t >= 0;
+        const size_t off = ok ? (size_t)(y0 + t * dy) * pitch + (x0 + t * dx) : 0;
+        double v = ok ? base[off] : 0.0;
+        // suffix scan within the chunk (lane 31 is the last element)
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, v, s);
+            if (lane + s < 32) v += o;
+        }
+        const double r = v + carry;
+        if (ok) {
+            base[off] = r;
+            if (out != nullptr) {
+                const int xx = x0 + t * dx - P, yy = y0 + t * dy - P;
+                if (xx >= 0 && xx < W && yy >= 0 && yy < H) out[(size_t)im * H * W + (size_t)yy * W + xx] = (float)r;
+            }
+        }
+        carry += __shfl_sync(0xffffffffu, v, 0);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp, int Wp, int pitch, int P, int H,
+                         int W, int C, int nimg, const float* scales, const float* gout, float* gscales, double* hbuf,
+                         unsigned* status, cudaStream_t st) {
+    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nimg);
+    if (mode == MODE_U64)
+        k_stencil4_grad<MODE_U64><<<grd, blk, 0, st>>>(buf, buf_stride, Hp, Wp, pitch, P, H, W, C, scales, gout,
+                                                        gscales, hbuf, status);
+    else if (mode == MODE_U128)
+        k_stencil4_grad<MODE_U128><<<grd, blk, 0, st>>>(buf, buf_stride, Hp, Wp, pitch, P, H, W, C, scales, gout,
+                                                         gscales, hbuf, status);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_scans(double* hbuf, int nimg, int Hp, int Wp, int pitch, int P, int H, int W,
+                                   float* gimage, cudaStream_t st) {
+    const long long stride = (long long)Hp * pitch;
+    const int dirs[4][2] = {{-1, 1}, {0, 1}, {1, 1}, {1, 0}};  // RS4^T, RS3^T, RS2^T, RS1^T
+    for (int k = 0; k < 4; ++k) {
+        const int dx = dirs[k][0], dy = dirs[k][1];
+        const int nlines = dy == 0 ? Hp : (dx == 0 ? Wp : Wp + Hp - 1);
+        dim3 g((unsigned)((nlines + 7) / 8), nimg);
+        k_line_suffix<<<g, 256, 0, st>>>(hbuf, stride, Hp, Wp, pitch, dx, dy, k == 3 ? gimage : nullptr, P, H, W);
+    }
+    return cudaGetLastError();
+}

@@ -19,6 +19,8 @@ struct bsf_ctx {
     size_t buf_bytes;
     void* work;              // scan carry workspace
     size_t work_bytes;
+    void* hbuf;              // FP64 scatter buffers of the adjoint
+    size_t hbuf_bytes;
     std::mutex mu;
     bool profiling;
     size_t prof_used;                                // event triples recorded since begin
@@ -120,6 +122,8 @@ bsf_status bsf_create(bsf_ctx** ctx, int device) {
     c->buf_bytes = 0;
     c->work = nullptr;
     c->work_bytes = 0;
+    c->hbuf = nullptr;
+    c->hbuf_bytes = 0;
     c->profiling = false;
     c->prof_used = 0;
     cudaError_t e = cudaMalloc((void**)&c->d_status, 2 * sizeof(unsigned));
@@ -144,6 +148,7 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     cudaDeviceSynchronize();
     if (c->buf) cudaFree(c->buf);
     if (c->work) cudaFree(c->work);
+    if (c->hbuf) cudaFree(c->hbuf);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& t : c->prof)
         for (int i = 0; i < 3; ++i) cudaEventDestroy(t[i]);
@@ -323,6 +328,59 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
         BSF_TRY(cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         BSF_TRY(cudaStreamSynchronize(st));
         if (h & (1u << BSF_EINFEASIBLE)) return BSF_EINFEASIBLE;
+    }
+    return BSF_OK;
+}
+
+bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                               int N, const float* scales, const float* grad_out, float* grad_image,
+                               float* grad_scales, const bsf_opts* opts, void* stream) {
+    if (!c || !image || !scales || !grad_out) return BSF_EINVAL;
+    if (!grad_image && !grad_scales) return BSF_EINVAL;
+    if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != BSF_PREC_EXACT) return BSF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t HW = H * W;
+    int P = 0;
+    bsf_status s = resolve_halo(c, scales, BSF_PARAM_SCALES, B, HW, o, st, &P);
+    if (s != BSF_OK) return s;
+    const int mode = mode_of(dtype, o.precision);
+    const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P, pitch = Wp;
+    const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
+    const size_t per_h = (size_t)Hp * pitch * sizeof(double);
+    const size_t budget = (size_t)16 << 30;
+    int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / ((per_img + per_h) * (size_t)C)));
+    bchunk = std::min<int64_t>(bchunk, B);
+    const size_t esz = (dtype == BSF_U8) ? 1 : 4;
+    if (grad_scales) BSF_TRY(cudaMemsetAsync(grad_scales, 0, (size_t)B * 4 * HW * sizeof(float), st));
+    for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
+        const int64_t nbat = std::min<int64_t>(bchunk, B - b0);
+        const int nimg = (int)(nbat * C);
+        const scan_plan plan = make_scan_plan(Hp, Wp, nimg, elem_bytes(mode));
+        BSF_TRY(grow(&c->buf, &c->buf_bytes, per_img * nimg));
+        BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
+        double* hb = nullptr;
+        if (grad_image) {
+            BSF_TRY(grow(&c->hbuf, &c->hbuf_bytes, per_h * nimg));
+            hb = (double*)c->hbuf;
+            BSF_TRY(cudaMemsetAsync(hb, 0, per_h * nimg, st));
+        }
+        const char* img0 = (const char*)image + (size_t)(b0 * C) * HW * esz;
+        BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf, (long long)Hp * pitch,
+                         pitch, c->work, st));
+        BSF_TRY(launch_grad4(mode, c->buf, (long long)Hp * pitch, Hp, Wp, pitch, P, (int)H, (int)W, (int)C, nimg,
+                             scales + (size_t)b0 * 4 * HW, grad_out + (size_t)(b0 * C) * HW,
+                             grad_scales ? grad_scales + (size_t)b0 * 4 * HW : nullptr, hb, c->d_status, st));
+        if (grad_image)
+            BSF_TRY(launch_transpose_scans(hb, nimg, Hp, Wp, pitch, P, (int)H, (int)W,
+                                           grad_image + (size_t)(b0 * C) * HW, st));
     }
     return BSF_OK;
 }

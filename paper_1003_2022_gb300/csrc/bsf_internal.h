@@ -41,3 +41,10 @@ cudaError_t launch_map4(const float* params, int kind, long long npix, float eps
                         uint8_t* flags, cudaStream_t st);
 cudaError_t launch_extent4(const float* params, int kind, long long npix, float eps, float eta, unsigned* ext_bits,
                            cudaStream_t st);
+
+// Adjoint (adjoint4.cu).
+cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp, int Wp, int pitch, int P, int H,
+                         int W, int C, int nimg, const float* scales, const float* gout, float* gscales, double* hbuf,
+                         unsigned* status, cudaStream_t st);
+cudaError_t launch_transpose_scans(double* hbuf, int nimg, int Hp, int Wp, int pitch, int P, int H, int W,
+                                   float* gimage, cudaStream_t st);
