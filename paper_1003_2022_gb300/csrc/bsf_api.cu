@@ -248,17 +248,19 @@ static bsf_status resolve_halo(bsf_ctx* c, const float* params, int kind, int64_
 }
 
 static cudaError_t run_scan(int mode, int dtype, const void* img, long long img_stride, int nimg, int H, int W, int P,
-                            void* G, long long G_stride, int pitch, void* work, cudaStream_t st) {
+                            void* G, long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0,
+                            int Ws = 0) {
     if (mode == MODE_U64)
         return launch_scan4<MODE_U64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st);
+                                               work, st, col0, Ws);
     if (mode == MODE_U128)
         return launch_scan4<MODE_U128, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                              work, st);
+                                              work, st, col0, Ws);
     if (dtype == BSF_U8)
         return launch_scan4<MODE_F64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st);
-    return launch_scan4<MODE_F64, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch, work, st);
+                                               work, st, col0, Ws);
+    return launch_scan4<MODE_F64, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch, work, st,
+                                         col0, Ws);
 }
 
 static bool dims_ok(int64_t H, int64_t W) {
@@ -284,7 +286,16 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
     bsf_status s = resolve_halo(c, params, kind, B, HW, o, st, &P);
     if (s != BSF_OK) return s;
     const int mode = mode_of(dtype, o.precision);
-    const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P, pitch = Wp;
+    // Rows wider than one band CTA can hold are cut into vertical strips.  The
+    // filter at a pixel depends only on f inside its footprint, so each strip is
+    // pre-integrated from the image columns it needs (its outputs +- P) and the
+    // exact integer result is the same as with one buffer.
+    const int maxw = scan_max_width(elem_bytes(mode));
+    const int Wfull = (int)W + 2 * P;
+    const int nstrip = Wfull <= maxw ? 1 : (int)((W + (maxw - 2 * P) - 1) / (maxw - 2 * P));
+    if (nstrip > 1 && maxw - 2 * P < 64) return BSF_EINVAL;
+    const int Ws = (int)((W + nstrip - 1) / nstrip);
+    const int Hp = (int)H + 2 * P, Wp = (nstrip == 1 ? (int)W : Ws) + 2 * P, pitch = Wp;
     const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
     // images per launch: whole batch entries, bounded by a 16 GiB buffer budget
     const size_t budget = (size_t)16 << 30;
@@ -296,32 +307,39 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
         const int64_t nbat = std::min<int64_t>(bchunk, B - b0);
         const int nimg = (int)(nbat * C);
         const scan_plan plan = make_scan_plan(Hp, Wp, nimg, elem_bytes(mode));
+        if (!plan.ok) return BSF_EINVAL;
         BSF_TRY(grow(&c->buf, &c->buf_bytes, per_img * nimg));
         BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
         const char* img0 = (const char*)image + (size_t)(b0 * C) * HW * esz;
-        BSF_TRY(prof_mark(c, 0, st));
-        BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf,
-                         (long long)Hp * pitch, pitch, c->work, st));
-        stencil_args a;
-        a.buf = c->buf;
-        a.buf_stride = (long long)Hp * pitch;
-        a.Hp = Hp;
-        a.Wp = Wp;
-        a.pitch = pitch;
-        a.P = P;
-        a.H = (int)H;
-        a.W = (int)W;
-        a.C = (int)C;
-        a.nimg = nimg;
-        a.params = params + (size_t)b0 * K * HW;
-        a.kind = kind;
-        a.eps = o.eps;
-        a.eta = o.eta;
-        a.out = out + (size_t)(b0 * C) * HW;
-        a.status = c->d_status;
-        BSF_TRY(prof_mark(c, 1, st));
-        BSF_TRY(launch_stencil4(mode, a, st));
-        BSF_TRY(prof_mark(c, 2, st));
+        for (int sidx = 0; sidx < nstrip; ++sidx) {
+            const int col0 = sidx * Ws;
+            const int ws = nstrip == 1 ? (int)W : std::min(Ws, (int)W - col0);
+            BSF_TRY(prof_mark(c, 0, st));
+            BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf,
+                             (long long)Hp * pitch, pitch, c->work, st, col0, nstrip == 1 ? 0 : ws));
+            stencil_args a;
+            a.col0 = col0;
+            a.Ws = nstrip == 1 ? 0 : ws;
+            a.buf = c->buf;
+            a.buf_stride = (long long)Hp * pitch;
+            a.Hp = Hp;
+            a.Wp = (nstrip == 1 ? (int)W : ws) + 2 * P;
+            a.pitch = pitch;
+            a.P = P;
+            a.H = (int)H;
+            a.W = (int)W;
+            a.C = (int)C;
+            a.nimg = nimg;
+            a.params = params + (size_t)b0 * K * HW;
+            a.kind = kind;
+            a.eps = o.eps;
+            a.eta = o.eta;
+            a.out = out + (size_t)(b0 * C) * HW;
+            a.status = c->d_status;
+            BSF_TRY(prof_mark(c, 1, st));
+            BSF_TRY(launch_stencil4(mode, a, st));
+            BSF_TRY(prof_mark(c, 2, st));
+        }
     }
     if (o.strict) {
         unsigned h = 0;

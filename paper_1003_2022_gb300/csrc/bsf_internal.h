@@ -16,14 +16,19 @@ struct scan_plan {
 };
 
 scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes);
+int scan_max_width(size_t elem_bytes);  // widest buffer row one band CTA can hold
 
 // Pre-integration (RS1-RS4) of nimg images of H x W (stride img_stride
 // elements) into buffers of Hp x pitch elements (stride G_stride elements).
+// The buffer covers the image columns [col0 - P, col0 + Ws + P) (Ws <= 0:
+// the whole width, col0 = 0), f taken as zero outside the image.
 template <int MODE, class InT>
 cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
-                         long long G_stride, int pitch, void* work, cudaStream_t st);
+                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0, int Ws = 0);
 
 struct stencil_args {
+    int col0 = 0;          // first output column of the strip the buffer covers
+    int Ws = 0;            // its width (0: the whole image)
     const void* buf;
     long long buf_stride;  // elements between consecutive images' buffers
     int Hp, Wp, pitch, P, H, W;

@@ -20,6 +20,12 @@
 // |d| + eps <= w <= min(a, c) - eps.  (The paper pivots p4 = 1 and enumerates
 // the real roots of its cubic zeta'(t); both give the same minimiser.)
 //
+// In FP32 a component much smaller than the largest is a difference of terms
+// of the size of the covariance and loses its relative accuracy; where the
+// kernel is also small (largest p below 500 px^2), so that the filter is
+// sensitive to that loss, the pixel is re-solved in FP64 (map4_refine64),
+// starting from the FP32 root.
+//
 // Elongations beyond Prop. 3.1's bound U(theta) = (1 + |sin 2t| + |cos 2t|)^2
 // / (2 |sin 2t| |cos 2t|) are lowered to (1 - eta) U keeping the size
 // s = lambda_max + lambda_min and the orientation (flag bit 0).  If p >= eps
@@ -34,6 +40,79 @@ struct map4_result {
     float a[4];
     int flag;
 };
+
+// sin and cos of x in [0, 2 pi) in FP64: reduction by pi/2 with a two-part
+// constant, then the Taylor series of sin and cos on [-pi/4, pi/4] to degree
+// 15 / 16 (truncation below 1e-16).
+__device__ __forceinline__ void map4_sincos64(double x, double& sn, double& cs) {
+    const double PIO2_HI = 1.5707963267948966, PIO2_LO = 6.123233995736766e-17;
+    const double k = rint(x * 0.63661977236758134);
+    const double r = fma(-k, PIO2_LO, fma(-k, PIO2_HI, x));
+    const double r2 = r * r;
+    const double s = r * (1.0 + r2 * (-1.0 / 6 + r2 * (1.0 / 120 + r2 * (-1.0 / 5040 + r2 * (1.0 / 362880 + r2 *
+                     (-1.0 / 39916800 + r2 * (1.0 / 6227020800.0 + r2 * (-1.0 / 1307674368000.0))))))));
+    const double c = 1.0 + r2 * (-0.5 + r2 * (1.0 / 24 + r2 * (-1.0 / 720 + r2 * (1.0 / 40320 + r2 * (-1.0 / 3628800 +
+                     r2 * (1.0 / 479001600.0 + r2 * (-1.0 / 87178291200.0 + r2 * (1.0 / 20922789888000.0))))))));
+    const int q = ((int)k) & 3;
+    sn = q == 0 ? s : (q == 1 ? c : (q == 2 ? -s : -c));
+    cs = q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
+}
+
+// FP64 re-solve of one pixel, started from the FP32 root w32.  Used where a
+// component of p is small compared with the largest: there FP32 loses it to
+// cancellation (it is a difference of terms of the size of the covariance),
+// and the filter is sensitive to it because two widths are tiny.
+__device__ __noinline__ void map4_refine64(int kind, float v0, float v1, float v2, float eps, float eta, bool clamp,
+                                           float w32, float* pk) {
+    double c1, c2, c3;
+    if (kind == BSF_PARAM_COV && !clamp) {
+        c1 = 24.0 * v0;
+        c2 = 24.0 * v1;
+        c3 = 24.0 * v2;
+    } else {
+        double lmax, lmin, s2, cc2;
+        if (kind == BSF_PARAM_SRT) {
+            lmax = (double)v0 * (double)v0;
+            lmin = lmax / (double)v1;
+            map4_sincos64(fmod(2.0 * (double)v2, 6.283185307179586476925), s2, cc2);
+            if (s2 == 0.0 && cc2 == 0.0) cc2 = 1.0;
+        } else {
+            const double a = v0, b = v1, c = v2;
+            const double D = sqrt((a - c) * (a - c) + 4.0 * b * b);
+            lmax = 0.5 * (a + c + D);
+            lmin = (a * c - b * b) / lmax;
+            cc2 = D > 0.0 ? (a - c) / D : 1.0;
+            s2 = D > 0.0 ? 2.0 * b / D : 0.0;
+        }
+        if (clamp) {
+            const double as = fabs(s2), ac = fabs(cc2);
+            const double U = (1.0 + as + ac) * (1.0 + as + ac) / (2.0 * as * ac);
+            const double rc = (1.0 - (double)eta) * U, s = lmax + lmin;
+            lmin = s / (1.0 + rc);
+            lmax = s - lmin;
+        }
+        const double m = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+        c1 = 24.0 * (m + d * cc2);
+        c2 = 24.0 * (d * s2);
+        c3 = 24.0 * (m - d * cc2);
+    }
+    const double a = 0.5 * c1, c = 0.5 * c3, hd = 0.5 * c2, e = eps;
+    const double lo = fabs(hd) + e, hi = fmin(a, c) - e;
+    const double s1 = a + c, s2 = a * a + c * c, s3 = a * a * a + c * c * c, d2 = hd * hd;
+    const double k1 = 4.0 * s2 + 8.0 * d2, k0 = s3 + s1 * d2;
+    double w = w32;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double g = ((8.0 * w - 6.0 * s1) * w + k1) * w - k0;
+        const double gp = (24.0 * w - 12.0 * s1) * w + k1;
+        w -= g / gp;
+    }
+    w = fmin(fmax(w, lo), hi);
+    pk[0] = (float)(a - w);
+    pk[1] = (float)(w + hd);
+    pk[2] = (float)(c - w);
+    pk[3] = (float)(w - hd);
+}
 
 // kind: BSF_PARAM_COV (v0,v1,v2) = (C11, C12, C22) or BSF_PARAM_SRT (sigma, rho, theta)
 __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, float v2, float eps, float eta) {
@@ -98,6 +177,7 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
     const float cmin = fminf(ha, hc);
     const float hi = cmin - eps;
     float p1, p2, p3, p4;
+    float w_root = 0.f;
     if (!(lo <= hi)) {
         const float w = 0.5f * (lo + hi);
         p1 = fmaxf(ha - w, eps);
@@ -120,6 +200,7 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
         z -= __fdividef(z * z * z + P * z + Q, 3.f * z * z + P);  // one Newton step against rounding
         float w = sc * (z + 0.25f * (an + cn));
         w = fminf(fmaxf(w, lo), hi);
+        w_root = w;
         // each component from the nearer end of the interval, so that small
         // components keep their relative accuracy
         if (w - lo <= hi - w) {
@@ -134,6 +215,23 @@ __device__ __forceinline__ map4_result map4_solve(int kind, float v0, float v1, 
             p3 = (hc - cmin) + eps + v;
             p2 = w + hd;
             p4 = w - hd;
+        }
+    }
+    if (!(R.flag & 2)) {
+        // a component well below the largest and not pinned at eps: redo in FP64
+        const float pmax = fmaxf(fmaxf(p1, p2), fmaxf(p3, p4));
+        const float thr = 0.05f * pmax, pin = 1.0001f * eps;
+        const bool small = (p1 < thr && p1 > pin) || (p2 < thr && p2 > pin) || (p3 < thr && p3 > pin) ||
+                           (p4 < thr && p4 > pin);
+        // only small kernels (widths below ~22 px) are sensitive enough to need it:
+        // with fewer lattice points the output depends more sharply on the widths
+        if (small && pmax < 500.f) {
+            float pk[4];
+            map4_refine64(kind, v0, v1, v2, eps, eta, clamp, w_root, pk);
+            p1 = pk[0];
+            p2 = pk[1];
+            p3 = pk[2];
+            p4 = pk[3];
         }
     }
     R.a[0] = sqrtf(fmaxf(p1, 0.f));

@@ -79,17 +79,17 @@ __device__ __forceinline__ void load_scales(int kind, const float* __restrict__ 
 
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restrict__ buf, long long buf_stride, int Hp,
-                                                         int Wp, int pitch, int P, int H, int W, int C,
-                                                         const float* __restrict__ params, float eps, float eta,
-                                                         float* __restrict__ out, unsigned* status) {
+                                                         int Wp, int pitch, int P, int H, int W, int C, int col0,
+                                                         int col1, const float* __restrict__ params, float eps,
+                                                         float eta, float* __restrict__ out, unsigned* status) {
     typedef typename mode_traits<MODE>::T T;
     constexpr int ACC = mode_traits<MODE>::ACC_BITS;
     constexpr int VAL = mode_traits<MODE>::VAL_BITS;
     constexpr int FRAC = mode_traits<MODE>::FRAC_BITS;
-    const int n1 = blockIdx.x * 32 + threadIdx.x;
+    const int n1 = col0 + blockIdx.x * 32 + threadIdx.x;
     const int n2 = blockIdx.y * 8 + threadIdx.y;
     const int im = blockIdx.z;
-    if (n1 >= W || n2 >= H) return;
+    if (n1 >= col1 || n2 >= H) return;
     const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
     const int K = (KIND == BSF_PARAM_SCALES) ? 4 : 3;
     const float* pr = params + (size_t)(im / C) * K * HW;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restric
     const int one = 1 << q;
     const int sh1 = q + 1;
     const T* G = (const T*)buf + (size_t)im * buf_stride;
-    const int bx = n1 + P, by = n2 + P;
+    const int bx = n1 - col0 + P, by = n2 + P;
     // S = 2^(2q+4) sum_i s_i F(y_i) = 2^(2q+2) SK + 2^(q+1) SL + SQ: the terms of
     // each power of two are summed over the taps first and shifted once
     T SK = T(0), SL = T(0), SQ = T(0);
@@ -182,13 +182,13 @@ __global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restric
 
 template <int KIND>
 __global__ void __launch_bounds__(256) k_stencil4_f64(const double* __restrict__ buf, long long buf_stride, int Hp,
-                                                       int Wp, int pitch, int P, int H, int W, int C,
-                                                       const float* __restrict__ params, float eps, float eta,
-                                                       float* __restrict__ out, unsigned* status) {
-    const int n1 = blockIdx.x * 32 + threadIdx.x;
+                                                       int Wp, int pitch, int P, int H, int W, int C, int col0,
+                                                       int col1, const float* __restrict__ params, float eps,
+                                                       float eta, float* __restrict__ out, unsigned* status) {
+    const int n1 = col0 + blockIdx.x * 32 + threadIdx.x;
     const int n2 = blockIdx.y * 8 + threadIdx.y;
     const int im = blockIdx.z;
-    if (n1 >= W || n2 >= H) return;
+    if (n1 >= col1 || n2 >= H) return;
     const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
     const int K = (KIND == BSF_PARAM_SCALES) ? 4 : 3;
     const float* pr = params + (size_t)(im / C) * K * HW;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_stencil4_f64(const double* __restrict__
     const double a1 = fa1, a3 = fa3;
     const double a2p = (double)fa2 * 0.70710678118654752440, a4p = (double)fa4 * 0.70710678118654752440;
     const double* G = buf + (size_t)im * buf_stride;
-    const int bx = n1 + P, by = n2 + P;
+    const int bx = n1 - col0 + P, by = n2 + P;
     double S = 0.0;
     bool bad = false;
 #pragma unroll
@@ -290,16 +290,20 @@ __global__ void k_extent4(const float* __restrict__ params, int kind, long long 
 
 template <int MODE, int KIND>
 static void launch_exact(const stencil_args& a, cudaStream_t st) {
-    dim3 blk(32, 8), grd((a.W + 31) / 32, (a.H + 7) / 8, a.nimg);
+    const int ws = a.Ws > 0 ? a.Ws : a.W;
+    dim3 blk(32, 8), grd((ws + 31) / 32, (a.H + 7) / 8, a.nimg);
     k_stencil4_exact<MODE, KIND><<<grd, blk, 0, st>>>(a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H, a.W, a.C,
-                                                      a.params, a.eps, a.eta, a.out, a.status);
+                                                      a.col0, min(a.col0 + ws, a.W), a.params, a.eps, a.eta, a.out,
+                                                      a.status);
 }
 
 template <int KIND>
 static void launch_f64(const stencil_args& a, cudaStream_t st) {
-    dim3 blk(32, 8), grd((a.W + 31) / 32, (a.H + 7) / 8, a.nimg);
+    const int ws = a.Ws > 0 ? a.Ws : a.W;
+    dim3 blk(32, 8), grd((ws + 31) / 32, (a.H + 7) / 8, a.nimg);
     k_stencil4_f64<KIND><<<grd, blk, 0, st>>>((const double*)a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H,
-                                              a.W, a.C, a.params, a.eps, a.eta, a.out, a.status);
+                                              a.W, a.C, a.col0, min(a.col0 + ws, a.W), a.params, a.eps, a.eta,
+                                              a.out, a.status);
 }
 
 template <int MODE>

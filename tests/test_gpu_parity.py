@@ -251,3 +251,23 @@ def test_unsupported_n_and_bad_args():
     rc = L.bsf_filter(api.context(dev), 0, L.BSF_U8, 1, 1, 8, 8, 4, p.data_ptr(), L.BSF_PARAM_SRT, None,
                       p.data_ptr(), 0)
     assert rc == L.BSF_EINVAL
+
+
+@pytest.mark.parametrize("dtype,W", [("f32", 3300), ("u8", 4200)])
+def test_wide_images_are_filtered_in_strips(dtype, W):
+    """Rows wider than one band CTA holds (float32: 3072 buffer columns, uint8:
+    4096) are cut into vertical strips; results match the oracle everywhere,
+    including the pixels on both sides of every strip seam."""
+    H = 40
+    f = synth.image(H, W, seed=31, dtype=dtype)
+    p = synth.srt_field(H, W, seed=31, sigma=(1.0, 4.0), rho=(1.0, 6.0))
+    out, st = _run(f, p, "srt", max_scale=4.0)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    rng = np.random.default_rng(3)
+    cols = np.concatenate([rng.integers(0, W, 60), np.arange(W // 2 - 60, W // 2 + 60, 7),
+                           np.arange(1300, 1700, 13), np.arange(2000, 2300, 11), [0, W - 1]]) % W
+    rows = rng.integers(0, H, cols.size)
+    idx = rows * W + cols
+    ref = O.direct4(f.astype(np.float64), a, idx)
+    assert _nerr(out.ravel()[idx], ref) < TOL

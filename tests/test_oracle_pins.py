@@ -431,3 +431,29 @@ def test_map_invalid_covariance():
     a, fl = O.map4(np.array([[1.0, np.nan], [2.0, 0.0], [1.0, 1.0]]), O.KIND_COV)
     assert fl[0] == 4 and fl[1] == 4
     assert np.all(np.isnan(a))
+
+
+# --------------------------------------------------------------- O-adjoint / FD gradient
+def test_adjoint_is_transpose_of_direct():
+    """<g, K f> = <K^T g, f> for the space-variant operator (independent loops)."""
+    H, W = 13, 15
+    a = RNG.uniform(0.6, 4.0, size=(4, H, W))
+    f = RNG.standard_normal((H, W))
+    g = RNG.standard_normal((H, W))
+    lhs = float(np.sum(g * O.direct4(f, a)))
+    rhs = float(np.sum(O.adjoint4(g, a, np.arange(H * W)).reshape(H, W) * f))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_fd_scale_gradient_closed_form_separable_limit():
+    """a = (a1, d, a3, d), d -> 0, no lattice point on the box edge: fbar =
+    sum_{3x3} f / (a1 a3), so dfbar/da1 = -fbar/a1 and dfbar/da3 = -fbar/a3."""
+    H, W = 9, 11
+    f = RNG.random((H, W))
+    d = 1e-6
+    a = np.broadcast_to(np.array([2.5, d, 3.5, d])[:, None, None], (4, H, W)).copy()
+    idx = np.array([3 * W + 4, 5 * W + 6, 4 * W + 5])
+    fb = O.direct4(f, a, idx)
+    fd = O.direct4_grad_fd(f, a, idx, h=1e-3)
+    assert np.allclose(fd[0], -fb / 2.5, rtol=1e-5)
+    assert np.allclose(fd[2], -fb / 3.5, rtol=1e-5)
