@@ -92,6 +92,10 @@ typedef struct {
                          (one stream synchronisation) */
     float max_scale;  /* optional bound on the largest footprint: for SCALES the largest a_k,
                          for COV/SRT the largest sqrt(lambda_max) (px); 0 = unknown */
+    int iterations;   /* m >= 1 (default 1): filter with the iterated box spline of Sec. 3.3,
+                         i.e. run the path m times with the scale vector a/sqrt(m) (the
+                         covariance of each pass is C/m, of the m passes together C).
+                         Passes after the first take the float32 output of the previous one. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -187,7 +191,7 @@ bsf_status bsf_profile_end(bsf_ctx* ctx, double* ms_preintegrate, double* ms_ste
  * fit).  opts is required and must give opts->halo or opts->max_scale.
  * Runs on the current device, asynchronously on `stream`; the first call on a
  * device looks up the array's device address, so make it before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * capture.  opts->iterations must be 1.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU race and must be serialised by the caller.
  * There is no device status word: pixels with invalid scales or with taps
  * outside the buffer are NaN. */

@@ -13,6 +13,7 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
   (Eq. SVF_2D with the Dirac-comb image used to derive Eq. keyeqn).
 * ``preint4_i64`` / ``preint4_f64``: Algorithm 1 step 2 (Sec. 3.1, RS1-RS4).
 * ``stencil4``: Algorithm 1 step 3 (Table 1, Eq. final_eqn, App. F).
+* ``direct4_iterated``: the iterated box-spline filter of Sec. 3.3.
 * ``adjoint4``: the transpose of the plain definition (gradient with respect
   to the image); ``direct4_grad_fd``: central differences of ``direct4`` with
   respect to the scales.
@@ -156,6 +157,16 @@ def adjoint4(g, a, idx) -> np.ndarray:
     ii, n = _idx(idx, H * W)
     out = np.empty(n)
     _load().bo_adjoint4(_ptr(g, _dp), H, W, _ptr(a, _dp), float(np.max(a)), _ptr(ii, _i64p), n, _ptr(out, _dp))
+    return out
+
+
+def direct4_iterated(f, a, m: int) -> np.ndarray:
+    """Sec. 3.3: the m-fold iterated filter, i.e. the plain definition applied m
+    times, each pass with the scale vectors a(n) / sqrt(m)."""
+    a = _d(a) / np.sqrt(m)
+    out = _d(f)
+    for _ in range(m):
+        out = direct4(out, a)
     return out
 
 

@@ -50,6 +50,7 @@ class bsf_opts(ctypes.Structure):
         ("strict", ctypes.c_int),
         ("halo", ctypes.c_int),
         ("max_scale", ctypes.c_float),
+        ("iterations", ctypes.c_int),
     ]
 
 

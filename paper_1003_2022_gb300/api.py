@@ -40,8 +40,10 @@ def _stream_ptr(stream) -> int:
     return int(s.cuda_stream)
 
 
-def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False) -> L.bsf_opts:
+def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False,
+              iterations=1) -> L.bsf_opts:
     o = L.default_opts()
+    o.iterations = int(iterations)
     o.precision = _PREC[precision]
     o.halo = int(halo)
     o.max_scale = float(max_scale)
@@ -63,8 +65,11 @@ def _as4d(image: torch.Tensor) -> torch.Tensor:
 
 def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int = 4, precision: str = "exact",
            halo: int = 0, max_scale: float = 0.0, eps: float = 1e-3, eta: float = 1e-3, strict: bool = False,
-           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k)."""
+           out: torch.Tensor | None = None, stream=None, iterations: int = 1) -> torch.Tensor:
+    """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k).
+
+    iterations = m > 1 applies the iterated box spline of Sec. 3.3 (m passes
+    with the widths a / sqrt(m))."""
     img = _as4d(image)
     if not img.is_cuda:
         raise ValueError("image must be a CUDA tensor")
@@ -82,7 +87,7 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
     if out is None:
         out = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device)
     dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
-    opts = make_opts(precision, halo, max_scale, eps, eta, strict)
+    opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations)
     rc = L.bsf_filter(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), _KINDS[kind],
                       opts, out.data_ptr(), _stream_ptr(stream))
     L.check(rc, "bsf_filter")

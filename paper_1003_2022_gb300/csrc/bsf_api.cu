@@ -21,6 +21,8 @@ struct bsf_ctx {
     size_t work_bytes;
     void* hbuf;              // FP64 scatter buffers of the adjoint
     size_t hbuf_bytes;
+    void* iter;              // scaled fields and intermediate images of the iterated filter
+    size_t iter_bytes;
     std::mutex mu;
     bool profiling;
     size_t prof_used;                                // event triples recorded since begin
@@ -89,6 +91,7 @@ void bsf_default_opts(bsf_opts* o) {
     o->strict = 0;
     o->halo = 0;
     o->max_scale = 0.f;
+    o->iterations = 1;
 }
 
 const char* bsf_status_string(bsf_status s) {
@@ -124,6 +127,8 @@ bsf_status bsf_create(bsf_ctx** ctx, int device) {
     c->work_bytes = 0;
     c->hbuf = nullptr;
     c->hbuf_bytes = 0;
+    c->iter = nullptr;
+    c->iter_bytes = 0;
     c->profiling = false;
     c->prof_used = 0;
     cudaError_t e = cudaMalloc((void**)&c->d_status, 2 * sizeof(unsigned));
@@ -149,6 +154,7 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->buf) cudaFree(c->buf);
     if (c->work) cudaFree(c->work);
     if (c->hbuf) cudaFree(c->hbuf);
+    if (c->iter) cudaFree(c->iter);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& t : c->prof)
         for (int i = 0; i < 3; ++i) cudaEventDestroy(t[i]);
@@ -267,20 +273,10 @@ static bool dims_ok(int64_t H, int64_t W) {
     return H > 0 && W > 0 && H <= (1 << 20) && W <= (1 << 20);
 }
 
-bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
-                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
-    if (!c || !image || !params || !out) return BSF_EINVAL;
-    if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
-    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
-    if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
-    if (N != 4) return BSF_EUNSUPPORTED;
-    bsf_opts o;
-    bsf_default_opts(&o);
-    if (opts) o = *opts;
-    if (o.precision != BSF_PREC_EXACT && o.precision != BSF_PREC_FP64) return BSF_EINVAL;
-    std::lock_guard<std::mutex> lock(c->mu);
-    BSF_TRY(cudaSetDevice(c->device));
-    cudaStream_t st = (cudaStream_t)stream;
+// one pass of the filter (the caller holds the context lock)
+static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                              const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
+                              float ascale = 1.f) {
     const int64_t HW = H * W;
     int P = 0;
     bsf_status s = resolve_halo(c, params, kind, B, HW, o, st, &P);
@@ -334,6 +330,7 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
             a.kind = kind;
             a.eps = o.eps;
             a.eta = o.eta;
+            a.ascale = ascale;
             a.out = out + (size_t)(b0 * C) * HW;
             a.status = c->d_status;
             BSF_TRY(prof_mark(c, 1, st));
@@ -341,6 +338,50 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
             BSF_TRY(prof_mark(c, 2, st));
         }
     }
+    return BSF_OK;
+}
+
+bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
+                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
+    if (!c || !image || !params || !out) return BSF_EINVAL;
+    if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
+    if (N != 4) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != BSF_PREC_EXACT && o.precision != BSF_PREC_FP64) return BSF_EINVAL;
+    if (o.iterations < 1 || o.iterations > 64) return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t HW = H * W;
+    bsf_status s;
+    if (o.iterations == 1) {
+        s = filter_pass(c, image, dtype, B, C, H, W, params, kind, o, out, st);
+    } else {
+        // iterated box spline (Sec. 3.3): m passes, each with the widths a / sqrt(m)
+        // of the optimal scale vector a (the mapped widths are scaled, so the
+        // covariance of each pass is C / m)
+        const int m = o.iterations;
+        const float asc = 1.f / sqrtf((float)m);
+        const size_t ibytes = (size_t)B * C * HW * sizeof(float);
+        BSF_TRY(grow(&c->iter, &c->iter_bytes, ibytes));
+        float* tmp = (float*)c->iter;
+        bsf_opts oi = o;
+        if (o.max_scale > 0.f) oi.max_scale = o.max_scale * asc;
+        // the halo of the unscaled field covers the scaled one; passes alternate
+        // between tmp and out so that the last one lands in out
+        float* dst = (m % 2 == 0) ? tmp : out;
+        s = filter_pass(c, image, dtype, B, C, H, W, params, kind, oi, dst, st, asc);
+        for (int it = 1; it < m && s == BSF_OK; ++it) {
+            float* src = dst;
+            dst = (src == tmp) ? out : tmp;
+            s = filter_pass(c, src, BSF_F32, B, C, H, W, params, kind, oi, dst, st, asc);
+        }
+    }
+    if (s != BSF_OK) return s;
     if (o.strict) {
         unsigned h = 0;
         BSF_TRY(cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

@@ -37,6 +37,7 @@ struct stencil_args {
     const float* params;   // parameter planes of the first image's field
     int kind;
     float eps, eta;
+    float ascale = 1.f;    // widths multiplier (1/sqrt(m) in a pass of the m-fold iterated filter)
     float* out;
     unsigned* status;
 };

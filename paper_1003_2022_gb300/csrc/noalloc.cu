@@ -39,6 +39,7 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
     if (opts->precision != BSF_PREC_EXACT && opts->precision != BSF_PREC_FP64) return BSF_EINVAL;
+    if (opts->iterations > 1) return BSF_EINVAL;
     if (N != 4) return BSF_EUNSUPPORTED;
     // the halo must come from the options (no device reduction, which would need a result word)
     int P = opts->halo;

@@ -81,7 +81,8 @@ template <int MODE, int KIND>
 __global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restrict__ buf, long long buf_stride, int Hp,
                                                          int Wp, int pitch, int P, int H, int W, int C, int col0,
                                                          int col1, const float* __restrict__ params, float eps,
-                                                         float eta, float* __restrict__ out, unsigned* status) {
+                                                         float eta, float ascale, float* __restrict__ out,
+                                                         unsigned* status) {
     typedef typename mode_traits<MODE>::T T;
     constexpr int ACC = mode_traits<MODE>::ACC_BITS;
     constexpr int VAL = mode_traits<MODE>::VAL_BITS;
@@ -96,6 +97,10 @@ __global__ void __launch_bounds__(256, 3) k_stencil4_exact(const void* __restric
     float a1, a2, a3, a4;
     int mflag;
     load_scales<MODE>(KIND, pr, HW, p, eps, eta, a1, a2, a3, a4, mflag);
+    a1 *= ascale;  // 1, or 1/sqrt(m) for a pass of the m-fold iterated filter
+    a2 *= ascale;
+    a3 *= ascale;
+    a4 *= ascale;
     float* o = out + (size_t)im * HW + p;
     if (mflag & 1) raise_status(status, BSF_EINFEASIBLE);
     if (!(a1 > 0.f && a2 > 0.f && a3 > 0.f && a4 > 0.f) || !(a1 < 1e30f && a2 < 1e30f && a3 < 1e30f && a4 < 1e30f)) {
@@ -184,7 +189,8 @@ template <int KIND>
 __global__ void __launch_bounds__(256) k_stencil4_f64(const double* __restrict__ buf, long long buf_stride, int Hp,
                                                        int Wp, int pitch, int P, int H, int W, int C, int col0,
                                                        int col1, const float* __restrict__ params, float eps,
-                                                       float eta, float* __restrict__ out, unsigned* status) {
+                                                       float eta, float ascale, float* __restrict__ out,
+                                                       unsigned* status) {
     const int n1 = col0 + blockIdx.x * 32 + threadIdx.x;
     const int n2 = blockIdx.y * 8 + threadIdx.y;
     const int im = blockIdx.z;
@@ -195,6 +201,10 @@ __global__ void __launch_bounds__(256) k_stencil4_f64(const double* __restrict__
     float fa1, fa2, fa3, fa4;
     int mflag;
     load_scales<MODE_F64>(KIND, pr, HW, p, eps, eta, fa1, fa2, fa3, fa4, mflag);
+    fa1 *= ascale;
+    fa2 *= ascale;
+    fa3 *= ascale;
+    fa4 *= ascale;
     float* o = out + (size_t)im * HW + p;
     if (mflag & 1) raise_status(status, BSF_EINFEASIBLE);
     if (!(fa1 > 0.f && fa2 > 0.f && fa3 > 0.f && fa4 > 0.f) ||
@@ -293,8 +303,8 @@ static void launch_exact(const stencil_args& a, cudaStream_t st) {
     const int ws = a.Ws > 0 ? a.Ws : a.W;
     dim3 blk(32, 8), grd((ws + 31) / 32, (a.H + 7) / 8, a.nimg);
     k_stencil4_exact<MODE, KIND><<<grd, blk, 0, st>>>(a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H, a.W, a.C,
-                                                      a.col0, min(a.col0 + ws, a.W), a.params, a.eps, a.eta, a.out,
-                                                      a.status);
+                                                      a.col0, min(a.col0 + ws, a.W), a.params, a.eps, a.eta, a.ascale,
+                                                      a.out, a.status);
 }
 
 template <int KIND>
@@ -303,7 +313,7 @@ static void launch_f64(const stencil_args& a, cudaStream_t st) {
     dim3 blk(32, 8), grd((ws + 31) / 32, (a.H + 7) / 8, a.nimg);
     k_stencil4_f64<KIND><<<grd, blk, 0, st>>>((const double*)a.buf, a.buf_stride, a.Hp, a.Wp, a.pitch, a.P, a.H,
                                               a.W, a.C, a.col0, min(a.col0 + ws, a.W), a.params, a.eps, a.eta,
-                                              a.out, a.status);
+                                              a.ascale, a.out, a.status);
 }
 
 template <int MODE>

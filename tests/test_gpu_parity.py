@@ -271,3 +271,16 @@ def test_wide_images_are_filtered_in_strips(dtype, W):
     idx = rows * W + cols
     ref = O.direct4(f.astype(np.float64), a, idx)
     assert _nerr(out.ravel()[idx], ref) < TOL
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_iterated_filter_matches_oracle(m):
+    """Sec. 3.3: m passes of the algorithm with a / sqrt(m) (a from the map)."""
+    H, W = 40, 52
+    f = synth.image(H, W, seed=9, dtype="f32")
+    p = synth.srt_field(H, W, seed=9, sigma=(1.5, 6.0), rho=(1.0, 5.0))
+    out, st = _run(f, p, "srt", max_scale=6.0, iterations=m)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    ref = O.direct4_iterated(f.astype(np.float64), a, m)
+    assert _nerr(out, ref) < TOL

@@ -457,3 +457,37 @@ def test_fd_scale_gradient_closed_form_separable_limit():
     fd = O.direct4_grad_fd(f, a, idx, h=1e-3)
     assert np.allclose(fd[0], -fb / 2.5, rtol=1e-5)
     assert np.allclose(fd[2], -fb / 3.5, rtol=1e-5)
+
+
+def _corr_with_gaussian(a, m, h=0.025):
+    """Normalised correlation of beta^{4,m}_{a/sqrt(m)} (m-fold continuous
+    self-convolution, on a fine grid) with the Gaussian of the same covariance."""
+    from scipy.signal import fftconvolve
+    a = np.asarray(a, float) / np.sqrt(m)
+    hx, hy = _support_extent(a)
+    R = max(hx, hy) * m + 1.0
+    xs = np.arange(-R, R + h / 2, h)
+    X1, X2 = np.meshgrid(xs, xs)
+    b = O.beta4_grid(a, X1, X2) * h * h
+    bm = b
+    for _ in range(m - 1):
+        bm = fftconvolve(bm, b, mode="same")
+    C = O.covariance4(a) * m
+    Ci = np.linalg.inv(C)
+    g = np.exp(-0.5 * (Ci[0, 0] * X1 * X1 + 2 * Ci[0, 1] * X1 * X2 + Ci[1, 1] * X2 * X2))
+    return float(np.sum(bm * g) / np.sqrt(np.sum(bm * bm) * np.sum(g * g)))
+
+
+def test_iterated_splines_approach_the_gaussian():
+    """Sec. 3.3 / Fig. errorplots: at the critical orientation 22.5 deg the
+    correlation of the optimal box spline with the target Gaussian is about
+    95 % at its worst and rises to about 99 % for the twice-iterated spline."""
+    th = np.pi / 8
+    worst = {1: 1.0, 2: 1.0}
+    for rho in (1.0, 2.0, 3.0, 4.0, 5.0):
+        a, fl = O.map4(np.array([[3.0], [rho], [th]]), O.KIND_SRT)
+        for m in (1, 2):
+            worst[m] = min(worst[m], _corr_with_gaussian(a[:, 0], m))
+    assert 0.93 < worst[1] < 0.975, worst
+    assert worst[2] > 0.985, worst
+    assert worst[2] > worst[1]
