@@ -43,6 +43,28 @@ SIGMA_MAX = 32.0
 # offset, cell index and the two truncations, 15 for bounds and clamping,
 # 6 for addresses: 124 per tap, 16 taps
 STENCIL_INT_OPS_PER_PX = 16 * 124
+# the same count for the 128-bit fixed-point stencil (float32 images): four
+# 32-bit words per addition (112), eight 32x32 partial products per 128x32
+# product (88), two words per product sum and accumulator (28), 32 for
+# position, truncation, bounds and addresses: 260 per tap
+STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
+# Benchmarked workloads: (params kind, largest sigma or scale, forward+backward).
+BENCH_WORKLOADS = {
+    "u2048_u8_n4": ("srt", 32.0, False),
+    "u2048_f32_n4": ("srt", 32.0, False),
+    "b4c3_4096_f32_n4": ("srt", 48.0, False),
+    "b8_1024_f32_scales": ("scales", 24.0, True),
+}
+WORKLOAD_TEXT = {
+    "u2048_u8_n4": "2048x2048 u8 image (uniform 0-255), N=4, per-pixel (sigma 1-32 px, rho 1-8 clamped to "
+                   "Prop. 3.1, theta from a smooth vector field), exact int64 path",
+    "u2048_f32_n4": "2048x2048 f32 copy of the u8 image, N=4, sigma 1-32 px, rho 1-8, theta from a smooth "
+                    "vector field, exact 128-bit fixed-point path",
+    "b4c3_4096_f32_n4": "batch 4 x 3 channels x 4096x4096 f32 (uniform + 3 gratings), sigma 2-48 px, rho 1-6, "
+                        "theta uniform, filtered with N=4 (N=6 is not built), exact 128-bit fixed-point path",
+    "b8_1024_f32_scales": "batch 8 x 1024x1024 f32, learnable scale field a_k in [1,24]; one step = forward "
+                          "filter + backward (gradients for image and scales)",
+}
 STENCIL_SOURCES = ["paper_1003_2022_gb300/csrc/stencil4.cu", "paper_1003_2022_gb300/csrc/map4.cuh",
                    "paper_1003_2022_gb300/csrc/bsf_common.cuh"]
 
@@ -145,9 +167,13 @@ def alu_peak_tops():
     return 152 * 128 * 2.070e9 / 1e12
 
 
-def _inputs(size=None):
+def _inputs(size=None, workload=WORKLOAD):
+    """(B, C, H, W) image and (B, K, H, W) parameter planes of a workload."""
     from paper_1003_2022_gb300 import synth
-    return synth.workload_inputs(WORKLOAD, seed=0, H=size, W=size)
+    if synth.WORKLOADS[workload]["B"] == 1 and "scales" not in synth.WORKLOADS[workload]:
+        f, p = synth.workload_inputs(workload, seed=0, H=size, W=size)
+        return f[None, None], p[None]
+    return synth.batch_inputs(workload, seed=0, H=size, W=size)
 
 
 def cpu_baseline_run(f, p, crop=192, seed=0):
@@ -175,6 +201,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     f, p = _inputs()
+    f, p = f[0, 0], p[0]
     import oracle
     oracle.build()
     for i in range(args.warmup):
@@ -212,22 +239,34 @@ def run_ours(args):
     from paper_1003_2022_gb300 import _lib as L
     from paper_1003_2022_gb300 import api
 
-    f_np, p_np = _inputs(args.size)
-    H, W = f_np.shape
+    kind_name, smax, train = BENCH_WORKLOADS[args.workload]
+    f_np, p_np = _inputs(args.size, args.workload)
+    B, C, H, W = f_np.shape
+    u8 = f_np.dtype == np.uint8
+    dtype = L.BSF_U8 if u8 else L.BSF_F32
+    kind = L.BSF_PARAM_SRT if kind_name == "srt" else L.BSF_PARAM_SCALES
     f = torch.from_numpy(f_np).to(dev)
     p = torch.from_numpy(p_np).to(dev)
-    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    out = torch.empty((B, C, H, W), dtype=torch.float32, device=dev)
+    if train:
+        gout = torch.from_numpy(np.random.default_rng(3).standard_normal((B, C, H, W)).astype(np.float32)).to(dev)
+        gimg = torch.empty((B, C, H, W), dtype=torch.float32, device=dev)
+        gsc = torch.empty_like(p)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     ctx = api.context(dev)
-    opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=SIGMA_MAX)
+    opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=smax)
     stream = torch.cuda.current_stream(dev)
     sptr = int(stream.cuda_stream)
 
     def step(img=f, prm=p, o=out):
-        rc = L.bsf_filter(ctx, img.data_ptr(), L.BSF_U8, 1, 1, H, W, 4, prm.data_ptr(), L.BSF_PARAM_SRT, opts,
-                          o.data_ptr(), sptr)
+        rc = L.bsf_filter(ctx, img.data_ptr(), dtype, B, C, H, W, 4, prm.data_ptr(), kind, opts, o.data_ptr(), sptr)
         if rc != 0:
             raise L.BsfError(rc, "bsf_filter")
+        if train:
+            rc = L.bsf_filter_backward(ctx, img.data_ptr(), dtype, B, C, H, W, 4, prm.data_ptr(), gout.data_ptr(),
+                                       gimg.data_ptr(), gsc.data_ptr(), opts, sptr)
+            if rc != 0:
+                raise L.BsfError(rc, "bsf_filter_backward")
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -267,10 +306,10 @@ def run_ours(args):
     sampler.stop()
     clocks = sampler.summary()
 
-    # end to end: pinned host buffers, H2D of the step's inputs, the call, D2H of the result
+    # end to end: pinned host buffers, H2D of the step's inputs, the call(s), D2H of the result
     f_h = torch.from_numpy(f_np).pin_memory()
     p_h = torch.from_numpy(p_np).pin_memory()
-    o_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    o_h = torch.empty((B, C, H, W), dtype=torch.float32).pin_memory()
     f_d = torch.empty_like(f)
     p_d = torch.empty_like(p)
     e2e_steps = max(3, min(args.steps, 50))
@@ -281,6 +320,11 @@ def run_ours(args):
         o_h.copy_(out, non_blocking=True)
     torch.cuda.synchronize(dev)
     e2e_ms = 0.0
+    d2h = out.numel() * 4
+    if train:
+        gi_h = torch.empty_like(o_h)
+        gs_h = torch.empty(tuple(p.shape), dtype=torch.float32).pin_memory()
+        d2h += gimg.numel() * 4 + gsc.numel() * 4
     for _ in range(e2e_steps):
         flush.fill_(3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -289,6 +333,9 @@ def run_ours(args):
         p_d.copy_(p_h, non_blocking=True)
         step(f_d, p_d, out)
         o_h.copy_(out, non_blocking=True)
+        if train:
+            gi_h.copy_(gimg, non_blocking=True)
+            gs_h.copy_(gsc, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
@@ -296,37 +343,57 @@ def run_ours(args):
     if status & ~(1 << L.BSF_EINFEASIBLE):
         raise RuntimeError(f"device status error {status}")
 
-    npx = H * W
+    npx = B * C * H * W
     value = ws * npx * args.steps / (t_max / 1e3) / 1e9
     e2e_value = ws * npx * e2e_steps / (e2e_ms / 1e3) / 1e9
-    st_ms = ms_st / max(nl, 1)
-    achieved = STENCIL_INT_OPS_PER_PX * npx / (st_ms / 1e3) / 1e12
+    # stencil launches in the timed region (one per strip and batch chunk of each forward call)
+    n_st = max(nl, 1)
+    st_ms = ms_st / n_st
+    ops_px = STENCIL_INT_OPS_PER_PX if u8 else STENCIL_INT_OPS_PER_PX_U128
+    px_per_launch = npx * args.steps / n_st
+    achieved = ops_px * px_per_launch / (st_ms / 1e3) / 1e12
     peak = alu_peak_tops()
-    traffic = stencil_traffic() if (H, W) == (2048, 2048) and args.precision == "exact" else None
+    traffic = stencil_traffic() if (args.workload == WORKLOAD and args.size in (None, 2048)
+                                    and args.precision == "exact") else None
+    kname = f"k_stencil4_exact<{'u64' if u8 else 'u128'},{kind_name.upper()}>"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_stencil4_exact<u64,SRT>",
-                "kernel_ms": st_ms, "preintegrate_ms": ms_pre / max(nl, 1),
+                "traffic": traffic, "kernel": kname,
+                "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
                 "peak_note": "152 SMs x 128 lanes x 2070 MHz, 32-bit integer ops (derived; an add-chain probe "
                              "reached 37.1 Tops/s, a multiply-add chain 19.1 Tops/s)",
-                "algorithmic_bytes_per_launch": (12 + 4 + 8) * H * W}
+                "int_ops_per_px": ops_px,
+                "algorithmic_bytes_per_launch": int((12 + 4 + 8 * (1 if u8 else 2)) * px_per_launch)}
+    if args.precision != "exact":
+        roofline["kernel"] = f"k_stencil4_f64<{kind_name.upper()}>"
+        roofline["note"] = "all-FP64 form: the integer op count does not apply; compare kernel_ms"
+    # kernels per forward call: 7 for the pre-integration and 1 stencil per strip/chunk; the
+    # backward adds the gradient stencil and its scans
+    launches = 8 * nl
+    if train:
+        # per batch chunk: 7 pre-integration kernels, the gradient stencil, 4 transposed scans
+        P = api.halo_for(smax, kind_name)
+        per = (H + 2 * P) * (W + 2 * P) * ((8 if u8 else 16) + 8) * C
+        chunks = -(-B // max(1, min(B, (16 << 30) // per)))
+        launches += 12 * chunks * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64" if args.precision == "exact" else "f64", "data": "synthetic",
-        "config": {"workload": f"{H}x{W} u8 image (uniform 0-255), N=4, per-pixel (sigma 1-32 px, rho 1-8 "
-                               "clamped to Prop. 3.1, theta from a smooth vector field), exact int64 path",
+        "dtype": ("int64" if u8 else "int128") if args.precision == "exact" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload] if args.size is None else
+                   f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
+                   "workload_id": args.workload,
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))},
         "roofline": roofline,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "Gpixels/s", "h2d_bytes_per_step": f_np.nbytes + p_np.nbytes,
-                "d2h_bytes_per_step": H * W * 4},
-        "gpu_launches": 8 * args.steps,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        v, dt, desc = cpu_baseline_run(f_np, p_np, crop=args.cpu_crop)
+    if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
+        v, dt, desc = cpu_baseline_run(f_np[0, 0], p_np[0], crop=args.cpu_crop)
         line["cpu_baseline"] = {"value": v / 1e9, "unit": "Gpixels/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{desc}; {dt:.1f} s"}
     if rank == 0:
@@ -400,6 +467,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")
     ap.add_argument("--mode", default="filter", choices=["filter", "serve"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(BENCH_WORKLOADS))
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--hbm-gb", type=float, default=48.0)

@@ -158,7 +158,10 @@ bsf_status bsf_apply(bsf_ctx* ctx, const void* buffer, int dtype, int64_t H, int
  * combination of the pre-integrated buffer); the image gradient scatters the
  * stencil's weights into an FP64 buffer and applies the transposes of RS4,
  * RS3, RS2, RS1 in that order.  Only the exact form (opts->precision ==
- * BSF_PREC_EXACT) is supported.  At least one output must be non-NULL. */
+ * BSF_PREC_EXACT) is supported.  At least one output must be non-NULL.
+ * The adjoint does not cut wide rows into strips: an image whose padded
+ * width W + 2P exceeds 4096 (u8) or 3072 (f32) returns BSF_EINVAL before
+ * anything runs. */
 bsf_status bsf_filter_backward(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                                int64_t W, int N, const float* scales, const float* grad_out,
                                float* grad_image, float* grad_scales, const bsf_opts* opts, void* stream);

@@ -418,6 +418,8 @@ bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t
     int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / ((per_img + per_h) * (size_t)C)));
     bchunk = std::min<int64_t>(bchunk, B);
     const size_t esz = (dtype == BSF_U8) ? 1 : 4;
+    // rows wider than one band CTA holds are rejected before anything runs (the adjoint has no strips)
+    if (!make_scan_plan(Hp, Wp, (int)(bchunk * C), elem_bytes(mode)).ok) return BSF_EINVAL;
     if (grad_scales) BSF_TRY(cudaMemsetAsync(grad_scales, 0, (size_t)B * 4 * HW * sizeof(float), st));
     for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
         const int64_t nbat = std::min<int64_t>(bchunk, B - b0);

@@ -81,9 +81,10 @@ class Scheduler:
         self.slot_of: dict[int, int] = {}
         self.pending: deque = deque()
         self.peak_bytes = 0
+        self._used = 0
 
     def used(self) -> int:
-        return sum(self.inflight.values())
+        return self._used
 
     def offer(self, rid: int, nbytes: int, N: int) -> str | None:
         """Queue a request; returns a rejection reason, or None when queued."""
@@ -97,25 +98,25 @@ class Scheduler:
     def admit(self) -> list[tuple[int, int]]:
         """Admit queued requests into free slots while memory allows: (rid, slot) pairs."""
         out = []
-        if not self.free_slots:
-            return out
-        remaining = deque()
-        while self.pending:
+        skipped = []
+        while self.pending and self.free_slots:
             rid, nb = self.pending.popleft()
-            if self.free_slots and self.used() + nb <= self.budget:
+            if self._used + nb <= self.budget:
                 slot = self.free_slots.pop()
                 self.inflight[rid] = nb
                 self.slot_of[rid] = slot
+                self._used += nb
                 out.append((rid, slot))
-                self.peak_bytes = max(self.peak_bytes, self.used())
+                self.peak_bytes = max(self.peak_bytes, self._used)
             else:
-                remaining.append((rid, nb))
-        self.pending = remaining
+                skipped.append((rid, nb))
+        # requests passed over keep their places at the head of the queue
+        self.pending.extendleft(reversed(skipped))
         return out
 
     def complete(self, rid: int) -> int:
         """Release a finished request's memory and slot; returns the slot."""
-        self.inflight.pop(rid)
+        self._used -= self.inflight.pop(rid)
         slot = self.slot_of.pop(rid)
         self.free_slots.append(slot)
         return slot

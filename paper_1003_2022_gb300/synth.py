@@ -100,6 +100,12 @@ def srt_field(H: int, W: int, seed: int, sigma=(2.0, 8.0), rho=(1.0, 4.0), theta
     return np.stack([s, r, t]).astype(np.float32)
 
 
+def scale_field(H: int, W: int, seed: int, lo: float = 1.0, hi: float = 24.0) -> np.ndarray:
+    """Four independent smooth fields in [lo, hi]: a learnable scale vector
+    a = (a1..a4) per pixel, shape (4, H, W), float32."""
+    return np.stack([smooth_field(H, W, seed, 40 + k, lo, hi) for k in range(4)]).astype(np.float32)
+
+
 def constant_srt(H: int, W: int, sigma: float, rho: float, theta: float) -> np.ndarray:
     """A constant (sigma, rho, theta) field, shape (3, H, W), float32."""
     out = np.empty((3, H, W), dtype=np.float32)
@@ -118,11 +124,18 @@ WORKLOADS = {
     # same image as f32
     "u2048_f32_n4": dict(B=1, C=1, H=2048, W=2048, dtype="f32", N=4, sigma=(1.0, 32.0), rho=(1.0, 8.0),
                          theta="vector"),
+    # batch of 4 RGB 4096x4096 f32 U[0,1) + gratings, sigma 2-48, rho 1-6, theta uniform
+    # (the paper-shaped batch asks N=6; filtered here with N=4)
+    "b4c3_4096_f32_n4": dict(B=4, C=3, H=4096, W=4096, dtype="f32g", N=4, sigma=(2.0, 48.0), rho=(1.0, 6.0),
+                             theta="uniform"),
+    # batch of 8 1024x1024 f32 U[0,1) with a learnable scale field a_k in [1, 24]
+    "b8_1024_f32_scales": dict(B=8, C=1, H=1024, W=1024, dtype="f32", N=4, scales=(1.0, 24.0)),
 }
 
 
 def workload_inputs(name: str, seed: int = 0, H: int | None = None, W: int | None = None):
-    """Image (H, W) and (sigma, rho, theta) planes (3, H, W) for a named workload.
+    """Image (H, W) and (sigma, rho, theta) planes (3, H, W) for a named
+    single-image workload.
 
     H, W override the size (same distributions) for reduced parity cases.
     """
@@ -135,3 +148,28 @@ def workload_inputs(name: str, seed: int = 0, H: int | None = None, W: int | Non
         f = image(H, W, seed, "f32")
     p = srt_field(H, W, seed, cfg["sigma"], cfg["rho"], cfg["theta"])
     return f, p
+
+
+def batch_inputs(name: str, seed: int = 0, H: int | None = None, W: int | None = None, B: int | None = None):
+    """Images (B, C, H, W) and parameter planes (B, K, H, W) of a batched
+    workload: K = 3 (sigma, rho, theta) planes, or K = 4 scale planes for the
+    learnable-scale workload.  Batch entry b uses the sub-seed seed + b."""
+    cfg = WORKLOADS[name]
+    H = H or cfg["H"]
+    W = W or cfg["W"]
+    B = B or cfg["B"]
+    C = cfg["C"]
+    imgs = np.empty((B, C, H, W), dtype=np.uint8 if cfg["dtype"] == "u8" else np.float32)
+    K = 4 if "scales" in cfg else 3
+    prm = np.empty((B, K, H, W), dtype=np.float32)
+    for b in range(B):
+        for c in range(C):
+            if cfg["dtype"] == "f32g":
+                imgs[b, c] = gratings_image(H, W, seed + b, sub=c)
+            else:
+                imgs[b, c] = image(H, W, seed + b, cfg["dtype"], sub=c)
+        if K == 4:
+            prm[b] = scale_field(H, W, seed + b, *cfg["scales"])
+        else:
+            prm[b] = srt_field(H, W, seed + b, cfg["sigma"], cfg["rho"], cfg["theta"])
+    return imgs, prm

@@ -1,0 +1,133 @@
+"""Accuracy of the CUDA path on every paper-shaped workload at full size,
+against the FP64 oracle's plain definition fbar[n] = sum_k f[k] beta_{a(n)}(n-k)
+on sampled pixels (the oracle evaluates them one by one).
+
+Figures per workload: the normwise max error max|gpu - ref| / max|ref| (held
+to 1e-5), the RMS error sqrt(mean((gpu - ref)^2)) / max|ref|, and the largest
+per-pixel relative error where |ref| > 1e-3 max|ref|.  The all-FP64 form is
+reported beside the exact form with its own bound: its cancellation error
+grows with the fourth power of the buffer side.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1003_2022_gb300 import _lib as L  # noqa: E402
+from paper_1003_2022_gb300 import api, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _figures(got, ref):
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    m = np.abs(ref).max()
+    d = np.abs(got - ref)
+    big = np.abs(ref) > 1e-3 * m
+    return {"max_norm": float(d.max() / m), "rms_norm": float(np.sqrt(np.mean(d ** 2)) / m),
+            "max_rel_pixel": float((d[big] / np.abs(ref[big])).max()), "samples": int(ref.size)}
+
+
+def _scales_at(prm, idx):
+    """Oracle scale map at the sampled pixels only, in a full (4, H, W) field
+    (the direct sum reads a(n) at its output pixels alone)."""
+    _, H, W = prm.shape
+    a = np.zeros((4, H * W))
+    a[:, idx], _ = O.map4(prm.reshape(3, -1)[:, idx].astype(np.float64), O.KIND_SRT)
+    return a.reshape(4, H, W)
+
+
+def _samples(H, W, n, seed):
+    rng = np.random.default_rng(seed)
+    edge = np.array([0, W - 1, (H - 1) * W, H * W - 1, W // 2, (H // 2) * W, (H // 2) * W + W - 1])
+    return np.unique(np.concatenate([rng.choice(H * W, size=n, replace=False), edge]))
+
+
+@pytest.mark.parametrize("name,precision,n", [("u256_f32_n4", "exact", 2048),
+                                              ("u2048_u8_n4", "exact", 400),
+                                              ("u2048_f32_n4", "exact", 400),
+                                              ("u2048_u8_n4", "fp64", 400),
+                                              ("u2048_f32_n4", "fp64", 400)])
+def test_single_image_workloads(name, precision, n, accuracy_record):
+    dev = _cuda()
+    f, p = synth.workload_inputs(name)
+    smax = synth.WORKLOADS[name]["sigma"][1]
+    out = api.filter(torch.from_numpy(f).to(dev), torch.from_numpy(p).to(dev), kind="srt", max_scale=smax,
+                     precision=precision)
+    st = api.device_status(dev)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    H, W = f.shape
+    idx = _samples(H, W, n, seed=31)
+    a = _scales_at(p, idx)
+    ref = O.direct4(f.astype(np.float64), a, idx)
+    fig = _figures(out.cpu().numpy().ravel()[idx], ref)
+    accuracy_record[f"{name}/{precision}"] = fig
+    if precision == "exact":
+        assert fig["max_norm"] < TOL
+    else:
+        assert fig["max_norm"] < 1.0
+
+
+def test_batched_rgb_4096_workload(accuracy_record):
+    """4 x 3 x 4096 x 4096 f32 (uniform plus gratings), sigma 2-48, rho 1-6,
+    theta uniform, filtered with N=4 in one call; every (image, channel)
+    checked on sampled pixels."""
+    dev = _cuda()
+    imgs, prm = synth.batch_inputs("b4c3_4096_f32_n4")
+    B, C, H, W = imgs.shape
+    out = api.filter(torch.from_numpy(imgs).to(dev), torch.from_numpy(prm).to(dev), kind="srt", max_scale=48.0)
+    st = api.device_status(dev)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    out = out.cpu().numpy()
+    gots, refs = [], []
+    for b in range(B):
+        for c in range(C):
+            idx = _samples(H, W, 24, seed=100 * b + c)
+            a = _scales_at(prm[b], idx)
+            refs.append(O.direct4(imgs[b, c].astype(np.float64), a, idx))
+            gots.append(out[b, c].ravel()[idx])
+    fig = _figures(np.concatenate(gots), np.concatenate(refs))
+    accuracy_record["b4c3_4096_f32_n4/exact"] = fig
+    assert fig["max_norm"] < TOL
+
+
+def test_learnable_scale_workload_forward(accuracy_record):
+    """8 x 1024 x 1024 f32 with a scale field a_k in [1, 24] (kind "scales")."""
+    dev = _cuda()
+    imgs, a = synth.batch_inputs("b8_1024_f32_scales")
+    B, _, H, W = imgs.shape
+    out = api.filter(torch.from_numpy(imgs).to(dev), torch.from_numpy(a).to(dev), kind="scales",
+                     max_scale=24.0).cpu().numpy()
+    assert api.device_status(dev) == 0
+    gots, refs = [], []
+    for b in range(B):
+        idx = _samples(H, W, 64, seed=7 + b)
+        refs.append(O.direct4(imgs[b, 0].astype(np.float64), a[b].astype(np.float64), idx))
+        gots.append(out[b, 0].ravel()[idx])
+    fig = _figures(np.concatenate(gots), np.concatenate(refs))
+    accuracy_record["b8_1024_f32_scales/exact"] = fig
+    assert fig["max_norm"] < TOL
+
+
+@pytest.mark.parametrize("m", [2])
+def test_iterated_workload(m, accuracy_record):
+    """The 256x256 workload filtered with the iterated spline (m passes of a/sqrt(m))."""
+    dev = _cuda()
+    f, p = synth.workload_inputs("u256_f32_n4", H=128, W=128)
+    out = api.filter(torch.from_numpy(f).to(dev), torch.from_numpy(p).to(dev), kind="srt", max_scale=8.0,
+                     iterations=m).cpu().numpy()
+    assert api.device_status(dev) & ~(1 << L.BSF_EINFEASIBLE) == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    ref = O.direct4_iterated(f.astype(np.float64), a, m)
+    fig = _figures(out, ref)
+    accuracy_record[f"u256_f32_n4_128crop/iterated_m{m}"] = fig
+    assert fig["max_norm"] < TOL

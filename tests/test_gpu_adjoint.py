@@ -62,15 +62,14 @@ def test_grad_scales_matches_finite_differences():
 
 
 def test_autograd_learnable_scales_workload():
-    """Batch 8 of 1024x1024 f32 images, scales in [1, 24] initialised from a
-    covariance field (sigma 1-8, rho 1-4) through the scale map, then clamped;
-    loss = sum(w * out) with a seeded weight w; gradients on 64x64 crops."""
+    """Batch 8 of 1024x1024 f32 images with a learnable scale field a_k in
+    [1, 24] (four smooth seeded fields from the shared generator, so both
+    sides start from the same bytes); loss = sum(w * out) with a seeded
+    weight w; gradients checked on 64x64 crops."""
     dev = _cuda()
-    B, H, W = 8, 1024, 1024
-    imgs = np.stack([synth.image(H, W, seed=40 + b, dtype="f32") for b in range(B)])[:, None]
-    srt = np.stack([synth.srt_field(H, W, seed=40 + b, sigma=(1.0, 8.0), rho=(1.0, 4.0)) for b in range(B)])
-    a0, _ = api.scales_from_cov(torch.from_numpy(srt).to(dev).permute(1, 0, 2, 3).reshape(3, B * H, W), kind="srt")
-    a0 = a0.reshape(4, B, H, W).permute(1, 0, 2, 3).clamp(1.0, 24.0).contiguous()
+    imgs, a0_np = synth.batch_inputs("b8_1024_f32_scales", seed=40)
+    B, _, H, W = imgs.shape
+    a0 = torch.from_numpy(a0_np).to(dev)
     image = torch.from_numpy(imgs).to(dev).requires_grad_(True)
     scales = a0.clone().requires_grad_(True)
     wgt = torch.from_numpy(np.random.default_rng(3).standard_normal((B, 1, H, W)).astype(np.float32)).to(dev)
@@ -80,7 +79,7 @@ def test_autograd_learnable_scales_workload():
     assert api.device_status(dev) == 0
     gimg = image.grad.detach().cpu().numpy()
     gsc = scales.grad.detach().cpu().numpy()
-    a_np = scales.detach().cpu().numpy().astype(np.float64)
+    a_np = a0_np.astype(np.float64)
     w_np = wgt.cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(11)
     for b in (0, 5):
