@@ -319,7 +319,9 @@ __global__ void k_prefix1(const T* __restrict__ S, T* __restrict__ P1, T* __rest
     block_row_scan<T, ITEMS>(Wp, [&](int i) { return s1[i]; }, [&](int i, T v) { p1[i] = v; }, sm);
     // over pairs i: (P1[2i], P1[2i+1], P1[2i] + P1[2i+1]) -> Q1[2i], Q1[2i+1], PP1[2i+1];
     // PP1[2i] = PP1[2i+1] - P1[2i+1]
-    __shared__ V3<T> sm3[32];
+    // raw storage: V3 has a constructor, which shared memory does not run
+    __shared__ __align__(16) unsigned char sm3_raw[32 * sizeof(V3<T>)];
+    V3<T>* sm3 = reinterpret_cast<V3<T>*>(sm3_raw);
     block_row_scan<V3<T>, ITEMS / 2>((Wp + 1) / 2,
         [&](int i) {
             const T e = p1[2 * i], o = (2 * i + 1 < Wp) ? p1[2 * i + 1] : T(0);
