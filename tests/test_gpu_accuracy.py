@@ -131,3 +131,33 @@ def test_iterated_workload(m, accuracy_record):
     fig = _figures(out, ref)
     accuracy_record[f"u256_f32_n4_128crop/iterated_m{m}"] = fig
     assert fig["max_norm"] < TOL
+
+
+@pytest.mark.parametrize("side", [1024, 2048])
+def test_image_gradient_large(side, accuracy_record):
+    """The image gradient (adjoint) of an f32 image with a learnable scale
+    field a_k in [1, 24], against the oracle's transpose sum on crops: the
+    FP64 scatter and transposed running sums must keep their accuracy as the
+    buffer grows."""
+    dev = _cuda()
+    f = synth.image(side, side, seed=70, dtype="f32")
+    a = synth.scale_field(side, side, seed=70)
+    g = np.random.default_rng(70).standard_normal((side, side)).astype(np.float32)
+    gi, _ = api.filter_backward(torch.from_numpy(f).to(dev), torch.from_numpy(a).to(dev),
+                                torch.from_numpy(g).to(dev), need_scales=False, max_scale=24.0)
+    assert api.device_status(dev) == 0
+    gi = gi.cpu().numpy()
+    rng = np.random.default_rng(71)
+    M = 40  # margin covering every footprint (a <= 24) that reaches the crop
+    gots, refs = [], []
+    for _ in range(3):
+        y0, x0 = (int(v) for v in rng.integers(M, side - 64 - M, size=2))
+        sl = (slice(y0 - M, y0 + 64 + M), slice(x0 - M, x0 + 64 + M))
+        gw, aw = g[sl].astype(np.float64), a[:, sl[0], sl[1]].astype(np.float64)
+        ww = gw.shape[1]
+        loc = np.array([(M + r) * ww + (M + c) for r in range(0, 64, 5) for c in range(0, 64, 7)])
+        refs.append(O.adjoint4(gw, aw, loc))
+        gots.append(np.array([gi[y0 + p // ww - M, x0 + p % ww - M] for p in loc]))
+    fig = _figures(np.concatenate(gots), np.concatenate(refs))
+    accuracy_record[f"grad_image_{side}_f32_scales/exact"] = fig
+    assert fig["max_norm"] < TOL
