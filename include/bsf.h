@@ -102,7 +102,11 @@ typedef struct {
 void bsf_default_opts(bsf_opts* opts);
 
 /* Create a context bound to CUDA device `device` (the device is made current
- * on the calling thread).  *ctx receives the handle. */
+ * on the calling thread).  *ctx receives the handle.  A context owns one set
+ * of scratch buffers that its calls share: calls are thread-safe, but work
+ * that one context enqueues on different streams must not overlap on the
+ * device (order it, or use one context per stream); bsf_filter_host keeps
+ * its own work in order on the context's streams. */
 bsf_status bsf_create(bsf_ctx** ctx, int device);
 
 /* Release a context and all scratch memory it owns (synchronises the device). */
@@ -116,6 +120,27 @@ bsf_status bsf_destroy(bsf_ctx* ctx);
 bsf_status bsf_filter(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                       int64_t W, int N, const float* params, int kind, const bsf_opts* opts,
                       float* out, void* stream);
+
+/* The whole path on HOST buffers, pipelined across calls (the paper has no
+ * counterpart; this is the streaming form of bsf_filter).  Enqueues on the
+ * context's own three CUDA streams: the copy of image_host and params_host to
+ * the device, bsf_filter on them, and the copy of the result into out_host;
+ * returns without waiting.  Two slots of device buffers alternate between
+ * consecutive calls, so the input copy of one call, the kernels of the
+ * previous one and the output copy of the one before can run at the same
+ * time.  Arguments and layouts are those of bsf_filter with host pointers.
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for
+ * the copies to overlap; they must stay valid and unchanged until
+ * bsf_host_sync returns.  Argument errors return synchronously and enqueue
+ * nothing; CUDA errors of the enqueued work are returned by bsf_host_sync.
+ * Slot buffers grow on demand, after draining the pipeline. */
+bsf_status bsf_filter_host(bsf_ctx* ctx, const void* image_host, int dtype, int64_t B, int64_t C,
+                           int64_t H, int64_t W, int N, const float* params_host, int kind,
+                           const bsf_opts* opts, float* out_host);
+
+/* Waits until every call of bsf_filter_host on ctx has completed and its
+ * output is in host memory. */
+bsf_status bsf_host_sync(bsf_ctx* ctx);
 
 /* Step (b), Sec. 3.2.2: covariance (COV) or (sigma, rho, theta) (SRT) planes
  * (3*npix floats) -> scale planes a_1..a_4 (4*npix floats, Eq. const widths).

@@ -38,7 +38,8 @@ BSF_PREC_FP64 = 1
 EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
-    "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward",
+    "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward", "bsf_filter_host",
+    "bsf_host_sync",
 ]
 
 
@@ -102,6 +103,10 @@ def load(path: str | None = None):
     lib.bsf_filter_backward.argtypes = [vp, vp, i32, i64, i64, i64, i64, i32, vp, vp, vp, vp, op, vp]
     lib.bsf_filter_noalloc.restype = i32
     lib.bsf_filter_noalloc.argtypes = [vp, i32, i64, i64, i32, vp, i32, op, vp, vp]
+    lib.bsf_filter_host.restype = i32
+    lib.bsf_filter_host.argtypes = [vp, vp, i32, i64, i64, i64, i64, i32, vp, i32, op, vp]
+    lib.bsf_host_sync.restype = i32
+    lib.bsf_host_sync.argtypes = [vp]
     lib.bsf_status_string.restype = ctypes.c_char_p
     lib.bsf_status_string.argtypes = [i32]
     _lib = lib
@@ -166,6 +171,16 @@ def bsf_filter_backward(ctx, image, dtype, B, C, H, W, N, scales, grad_out, grad
                         stream) -> int:
     return load().bsf_filter_backward(ctx, image, dtype, B, C, H, W, N, scales, grad_out, grad_image, grad_scales,
                                       ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def bsf_filter_host(ctx, image_host, dtype, B, C, H, W, N, params_host, kind, opts, out_host) -> int:
+    """Pipelined filter of host buffers (returns before the work completes; see bsf_host_sync)."""
+    return load().bsf_filter_host(ctx, image_host, dtype, B, C, H, W, N, params_host, kind,
+                                  ctypes.byref(opts) if opts is not None else None, out_host)
+
+
+def bsf_host_sync(ctx) -> int:
+    return load().bsf_host_sync(ctx)
 
 
 def bsf_filter_noalloc(image, dtype, H, W, N, params, kind, opts, out, stream) -> int:

@@ -24,6 +24,19 @@ struct bsf_ctx {
     void* iter;              // scaled fields and intermediate images of the iterated filter
     size_t iter_bytes;
     std::mutex mu;
+    // host-buffer pipeline (bsf_filter_host): three streams and two slots of
+    // device buffers that alternate between calls
+    struct host_slot {
+        void* img = nullptr;
+        size_t img_bytes = 0;
+        void* prm = nullptr;
+        size_t prm_bytes = 0;
+        void* out = nullptr;
+        size_t out_bytes = 0;
+        cudaEvent_t in_ready = nullptr, comp_done = nullptr, out_done = nullptr;
+    } hs[2];
+    cudaStream_t s_h2d, s_comp, s_d2h;
+    unsigned long long host_calls;
     bool profiling;
     size_t prof_used;                                // event triples recorded since begin
     std::vector<std::array<cudaEvent_t, 3>> prof;    // pool of event triples
@@ -131,6 +144,8 @@ bsf_status bsf_create(bsf_ctx** ctx, int device) {
     c->iter_bytes = 0;
     c->profiling = false;
     c->prof_used = 0;
+    c->s_h2d = c->s_comp = c->s_d2h = nullptr;
+    c->host_calls = 0;
     cudaError_t e = cudaMalloc((void**)&c->d_status, 2 * sizeof(unsigned));
     if (e != cudaSuccess) {
         delete c;
@@ -156,6 +171,16 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->hbuf) cudaFree(c->hbuf);
     if (c->iter) cudaFree(c->iter);
     if (c->d_status) cudaFree(c->d_status);
+    for (auto& h : c->hs) {
+        if (h.img) cudaFree(h.img);
+        if (h.prm) cudaFree(h.prm);
+        if (h.out) cudaFree(h.out);
+        if (h.in_ready) cudaEventDestroy(h.in_ready);
+        if (h.comp_done) cudaEventDestroy(h.comp_done);
+        if (h.out_done) cudaEventDestroy(h.out_done);
+    }
+    for (cudaStream_t s_ : {c->s_h2d, c->s_comp, c->s_d2h})
+        if (s_) cudaStreamDestroy(s_);
     for (auto& t : c->prof)
         for (int i = 0; i < 3; ++i) cudaEventDestroy(t[i]);
     delete c;
@@ -341,21 +366,25 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
     return BSF_OK;
 }
 
-bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
-                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
+// argument checks shared by bsf_filter and bsf_filter_host
+static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                              int N, const float* params, int kind, const bsf_opts* opts, const float* out,
+                              bsf_opts* o) {
     if (!c || !image || !params || !out) return BSF_EINVAL;
     if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
     if (N != 4) return BSF_EUNSUPPORTED;
-    bsf_opts o;
-    bsf_default_opts(&o);
-    if (opts) o = *opts;
-    if (o.precision != BSF_PREC_EXACT && o.precision != BSF_PREC_FP64) return BSF_EINVAL;
-    if (o.iterations < 1 || o.iterations > 64) return BSF_EINVAL;
-    std::lock_guard<std::mutex> lock(c->mu);
-    BSF_TRY(cudaSetDevice(c->device));
-    cudaStream_t st = (cudaStream_t)stream;
+    bsf_default_opts(o);
+    if (opts) *o = *opts;
+    if (o->precision != BSF_PREC_EXACT && o->precision != BSF_PREC_FP64) return BSF_EINVAL;
+    if (o->iterations < 1 || o->iterations > 64) return BSF_EINVAL;
+    return BSF_OK;
+}
+
+// the filter on device buffers, enqueued on st (the caller holds the context lock)
+static bsf_status filter_locked(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                                const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st) {
     const int64_t HW = H * W;
     bsf_status s;
     if (o.iterations == 1) {
@@ -388,6 +417,79 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
         BSF_TRY(cudaStreamSynchronize(st));
         if (h & (1u << BSF_EINFEASIBLE)) return BSF_EINFEASIBLE;
     }
+    return BSF_OK;
+}
+
+bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
+                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
+    bsf_opts o;
+    const bsf_status a = filter_args(c, image, dtype, B, C, H, W, N, params, kind, opts, out, &o);
+    if (a != BSF_OK) return a;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    return filter_locked(c, image, dtype, B, C, H, W, params, kind, o, out, (cudaStream_t)stream);
+}
+
+// Slot buffers grow only while no enqueued work of the pipeline is in flight.
+static cudaError_t host_grow(bsf_ctx* c, void** p, size_t* cur, size_t need) {
+    if (need <= *cur) return cudaSuccess;
+    for (cudaStream_t s_ : {c->s_h2d, c->s_comp, c->s_d2h}) {
+        cudaError_t e = cudaStreamSynchronize(s_);
+        if (e != cudaSuccess) return e;
+    }
+    return grow(p, cur, need);
+}
+
+bsf_status bsf_filter_host(bsf_ctx* c, const void* image_host, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                           int N, const float* params_host, int kind, const bsf_opts* opts, float* out_host) {
+    bsf_opts o;
+    const bsf_status a = filter_args(c, image_host, dtype, B, C, H, W, N, params_host, kind, opts, out_host, &o);
+    if (a != BSF_OK) return a;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    if (!c->s_h2d) {
+        BSF_TRY(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
+        BSF_TRY(cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+        BSF_TRY(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
+        for (auto& h : c->hs) {
+            BSF_TRY(cudaEventCreateWithFlags(&h.in_ready, cudaEventDisableTiming));
+            BSF_TRY(cudaEventCreateWithFlags(&h.comp_done, cudaEventDisableTiming));
+            BSF_TRY(cudaEventCreateWithFlags(&h.out_done, cudaEventDisableTiming));
+        }
+    }
+    auto& h = c->hs[c->host_calls & 1];
+    const int K = (kind == BSF_PARAM_SCALES) ? 4 : 3;
+    const size_t ib = (size_t)(B * C * H * W) * (dtype == BSF_U8 ? 1 : 4);
+    const size_t pb = (size_t)(B * K * H * W) * sizeof(float);
+    const size_t ob = (size_t)(B * C * H * W) * sizeof(float);
+    BSF_TRY(host_grow(c, &h.img, &h.img_bytes, ib));
+    BSF_TRY(host_grow(c, &h.prm, &h.prm_bytes, pb));
+    BSF_TRY(host_grow(c, &h.out, &h.out_bytes, ob));
+    // inputs of this slot are overwritten once the kernels of its previous call have read them
+    BSF_TRY(cudaStreamWaitEvent(c->s_h2d, h.comp_done, 0));
+    BSF_TRY(cudaMemcpyAsync(h.img, image_host, ib, cudaMemcpyHostToDevice, c->s_h2d));
+    BSF_TRY(cudaMemcpyAsync(h.prm, params_host, pb, cudaMemcpyHostToDevice, c->s_h2d));
+    BSF_TRY(cudaEventRecord(h.in_ready, c->s_h2d));
+    // the output of this slot is overwritten once its previous copy-out has finished
+    BSF_TRY(cudaStreamWaitEvent(c->s_comp, h.in_ready, 0));
+    BSF_TRY(cudaStreamWaitEvent(c->s_comp, h.out_done, 0));
+    const bsf_status s = filter_locked(c, h.img, dtype, B, C, H, W, (const float*)h.prm, kind, o, (float*)h.out,
+                                       c->s_comp);
+    if (s != BSF_OK) return s;
+    BSF_TRY(cudaEventRecord(h.comp_done, c->s_comp));
+    BSF_TRY(cudaStreamWaitEvent(c->s_d2h, h.comp_done, 0));
+    BSF_TRY(cudaMemcpyAsync(out_host, h.out, ob, cudaMemcpyDeviceToHost, c->s_d2h));
+    BSF_TRY(cudaEventRecord(h.out_done, c->s_d2h));
+    ++c->host_calls;
+    return BSF_OK;
+}
+
+bsf_status bsf_host_sync(bsf_ctx* c) {
+    if (!c) return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    if (!c->s_h2d) return BSF_OK;
+    BSF_TRY(cudaSetDevice(c->device));
+    for (cudaStream_t s_ : {c->s_h2d, c->s_comp, c->s_d2h}) BSF_TRY(cudaStreamSynchronize(s_));
     return BSF_OK;
 }
 

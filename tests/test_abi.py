@@ -50,6 +50,8 @@ def test_host_only_calls(lib):
     # null context and null pointers are rejected before any CUDA call
     assert lib.bsf_filter(None, 0, 0, 1, 1, 8, 8, 4, 0, 0, None, 0, 0) == lib.BSF_EINVAL
     assert lib.bsf_scales_from_cov(None, 0, 2, 10, 4, None, 0, 0, 0) == lib.BSF_EINVAL
+    assert lib.bsf_filter_host(None, 0, 0, 1, 1, 8, 8, 4, 0, 0, None, 0) == lib.BSF_EINVAL
+    assert lib.bsf_host_sync(None) == lib.BSF_EINVAL
 
 
 def test_python_binding_refuses_to_run_without_library(tmp_path, lib):

@@ -284,3 +284,28 @@ def test_iterated_filter_matches_oracle(m):
     a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
     ref = O.direct4_iterated(f.astype(np.float64), a, m)
     assert _nerr(out, ref) < TOL
+
+
+# ------------------------------------------------------------------ host-buffer pipeline
+def test_filter_host_pipeline_matches_device_calls():
+    """bsf_filter_host on pinned host buffers, several calls in flight on two
+    alternating slots (different sizes and dtypes force a slot to grow while
+    the pipeline runs): each output equals bsf_filter on the same inputs."""
+    dev = _cuda()
+    ctx = api.context(dev)
+    cases = [(96, 112, "u8"), (64, 80, "f32"), (96, 112, "f32"), (120, 90, "u8"), (64, 80, "u8")]
+    jobs = []
+    for k, (H, W, dt) in enumerate(cases):
+        f = torch.from_numpy(synth.image(H, W, seed=300 + k, dtype=dt)).pin_memory()
+        p = torch.from_numpy(synth.srt_field(H, W, seed=300 + k, sigma=(1.0, 6.0), rho=(1.0, 4.0))).pin_memory()
+        o = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        opts = api.make_opts(max_scale=6.0)
+        rc = L.bsf_filter_host(ctx, f.data_ptr(), L.BSF_U8 if dt == "u8" else L.BSF_F32, 1, 1, H, W, 4,
+                               p.data_ptr(), L.BSF_PARAM_SRT, opts, o.data_ptr())
+        assert rc == L.BSF_OK
+        jobs.append((f, p, o))
+    assert L.bsf_host_sync(ctx) == L.BSF_OK
+    for f, p, o in jobs:
+        want = api.filter(f.to(dev), p.to(dev), kind="srt", max_scale=6.0).cpu().numpy()
+        assert np.array_equal(o.numpy(), want)
+    assert api.device_status(dev) & ~(1 << L.BSF_EINFEASIBLE) == 0

@@ -27,7 +27,9 @@ def test_results_same_alone_and_in_the_mix():
         prm = synth.srt_field(side, side, seed=100 + i, sigma=(1.0, 12.0), rho=(1.0, 8.0))
         N = 6 if i == 7 else 4
         reqs.append(Request(i, img, prm, N=N, arrival=t, max_scale=12.0))
-        t += float(rng.exponential(0.002))
+        # a burst of six at t = 0 fills the slots together; the rest arrive over time
+        if i >= 5:
+            t += float(rng.exponential(0.002))
     srv = Server(slots=3, budget_bytes=96 << 20, device=0)
     try:
         results, stats = srv.run(reqs)
