@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
 
     const InT* f = img + (size_t)im * img_stride;
     // samples of the next D rows are kept in flight in a register ring
-    constexpr int D = 4;
+    constexpr int D = 2;
     auto fetch = [&](int y, InT* dst) {
         const int iy = y - P;
 #pragma unroll
