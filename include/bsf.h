@@ -142,6 +142,25 @@ bsf_status bsf_filter_host(bsf_ctx* ctx, const void* image_host, int dtype, int6
  * output is in host memory. */
 bsf_status bsf_host_sync(bsf_ctx* ctx);
 
+/* Feature-preserving smoothing (Sec. 4.2): the adaptive covariance field of
+ * a batch of images, to be passed to bsf_filter with kind BSF_PARAM_COV.
+ * Per pixel, J = w * (g g^T) is the structure tensor (g: central differences
+ * replicated at the border, summed over the C channels; w: the isotropic
+ * box spline with the covariance of a Gaussian of std sigma_w px, applied by
+ * this library's exact filter), and
+ *     C = sigma0^2 adj(M) / sqrt(det M),   M = J + tau I,
+ * i.e. a window of the area of an isotropic Gaussian of std sigma0 px,
+ * stretched along the eigenvector of the smallest eigenvalue of J (the
+ * orientation of minimal intensity variation) with elongation
+ * (lambda_max + tau) / (lambda_min + tau).  tau > 0 (in squared intensity
+ * units per px^2) is the gradient energy below which a region counts as
+ * uniform.  image: B*C*H*W elements of dtype; cov: B*3*H*W floats
+ * (C11, C12, C22 planes per batch entry).  Scratch: 10*B*H*W floats owned
+ * by the context.  Errors: BSF_EINVAL for non-positive or non-finite
+ * sigma_w, sigma0, tau and the argument errors of bsf_filter. */
+bsf_status bsf_structure_cov(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
+                             int64_t W, float sigma_w, float sigma0, float tau, float* cov, void* stream);
+
 /* Step (b), Sec. 3.2.2: covariance (COV) or (sigma, rho, theta) (SRT) planes
  * (3*npix floats) -> scale planes a_1..a_4 (4*npix floats, Eq. const widths).
  * flags (nullable, npix bytes): bit0 elongation clamped (Prop. 3.1), bit1

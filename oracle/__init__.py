@@ -19,6 +19,9 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
   respect to the scales.
 * ``map4``: the optimal scale vector of Sec. 3.2.2, steps (i)-(iii).
 * ``U_bound``: the elongation bound of Prop. 3.1.
+* ``structure_cov``: the adaptive covariance field of the feature-preserving
+  smoothing application (Sec. 4.2): structure tensor J = w * (g g^T) with the
+  plain-definition window, C = sigma0^2 adj(J + tau I) / sqrt(det(J + tau I)).
 
 The C source is ``bsf_oracle.c``; it is compiled with gcc on first use (or by
 ``__graft_entry__.build()``) into ``oracle/_build/``.
@@ -266,3 +269,40 @@ def kurtosis4_norm2(p) -> float:
     """||K||^2 up to the factor (mu4 - 3 mu2^2)^2 (App. E): sum p^4 + (p1^2+p3^2)(p2^2+p4^2), p = a^2."""
     p = np.asarray(p, float)
     return float(np.sum(p ** 4) + (p[0] ** 2 + p[2] ** 2) * (p[1] ** 2 + p[3] ** 2))
+
+
+def _central_gradient(f):
+    """Central differences of one (H, W) plane, with the border replicated."""
+    fp = np.pad(f, 1, mode="edge")
+    return 0.5 * (fp[1:-1, 2:] - fp[1:-1, :-2]), 0.5 * (fp[2:, 1:-1] - fp[:-2, 1:-1])
+
+
+def structure_tensor(f, sigma_w: float) -> np.ndarray:
+    """Sec. 4.2: J = w * (g g^T) per pixel, (3, H, W) planes (J11, J12, J22).
+
+    f: (H, W) or (C, H, W) (the products of the channels are summed);
+    g: central differences with the border replicated; w: the isotropic
+    four-directional box spline a_k = sigma_w sqrt(6) (the covariance of a
+    Gaussian of std sigma_w), applied by the plain definition (``direct4``)."""
+    f = _d(f)
+    if f.ndim == 2:
+        f = f[None]
+    H, W = f.shape[1:]
+    P = np.zeros((3, H, W))
+    for c in range(f.shape[0]):
+        gx, gy = _central_gradient(f[c])
+        P[0] += gx * gx
+        P[1] += gx * gy
+        P[2] += gy * gy
+    a = np.full((4, H, W), sigma_w * np.sqrt(6.0))
+    return np.stack([direct4(P[k], a) for k in range(3)])
+
+
+def structure_cov(f, sigma_w: float, sigma0: float, tau: float) -> np.ndarray:
+    """Sec. 4.2: the adaptive covariance field, (3, H, W) planes (C11, C12, C22):
+    C = sigma0^2 adj(M) / sqrt(det M), M = J + tau I (long axis along the
+    eigenvector of the smallest eigenvalue of J, det C = sigma0^4)."""
+    J = structure_tensor(f, sigma_w)
+    m11, m12, m22 = J[0] + tau, J[1], J[2] + tau
+    s = sigma0 * sigma0 / np.sqrt(m11 * m22 - m12 * m12)
+    return np.stack([s * m22, -s * m12, s * m11])

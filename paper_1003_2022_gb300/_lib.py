@@ -39,7 +39,7 @@ EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
     "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward", "bsf_filter_host",
-    "bsf_host_sync",
+    "bsf_host_sync", "bsf_structure_cov",
 ]
 
 
@@ -107,6 +107,9 @@ def load(path: str | None = None):
     lib.bsf_filter_host.argtypes = [vp, vp, i32, i64, i64, i64, i64, i32, vp, i32, op, vp]
     lib.bsf_host_sync.restype = i32
     lib.bsf_host_sync.argtypes = [vp]
+    lib.bsf_structure_cov.restype = i32
+    lib.bsf_structure_cov.argtypes = [vp, vp, i32, i64, i64, i64, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      vp, vp]
     lib.bsf_status_string.restype = ctypes.c_char_p
     lib.bsf_status_string.argtypes = [i32]
     _lib = lib
@@ -177,6 +180,11 @@ def bsf_filter_host(ctx, image_host, dtype, B, C, H, W, N, params_host, kind, op
     """Pipelined filter of host buffers (returns before the work completes; see bsf_host_sync)."""
     return load().bsf_filter_host(ctx, image_host, dtype, B, C, H, W, N, params_host, kind,
                                   ctypes.byref(opts) if opts is not None else None, out_host)
+
+
+def bsf_structure_cov(ctx, image, dtype, B, C, H, W, sigma_w, sigma0, tau, cov, stream) -> int:
+    return load().bsf_structure_cov(ctx, image, dtype, B, C, H, W, float(sigma_w), float(sigma0), float(tau), cov,
+                                    stream)
 
 
 def bsf_host_sync(ctx) -> int:

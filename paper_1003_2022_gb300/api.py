@@ -148,6 +148,36 @@ def apply(buffer: torch.Tensor, image_dtype: torch.dtype, H: int, W: int, halo: 
     return out
 
 
+def structure_cov(image: torch.Tensor, sigma_w: float, sigma0: float, tau: float, stream=None) -> torch.Tensor:
+    """Sec. 4.2: the adaptive covariance field of feature-preserving smoothing,
+    (B, 3, H, W) float32 (C11, C12, C22) for an image of shape (H,W), (C,H,W) or
+    (B,C,H,W): a window of the area of an isotropic Gaussian of std sigma0,
+    stretched along the local orientation given by the structure tensor
+    (window std sigma_w); tau is the gradient energy below which the window
+    stays isotropic."""
+    img = _as4d(image)
+    if not img.is_cuda or img.dtype not in (torch.uint8, torch.float32):
+        raise ValueError("image must be a uint8 or float32 CUDA tensor")
+    img = img.contiguous()
+    B, C, H, W = img.shape
+    cov = torch.empty((B, 3, H, W), dtype=torch.float32, device=img.device)
+    dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
+    rc = L.bsf_structure_cov(context(img.device), img.data_ptr(), dtype, B, C, H, W, sigma_w, sigma0, tau,
+                             cov.data_ptr(), _stream_ptr(stream))
+    L.check(rc, "bsf_structure_cov")
+    return cov
+
+
+def adaptive_smooth(image: torch.Tensor, sigma_w: float = 2.0, sigma0: float = 1.0, tau: float = 0.005,
+                    iterations: int = 1, stream=None) -> torch.Tensor:
+    """Feature-preserving smoothing (Sec. 4.2): the filter with the covariance
+    field of structure_cov, on the same image (output shaped like the input)."""
+    cov = structure_cov(image, sigma_w, sigma0, tau, stream=stream)
+    img = _as4d(image)
+    out = filter(img, cov, kind="cov", stream=stream, iterations=iterations)
+    return out.reshape(image.shape) if image.dim() < 4 else out
+
+
 def device_status(device=None, stream=None) -> int:
     """Synchronise the stream and return (and clear) the device status bits."""
     return L.bsf_get_device_status(context(device), _stream_ptr(stream))

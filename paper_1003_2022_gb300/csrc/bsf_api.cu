@@ -23,6 +23,8 @@ struct bsf_ctx {
     size_t hbuf_bytes;
     void* iter;              // scaled fields and intermediate images of the iterated filter
     size_t iter_bytes;
+    void* stbuf;             // structure-tensor planes of bsf_structure_cov
+    size_t stbuf_bytes;
     std::mutex mu;
     // host-buffer pipeline (bsf_filter_host): three streams and two slots of
     // device buffers that alternate between calls
@@ -142,6 +144,8 @@ bsf_status bsf_create(bsf_ctx** ctx, int device) {
     c->hbuf_bytes = 0;
     c->iter = nullptr;
     c->iter_bytes = 0;
+    c->stbuf = nullptr;
+    c->stbuf_bytes = 0;
     c->profiling = false;
     c->prof_used = 0;
     c->s_h2d = c->s_comp = c->s_d2h = nullptr;
@@ -170,6 +174,7 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->work) cudaFree(c->work);
     if (c->hbuf) cudaFree(c->hbuf);
     if (c->iter) cudaFree(c->iter);
+    if (c->stbuf) cudaFree(c->stbuf);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& h : c->hs) {
         if (h.img) cudaFree(h.img);
@@ -490,6 +495,35 @@ bsf_status bsf_host_sync(bsf_ctx* c) {
     if (!c->s_h2d) return BSF_OK;
     BSF_TRY(cudaSetDevice(c->device));
     for (cudaStream_t s_ : {c->s_h2d, c->s_comp, c->s_d2h}) BSF_TRY(cudaStreamSynchronize(s_));
+    return BSF_OK;
+}
+
+bsf_status bsf_structure_cov(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                             float sigma_w, float sigma0, float tau, float* cov, void* stream) {
+    if (!c || !image || !cov) return BSF_EINVAL;
+    if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (!(sigma_w > 0.f && sigma_w < 1e4f) || !(sigma0 > 0.f && sigma0 < 1e4f) || !(tau > 0.f && tau < 1e30f))
+        return BSF_EINVAL;
+    std::lock_guard<std::mutex> lock(c->mu);
+    BSF_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t HW = H * W;
+    const size_t n3 = (size_t)(3 * B * HW);
+    BSF_TRY(grow(&c->stbuf, &c->stbuf_bytes, (2 * n3 + (size_t)(4 * B * HW)) * sizeof(float)));
+    float* prod = (float*)c->stbuf;
+    float* J = prod + n3;
+    float* prm = J + n3;
+    BSF_TRY(launch_st_products(image, dtype == BSF_U8, (int)B, (int)C, (int)H, (int)W, prod, st));
+    // the window: the isotropic box spline with the covariance of a Gaussian of std sigma_w
+    const float a = sigma_w * 2.44948974278317810f;
+    BSF_TRY(launch_fill(prm, (size_t)(4 * B * HW), a, st));
+    bsf_opts o;
+    bsf_default_opts(&o);
+    o.max_scale = a;
+    const bsf_status s = filter_locked(c, prod, BSF_F32, B, 3, H, W, prm, BSF_PARAM_SCALES, o, J, st);
+    if (s != BSF_OK) return s;
+    BSF_TRY(launch_adaptive_cov(J, (long long)HW, (int)B, sigma0 * sigma0, tau, cov, st));
     return BSF_OK;
 }
 

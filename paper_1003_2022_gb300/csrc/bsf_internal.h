@@ -54,3 +54,10 @@ cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp
                          unsigned* status, cudaStream_t st);
 cudaError_t launch_transpose_scans(double* hbuf, int nimg, int Hp, int Wp, int pitch, int P, int H, int W,
                                    float* gimage, cudaStream_t st);
+
+// Feature-preserving smoothing (adaptive.cu).
+cudaError_t launch_st_products(const void* img, int dtype_u8, int B, int C, int H, int W, float* prod,
+                               cudaStream_t st);
+cudaError_t launch_fill(float* p, size_t n, float v, cudaStream_t st);
+cudaError_t launch_adaptive_cov(const float* J, long long HW, int B, float s0sq, float tau, float* cov,
+                                cudaStream_t st);

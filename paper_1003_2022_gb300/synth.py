@@ -106,6 +106,23 @@ def scale_field(H: int, W: int, seed: int, lo: float = 1.0, hi: float = 24.0) ->
     return np.stack([smooth_field(H, W, seed, 40 + k, lo, hi) for k in range(4)]).astype(np.float32)
 
 
+def rings_image(H: int, W: int, period: float = 8.0, cy: float | None = None, cx: float | None = None,
+                contrast: float = 0.4) -> np.ndarray:
+    """Concentric rings 0.5 + contrast * sin(2 pi r / period) around (cy, cx): an
+    oriented pattern whose orientation changes everywhere (f32)."""
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    cy = 0.5 * (H - 1) if cy is None else cy
+    cx = 0.5 * (W - 1) if cx is None else cx
+    r = np.hypot(y - cy, x - cx)
+    return (0.5 + contrast * np.sin(2.0 * np.pi * r / period)).astype(np.float32)
+
+
+def add_noise(f: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """f plus white Gaussian noise of std sigma (f32)."""
+    g = _rng(seed, 300)
+    return (f.astype(np.float64) + sigma * g.standard_normal(f.shape)).astype(np.float32)
+
+
 def constant_srt(H: int, W: int, sigma: float, rho: float, theta: float) -> np.ndarray:
     """A constant (sigma, rho, theta) field, shape (3, H, W), float32."""
     out = np.empty((3, H, W), dtype=np.float32)
