@@ -135,6 +135,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """The largest of the ranks' timed-region durations (the job's time when
+    independent replicas run one per GPU); the local value without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(units_per_rank: float, ms_max: float, world_size: int) -> float:
+    """Whole-job throughput of replicas: the units all ranks processed / the max time."""
+    return world_size * units_per_rank / (ms_max / 1e3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -297,11 +314,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    t_max = total_ms
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, dev)
     time.sleep(0.25)
     sampler.stop()
     clocks = sampler.summary()
@@ -360,7 +373,7 @@ def run_ours(args):
         raise RuntimeError(f"device status error {status}")
 
     npx = B * C * H * W
-    value = ws * npx * args.steps / (t_max / 1e3) / 1e9
+    value = replicas_value(npx * args.steps, t_max, ws) / 1e9
     e2e_value = ws * npx * e2e_steps / (e2e_ms / 1e3) / 1e9
     # stencil launches in the timed region (one per strip and batch chunk of each forward call)
     n_st = max(nl, 1)
