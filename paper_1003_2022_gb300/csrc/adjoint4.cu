@@ -259,58 +259,72 @@ __global__ void __launch_bounds__(256) k_grad_scatter(int Hp, int Wp, int pitch,
     }
 }
 
-// Suffix sums along direction (dx, dy) in {(-1,1), (0,1), (1,1), (1,0)} of
-// nimg FP64 buffers (Hp x pitch), one warp per line.  When crop is set (the
-// last, row-direction pass) the image window [P, P+H) x [P, P+W) of the
-// result is also written to out as float.
-__global__ void k_line_suffix(double* __restrict__ X, long long stride, int Hp, int Wp, int pitch, int dx, int dy,
-                              float* __restrict__ out, int P, int H, int W) {
+// Transposed running sums.  Each is a suffix sum along a lattice direction d,
+// out[p] = sum_{j >= 0} in[p + j d], stopping at the buffer edge (the exact
+// transpose of the finite-buffer recursions), in place on nimg FP64 buffers.
+//
+// Directions (dx, 1): one thread per line, neighbouring threads on
+// neighbouring lines, so every row is read and written coalesced; each
+// thread walks its line from the bottom row up, with the loads of the next
+// kChunk rows issued before the running sum consumes them.  One FP64 add per
+// element.
+constexpr int kChunk = 32;
+
+__global__ void __launch_bounds__(128) k_suffix_lines(double* __restrict__ X, long long stride, int Hp, int Wp,
+                                                      int pitch, int dx) {
     const int im = blockIdx.y;
-    const int line = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    // line start points: the cells whose predecessor (start - d) is outside the buffer
-    int x0, y0;
-    if (dy == 0) {             // rows
-        if (line >= Hp) return;
-        x0 = 0; y0 = line;
-    } else if (dx == 0) {      // columns
-        if (line >= Wp) return;
-        x0 = line; y0 = 0;
-    } else if (dx == 1) {      // (1,1): starts on the top row and the left column
-        if (line >= Wp + Hp - 1) return;
-        if (line < Wp) { x0 = line; y0 = 0; } else { x0 = 0; y0 = line - Wp + 1; }
-    } else {                   // (-1,1): starts on the top row and the right column
-        if (line >= Wp + Hp - 1) return;
-        if (line < Wp) { x0 = line; y0 = 0; } else { x0 = Wp - 1; y0 = line - Wp + 1; }
-    }
-    int len;
-    {
-        const int lx = dx > 0 ? Wp - x0 : (dx < 0 ? x0 + 1 : 1 << 30);
-        const int ly = dy > 0 ? Hp - y0 : 1 << 30;
-        len = min(lx, ly);
-    }
+    const int k = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    // line k holds the cells (x, y) with x = k + dx * y - off, off = (dx < 0 ? 0 : dx * (Hp - 1))
+    const int off = dx > 0 ? Hp - 1 : 0;
+    const int nlines = dx == 0 ? Wp : Wp + Hp - 1;
+    if (k >= nlines) return;
     double* base = X + (size_t)im * stride;
-    double carry = 0.0;
-    for (int end = len; end > 0; end -= 32) {
-        const int t = end - 32 + lane;
-        const bool ok = t >= 0;
-        const size_t off = ok ? (size_t)(y0 + t * dy) * pitch + (x0 + t * dx) : 0;
-        double v = ok ? base[off] : 0.0;
-        // suffix scan within the chunk (lane 31 is the last element)
+    // x at row y: dx = 0: k;  dx = 1: k - off + y;  dx = -1: k - y
+    auto xat = [&](int y) { return dx == 0 ? k : (dx > 0 ? k - off + y : k - y); };
+    double run = 0.0;
+    for (int y1 = Hp - 1; y1 >= 0; y1 -= kChunk) {
+        double v[kChunk];
 #pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, v, s);
-            if (lane + s < 32) v += o;
+        for (int j = 0; j < kChunk; ++j) {
+            const int y = y1 - j, x = xat(y);
+            v[j] = (y >= 0 && x >= 0 && x < Wp) ? base[(size_t)y * pitch + x] : 0.0;
         }
-        const double r = v + carry;
-        if (ok) {
-            base[off] = r;
-            if (out != nullptr) {
-                const int xx = x0 + t * dx - P, yy = y0 + t * dy - P;
-                if (xx >= 0 && xx < W && yy >= 0 && yy < H) out[(size_t)im * H * W + (size_t)yy * W + xx] = (float)r;
-            }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            const int y = y1 - j, x = xat(y);
+            run += v[j];
+            if (y >= 0 && x >= 0 && x < Wp) base[(size_t)y * pitch + x] = run;
         }
-        carry += __shfl_sync(0xffffffffu, v, 0);
+    }
+}
+
+// Direction (1, 0), the last transpose: one warp per row, each lane owning a
+// contiguous segment of it: local suffix sums, a warp scan of the segment
+// totals, then the carry; the image window [P, P+H) x [P, P+W) of the result
+// is written to out as float.
+__global__ void __launch_bounds__(256) k_suffix_rows(const double* __restrict__ X, long long stride, int Hp, int Wp,
+                                                     int pitch, float* __restrict__ out, int P, int H, int W) {
+    const int im = blockIdx.y;
+    const int y = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (y < P || y >= P + H) return;  // only image rows reach the output
+    const double* row = X + (size_t)im * stride + (size_t)y * pitch;
+    const int seg = (Wp + 31) / 32, x0 = lane * seg, x1 = min(Wp, x0 + seg);
+    double tot = 0.0;
+    for (int x = x0; x < x1; ++x) tot += row[x];
+    // suffix over the lanes after this one
+    double after = tot;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, after, d);
+        if (lane + d < 32) after += o;
+    }
+    double run = after - tot;  // sum of the segments to the right
+    float* o = out + (size_t)im * H * W + (size_t)(y - P) * W;
+    for (int x = x1 - 1; x >= x0; --x) {
+        run += row[x];
+        const int xx = x - P;
+        if (xx >= 0 && xx < W) o[xx] = (float)run;
     }
 }
 
@@ -341,12 +355,12 @@ cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp
 cudaError_t launch_transpose_scans(double* hbuf, int nimg, int Hp, int Wp, int pitch, int P, int H, int W,
                                    float* gimage, cudaStream_t st) {
     const long long stride = (long long)Hp * pitch;
-    const int dirs[4][2] = {{-1, 1}, {0, 1}, {1, 1}, {1, 0}};  // RS4^T, RS3^T, RS2^T, RS1^T
-    for (int k = 0; k < 4; ++k) {
-        const int dx = dirs[k][0], dy = dirs[k][1];
-        const int nlines = dy == 0 ? Hp : (dx == 0 ? Wp : Wp + Hp - 1);
-        dim3 g((unsigned)((nlines + 7) / 8), nimg);
-        k_line_suffix<<<g, 256, 0, st>>>(hbuf, stride, Hp, Wp, pitch, dx, dy, k == 3 ? gimage : nullptr, P, H, W);
+    const int dxs[3] = {-1, 0, 1};  // RS4^T, RS3^T, RS2^T; then RS1^T along the rows
+    for (int k = 0; k < 3; ++k) {
+        const int nlines = dxs[k] == 0 ? Wp : Wp + Hp - 1;
+        k_suffix_lines<<<dim3((unsigned)((nlines + 127) / 128), nimg), 128, 0, st>>>(hbuf, stride, Hp, Wp, pitch,
+                                                                                    dxs[k]);
     }
+    k_suffix_rows<<<dim3((unsigned)((Hp + 7) / 8), nimg), 256, 0, st>>>(hbuf, stride, Hp, Wp, pitch, gimage, P, H, W);
     return cudaGetLastError();
 }
