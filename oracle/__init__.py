@@ -19,6 +19,13 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
   respect to the scales.
 * ``map4``: the optimal scale vector of Sec. 3.2.2, steps (i)-(iii).
 * ``U_bound``: the elongation bound of Prop. 3.1.
+* ``box_spline_hat`` / ``covarianceN`` / ``kurtosis_normN2`` / ``mapN`` /
+  ``gaussian_correlation``: the N-direction box spline in the Fourier domain
+  (Eq. const as a convolution of N boxes), its covariance (Eq. covariance),
+  the paper's kurtosis norm (Eq. finalForm, written for any N), the optimal
+  scale vector for any N (minimal kurtosis norm at the target covariance), and
+  the normalised correlation of an m-fold iterated spline with the Gaussian of
+  the same covariance (Sec. 3.3, Fig. errorplots).
 * ``structure_cov``: the adaptive covariance field of the feature-preserving
   smoothing application (Sec. 4.2): structure tensor J = w * (g g^T) with the
   plain-definition window, C = sigma0^2 adj(J + tau I) / sqrt(det(J + tau I)).
@@ -306,3 +313,86 @@ def structure_cov(f, sigma_w: float, sigma0: float, tau: float) -> np.ndarray:
     m11, m12, m22 = J[0] + tau, J[1], J[2] + tau
     s = sigma0 * sigma0 / np.sqrt(m11 * m22 - m12 * m12)
     return np.stack([s * m22, -s * m12, s * m11])
+
+
+def directions(N: int) -> np.ndarray:
+    """theta_k = (k - 1) pi / N, k = 1..N (the radially-uniform directions)."""
+    return np.arange(N) * np.pi / N
+
+
+def box_spline_hat(theta, a, W1, W2) -> np.ndarray:
+    """Fourier transform of beta^N_a at the angular frequencies (W1, W2): the box
+    spline is the convolution of N centred boxes of length a_k along u_k (Eq.
+    const), so its transform is prod_k sinc(a_k u_k . w / 2), sinc(x) = sin(x)/x."""
+    r = np.ones_like(np.asarray(W1, float))
+    for t, ak in zip(theta, a):
+        r = r * np.sinc(0.5 * ak * (np.cos(t) * W1 + np.sin(t) * W2) / np.pi)
+    return r
+
+
+def covarianceN(theta, a) -> np.ndarray:
+    """Eq. covariance: (1/12) sum_k a_k^2 u_k u_k^T."""
+    C = np.zeros((2, 2))
+    for t, ak in zip(theta, a):
+        u = np.array([np.cos(t), np.sin(t)])
+        C += ak * ak / 12.0 * np.outer(u, u)
+    return C
+
+
+def kurtosis_normN2(theta, p) -> float:
+    """||K||^2 of K = sum_k p_k^2 u_k u_k^T (Eq. finalForm up to the factor
+    (mu4 - 3 mu2^2)), p = a^2: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m).
+    For N = 4 it equals kurtosis4_norm2."""
+    p = np.asarray(p, float)
+    d = np.subtract.outer(np.asarray(theta, float), np.asarray(theta, float))
+    return float((p ** 2) @ (np.cos(d) ** 2) @ (p ** 2))
+
+
+def mapN(theta, C, eps: float = 1e-9, starts: int = 24, seed: int = 0) -> np.ndarray:
+    """The optimal scale vector for any N: minimise kurtosis_normN2 over p = a^2
+    subject to (1/12) sum p_k u_k u_k^T = C and p >= eps (the criterion of Sec.
+    3.2.2, for N directions; the feasible set is an (N-3)-dimensional polytope
+    and the objective is convex on it), by SLSQP from several starting points.
+    Returns a (length N)."""
+    from scipy.optimize import minimize
+    theta = np.asarray(theta, float)
+    U = np.stack([np.cos(theta) ** 2, np.cos(theta) * np.sin(theta), np.sin(theta) ** 2], axis=1) / 12.0
+    c = np.array([C[0][0], C[0][1], C[1][1]], float)
+    D = np.cos(np.subtract.outer(theta, theta)) ** 2
+    scale = float(np.trace(np.asarray(C, float)))
+
+    def f(p):
+        q = p * p
+        return q @ D @ q / scale ** 4
+
+    def g(p):
+        q = p * p
+        return 4.0 * p * (D @ q) / scale ** 4
+
+    cons = {"type": "eq", "fun": lambda p: (U.T @ p - c) / scale, "jac": lambda p: U.T / scale}
+    rng = np.random.default_rng(seed)
+    best = None
+    for _ in range(starts):
+        p0 = rng.uniform(0.2, 2.0, theta.size) * 12.0 * scale / theta.size
+        r = minimize(f, p0, jac=g, constraints=[cons], bounds=[(eps, None)] * theta.size, method="SLSQP",
+                     options={"ftol": 1e-15, "maxiter": 1000})
+        if r.success and np.abs(U.T @ r.x - c).max() < 1e-9 * scale and (best is None or r.fun < best.fun):
+            best = r
+    if best is None:
+        raise RuntimeError("mapN: no feasible optimum found")
+    return np.sqrt(best.x)
+
+
+def gaussian_correlation(theta, a, C, m: int = 1, half_width: float | None = None, n: int = 801) -> float:
+    """Normalised correlation <beta, g> / (||beta|| ||g||) of the m-fold iterated
+    spline beta^{N,m} (m-fold convolution of beta_{a / sqrt m}) with the Gaussian
+    g of covariance C, by Parseval on a frequency grid: both transforms are real
+    and even."""
+    C = np.asarray(C, float)
+    if half_width is None:
+        half_width = 12.0 / np.sqrt(np.linalg.eigvalsh(C)[0])
+    w = np.linspace(-half_width, half_width, n)
+    W1, W2 = np.meshgrid(w, w)
+    b = box_spline_hat(theta, np.asarray(a, float) / np.sqrt(m), W1, W2) ** m
+    gh = np.exp(-0.5 * (C[0, 0] * W1 * W1 + 2 * C[0, 1] * W1 * W2 + C[1, 1] * W2 * W2))
+    return float(np.sum(b * gh) / np.sqrt(np.sum(b * b) * np.sum(gh * gh)))
