@@ -20,7 +20,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, times, out):
+def _rank(rank, world, port, times, outdir):
     sys.path.insert(0, ROOT)
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -30,18 +30,17 @@ def _rank(rank, world, port, times, out):
     t = bench.max_over_ranks(times[rank], device="cpu")
     v = bench.replicas_value(1000.0, t, dist.get_world_size())
     dist.barrier()
-    out[rank] = (t, v)
+    with open(os.path.join(outdir, f"rank{rank}.txt"), "w") as fh:
+        fh.write(f"{t!r} {v!r}")
     dist.destroy_process_group()
 
 
-def test_two_rank_replicas_take_the_slowest_rank():
+def test_two_rank_replicas_take_the_slowest_rank(tmp_path):
     port = _free_port()
     times = [12.5, 20.0]
-    mgr = mp.Manager()
-    out = mgr.dict()
-    mp.spawn(_rank, args=(2, port, times, out), nprocs=2, join=True)
+    mp.spawn(_rank, args=(2, port, times, str(tmp_path)), nprocs=2, join=True)
     for r in range(2):
-        t, v = out[r]
+        t, v = (float(x) for x in (tmp_path / f"rank{r}.txt").read_text().split())
         assert t == 20.0
         assert v == pytest.approx(2 * 1000.0 / 0.020)
 
