@@ -22,7 +22,7 @@
  *     directions are (1,0), (1,1)/sqrt2, (0,1), (-1,1)/sqrt2.
  *   - Images are dense row-major arrays of B*C*H*W elements (batch, channel,
  *     row, column), dtype BSF_U8 (uint8) or BSF_F32 (float32).  f is zero
- *     outside the image (reading 1 of the paper's unspecified boundary).
+ *     outside the image (the paper leaves the boundary condition open).
  *   - Parameter fields are dense float32 planes, one set per image of the
  *     batch and shared by its C channels: B*K*H*W floats, plane k of image b
  *     at params + (b*K + k)*H*W.  K = N for BSF_PARAM_SCALES (a_1..a_N in px,
