@@ -309,3 +309,41 @@ def test_filter_host_pipeline_matches_device_calls():
         want = api.filter(f.to(dev), p.to(dev), kind="srt", max_scale=6.0).cpu().numpy()
         assert np.array_equal(o.numpy(), want)
     assert api.device_status(dev) & ~(1 << L.BSF_EINFEASIBLE) == 0
+
+
+# ------------------------------------------------------------------ the steps one at a time
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_apply_on_preintegrated_buffer_matches_algorithm_1(dtype):
+    """bsf_preintegrate then bsf_apply (Algorithm 1 steps 2 and 3 as separate
+    calls) equal bsf_filter, and the oracle's step-by-step Algorithm 1."""
+    dev = _cuda()
+    H, W, P = 40, 52, 12
+    f = synth.image(H, W, seed=91, dtype=dtype)
+    a = np.random.default_rng(91).uniform(0.5, 6.0, size=(4, H, W)).astype(np.float32)
+    img = torch.from_numpy(f).to(dev)
+    prm = torch.from_numpy(a).to(dev)
+    buf = api.preintegrate(img, halo=P)
+    out = api.apply(buf, img.dtype, H, W, P, prm, kind="scales").cpu().numpy()
+    whole = api.filter(img, prm, kind="scales", halo=P).cpu().numpy()
+    assert api.device_status(dev) == 0
+    assert np.array_equal(out, whole)
+    ref, bad = O.alg1_filter4(f.astype(np.int64) if dtype == "u8" else f.astype(np.float64), a.astype(np.float64),
+                              P, integer=(dtype == "u8"))
+    assert bad == 0
+    assert _nerr(out, ref) < TOL
+
+
+def test_extreme_scales():
+    """Widths far below a pixel (all taps inside one ZP cell) and far beyond the
+    image, next to ordinary ones."""
+    dev = _cuda()
+    H, W = 36, 40
+    f = synth.image(H, W, seed=92, dtype="u8")
+    rng = np.random.default_rng(92)
+    a = rng.uniform(0.04, 0.3, size=(4, H, W)).astype(np.float32)
+    a[:, :, W // 2:] = rng.uniform(40.0, 150.0, size=(4, H, W - W // 2)).astype(np.float32)
+    out, st = _run(f, a, "scales", max_scale=150.0)
+    assert st == 0
+    ref = O.direct4(f.astype(np.float64), a.astype(np.float64))
+    assert _nerr(out[:, : W // 2], ref[:, : W // 2]) < TOL
+    assert _nerr(out[:, W // 2:], ref[:, W // 2:]) < TOL
