@@ -180,7 +180,10 @@ bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, in
  * running sum started from zero at the buffer edge; the two sqrt2 factors
  * are taken out, so g_b = 2 * buffer).  Integer forms wrap modulo 2^64
  * (u8) or 2^128 (f32 fixed point), which the exact finite difference
- * tolerates.  buffer: caller-owned device memory of bsf_buffer_bytes. */
+ * tolerates.  buffer: caller-owned device memory of bsf_buffer_bytes.  A
+ * padded row wider than 4096 elements (u8, FP64 form) or 3072 (f32 exact
+ * form) returns BSF_EINVAL: one buffer row must fit one band CTA
+ * (bsf_filter cuts such images into vertical strips instead). */
 bsf_status bsf_preintegrate(bsf_ctx* ctx, const void* image, int dtype, int64_t H, int64_t W, int N,
                             int halo, int precision, void* buffer, void* stream);
 

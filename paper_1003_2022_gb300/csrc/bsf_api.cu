@@ -593,6 +593,7 @@ bsf_status bsf_preintegrate(bsf_ctx* c, const void* image, int dtype, int64_t H,
     const int mode = mode_of(dtype, precision);
     const int Hp = (int)H + 2 * halo, Wp = (int)W + 2 * halo;
     const scan_plan plan = make_scan_plan(Hp, Wp, 1, elem_bytes(mode));
+    if (!plan.ok) return BSF_EINVAL;  // a row wider than one band CTA holds (bsf_filter uses strips)
     BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
     BSF_TRY(run_scan(mode, dtype, image, (long long)H * W, 1, (int)H, (int)W, halo, buffer, (long long)Hp * Wp, Wp,
                      c->work, (cudaStream_t)stream));

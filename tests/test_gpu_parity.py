@@ -347,3 +347,11 @@ def test_extreme_scales():
     ref = O.direct4(f.astype(np.float64), a.astype(np.float64))
     assert _nerr(out[:, : W // 2], ref[:, : W // 2]) < TOL
     assert _nerr(out[:, W // 2:], ref[:, W // 2:]) < TOL
+
+
+def test_preintegrate_rejects_rows_wider_than_a_band():
+    dev = _cuda()
+    f = torch.zeros((4, 3200), dtype=torch.float32, device=dev)
+    with pytest.raises(L.BsfError) as e:
+        api.preintegrate(f, halo=8)
+    assert e.value.code == L.BSF_EINVAL
