@@ -16,7 +16,9 @@ struct scan_plan {
 };
 
 scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes);
-int scan_max_width(size_t elem_bytes);  // widest buffer row one band CTA can hold
+// widest buffer row one band CTA holds; narrow: the width at which the 128-bit
+// form keeps four columns per thread (chosen for batches of several waves)
+int scan_max_width(size_t elem_bytes, bool narrow = false);
 
 // Pre-integration (RS1-RS4) of nimg images of H x W (stride img_stride
 // elements) into buffers of Hp x pitch elements (stride G_stride elements).

@@ -371,7 +371,10 @@ scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes) {
     return p;
 }
 
-int scan_max_width(size_t elem_bytes) { return 8 * band_maxt(elem_bytes > 8, 8); }
+int scan_max_width(size_t elem_bytes, bool narrow) {
+    const bool wide = elem_bytes > 8;
+    return (wide && narrow) ? 4 * band_maxt(true, 4) : 8 * band_maxt(wide, 8);
+}
 
 template <int MODE, class InT, int CPT>
 static void launch_band(const scan_plan& p, const InT* img, long long img_stride, int nimg, int H, int W, int col0,
