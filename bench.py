@@ -563,7 +563,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="exact", choices=["exact", "fp64"])
-    ap.add_argument("--cpu-crop", type=int, default=640)
+    ap.add_argument("--cpu-crop", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")
     ap.add_argument("--mode", default="filter", choices=["filter", "serve", "smooth"])
