@@ -392,6 +392,22 @@ def run_ours(args):
                              "reached 37.1 Tops/s, a multiply-add chain 19.1 Tops/s)",
                 "int_ops_per_px": ops_px,
                 "algorithmic_bytes_per_launch": int((12 + 4 + 8 * (1 if u8 else 2)) * px_per_launch)}
+    # the HBM side of both kernels, against the measured copy bandwidth
+    peaks, peak_src = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    P = api.halo_for(smax, kind_name)
+    elem = 8 if (u8 or args.precision != "exact") else 16
+    nstrip_one = (W + 2 * P) <= (4096 if elem == 8 else 3072)
+    pre_bytes = (H + 2 * P) * (W + 2 * P) * ((1 if u8 else 4) + elem) * B * C if nstrip_one else None
+    pre_ms = ms_pre / n_st
+    roofline["hbm"] = {
+        "peak_gbs": hbm_peak, "peak_source": peak_src,
+        "stencil_dram_gbs": traffic / (st_ms * 1e6) if traffic else None,
+        "stencil_frac": traffic / (st_ms * 1e6) / hbm_peak if traffic else None,
+        "preintegrate_algorithmic_bytes": pre_bytes,
+        "preintegrate_gbs": pre_bytes / (pre_ms * 1e6) if pre_bytes else None,
+        "preintegrate_frac": pre_bytes / (pre_ms * 1e6) / hbm_peak if pre_bytes else None,
+    }
     if args.precision != "exact":
         roofline["kernel"] = f"k_stencil4_f64<{kind_name.upper()}>"
         roofline["note"] = "all-FP64 form: the integer op count does not apply; compare kernel_ms"
