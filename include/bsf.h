@@ -208,7 +208,11 @@ bsf_status bsf_apply(bsf_ctx* ctx, const void* buffer, int dtype, int64_t H, int
  * BSF_PREC_EXACT) is supported.  At least one output must be non-NULL.
  * The adjoint does not cut wide rows into strips: an image whose padded
  * width W + 2P exceeds 4096 (u8) or 3072 (f32) returns BSF_EINVAL before
- * anything runs. */
+ * anything runs.  opts->iterations = m > 1 differentiates the m-fold
+ * iterated filter of bsf_filter (Sec. 3.3, widths a / sqrt(m) in every
+ * pass): the m - 1 intermediate images are recomputed (scratch: (m + 1)
+ * B*C*H*W floats owned by the context), the passes are differentiated in
+ * reverse order, and every pass adds its scale gradient. */
 bsf_status bsf_filter_backward(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                                int64_t W, int N, const float* scales, const float* grad_out,
                                float* grad_image, float* grad_scales, const bsf_opts* opts, void* stream);

@@ -192,8 +192,9 @@ def halo_for(max_scale: float, kind: str = "srt") -> int:
 
 
 def filter_backward(image: torch.Tensor, scales: torch.Tensor, grad_out: torch.Tensor, need_image: bool = True,
-                    need_scales: bool = True, N: int = 4, halo: int = 0, max_scale: float = 0.0, stream=None):
-    """Gradients of sum(grad_out * filter(image, scales)) w.r.t. image and scales (kind "scales")."""
+                    need_scales: bool = True, N: int = 4, halo: int = 0, max_scale: float = 0.0, stream=None,
+                    iterations: int = 1):
+    """Gradients of sum(grad_out * filter(image, scales, iterations=m)) w.r.t. image and scales (kind "scales")."""
     img = _as4d(image).contiguous()
     B, C, H, W = img.shape
     sc = (scales if scales.dim() == 4 else scales[None]).contiguous()
@@ -203,7 +204,7 @@ def filter_backward(image: torch.Tensor, scales: torch.Tensor, grad_out: torch.T
     gi = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device) if need_image else None
     gs = torch.empty((B, 4, H, W), dtype=torch.float32, device=img.device) if need_scales else None
     dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
-    opts = make_opts("exact", halo, max_scale)
+    opts = make_opts("exact", halo, max_scale, iterations=iterations)
     rc = L.bsf_filter_backward(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, sc.data_ptr(),
                                g.data_ptr(), gi.data_ptr() if gi is not None else None,
                                gs.data_ptr() if gs is not None else None, opts, _stream_ptr(stream))
@@ -223,21 +224,25 @@ class BoxSplineFilter(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, image, scales, halo: int = 0, max_scale: float = 0.0):
-        out = filter(image, scales, kind="scales", halo=halo, max_scale=max_scale)
+    def forward(ctx, image, scales, halo: int = 0, max_scale: float = 0.0, iterations: int = 1):
+        out = filter(image, scales, kind="scales", halo=halo, max_scale=max_scale, iterations=iterations)
         ctx.save_for_backward(image, scales)
         ctx.halo = halo
         ctx.max_scale = max_scale
+        ctx.iterations = iterations
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
         image, scales = ctx.saved_tensors
         gi, gs = filter_backward(image, scales, grad_out, need_image=ctx.needs_input_grad[0],
-                                 need_scales=ctx.needs_input_grad[1], halo=ctx.halo, max_scale=ctx.max_scale)
-        return gi, gs, None, None
+                                 need_scales=ctx.needs_input_grad[1], halo=ctx.halo, max_scale=ctx.max_scale,
+                                 iterations=ctx.iterations)
+        return gi, gs, None, None, None
 
 
-def box_spline_filter(image: torch.Tensor, scales: torch.Tensor, halo: int = 0, max_scale: float = 0.0):
-    """Autograd entry point of the filter with a learnable scale field."""
-    return BoxSplineFilter.apply(image, scales, halo, max_scale)
+def box_spline_filter(image: torch.Tensor, scales: torch.Tensor, halo: int = 0, max_scale: float = 0.0,
+                      iterations: int = 1):
+    """Autograd entry point of the filter with a learnable scale field (iterations = m:
+    the m-fold iterated spline of Sec. 3.3)."""
+    return BoxSplineFilter.apply(image, scales, halo, max_scale, iterations)

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, 2) k_grad_scales(const void* __restrict__
                                                         int Wp, int pitch, int P, int H, int W, int C,
                                                         const float* __restrict__ scales,
                                                         const float* __restrict__ gout, float* __restrict__ gscales,
-                                                        unsigned* status) {
+                                                        float ascale, unsigned* status) {
     typedef typename mode_traits<MODE>::T T;
     constexpr int FRAC = mode_traits<MODE>::FRAC_BITS;
     const int n1 = blockIdx.x * 32 + threadIdx.x;
@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(256, 2) k_grad_scales(const void* __restrict__
     if (n1 >= W || n2 >= H) return;
     const size_t HW = (size_t)H * W, p = (size_t)n2 * W + n1;
     const float* pr = scales + (size_t)(im / C) * 4 * HW;
-    const float a1 = pr[p], a2 = pr[HW + p], a3 = pr[2 * HW + p], a4 = pr[3 * HW + p];
-    const float gv = gout[(size_t)im * HW + p];
+    const float a1 = pr[p] * ascale, a2 = pr[HW + p] * ascale, a3 = pr[2 * HW + p] * ascale,
+                a4 = pr[3 * HW + p] * ascale;
+    const float gv = gout[(size_t)im * HW + p] * ascale;  // d/da = ascale d/d(a ascale)
     float* gs = gscales + (size_t)(im / C) * 4 * HW + p;
     const float qnan = __int_as_float(0x7fc00000);
     int q, A1, A2, A3, A4;
@@ -201,7 +202,7 @@ __device__ __forceinline__ double scaled_weight(unsigned mc, int ec, unsigned lo
 template <int MODE>
 __global__ void __launch_bounds__(256) k_grad_scatter(int Hp, int Wp, int pitch, int P, int H, int W, int C,
                                                       const float* __restrict__ scales, const float* __restrict__ gout,
-                                                      double* __restrict__ hbuf, unsigned* status) {
+                                                      double* __restrict__ hbuf, float ascale, unsigned* status) {
     const int n1 = blockIdx.x * 32 + threadIdx.x;
     const int n2 = blockIdx.y * 8 + threadIdx.y;
     const int im = blockIdx.z;
@@ -210,7 +211,9 @@ __global__ void __launch_bounds__(256) k_grad_scatter(int Hp, int Wp, int pitch,
     const float* pr = scales + (size_t)(im / C) * 4 * HW;
     const float gv = gout[(size_t)im * HW + p];
     int q, A1, A2, A3, A4;
-    if (!grad_scales_of<MODE>(pr[p], pr[HW + p], pr[2 * HW + p], pr[3 * HW + p], q, A1, A2, A3, A4, status)) return;
+    if (!grad_scales_of<MODE>(pr[p] * ascale, pr[HW + p] * ascale, pr[2 * HW + p] * ascale, pr[3 * HW + p] * ascale, q,
+                              A1, A2, A3, A4, status))
+        return;
     const int bx = n1 + P, by = n2 + P;
     if (!taps_inside(bx, by, q, A1, A2, A3, A4, Wp, Hp)) {
         raise_status(status, BSF_EHALO);
@@ -332,22 +335,24 @@ __global__ void __launch_bounds__(256) k_suffix_rows(const double* __restrict__ 
 
 cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp, int Wp, int pitch, int P, int H,
                          int W, int C, int nimg, const float* scales, const float* gout, float* gscales, double* hbuf,
-                         unsigned* status, cudaStream_t st) {
+                         float ascale, unsigned* status, cudaStream_t st) {
     if (mode != MODE_U64 && mode != MODE_U128) return cudaErrorInvalidValue;
     dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nimg);
     if (gscales != nullptr) {
         if (mode == MODE_U64)
             k_grad_scales<MODE_U64><<<grd, blk, 0, st>>>(buf, buf_stride, Hp, Wp, pitch, P, H, W, C, scales, gout,
-                                                          gscales, status);
+                                                          gscales, ascale, status);
         else
             k_grad_scales<MODE_U128><<<grd, blk, 0, st>>>(buf, buf_stride, Hp, Wp, pitch, P, H, W, C, scales, gout,
-                                                           gscales, status);
+                                                           gscales, ascale, status);
     }
     if (hbuf != nullptr) {
         if (mode == MODE_U64)
-            k_grad_scatter<MODE_U64><<<grd, blk, 0, st>>>(Hp, Wp, pitch, P, H, W, C, scales, gout, hbuf, status);
+            k_grad_scatter<MODE_U64><<<grd, blk, 0, st>>>(Hp, Wp, pitch, P, H, W, C, scales, gout, hbuf, ascale,
+                                                           status);
         else
-            k_grad_scatter<MODE_U128><<<grd, blk, 0, st>>>(Hp, Wp, pitch, P, H, W, C, scales, gout, hbuf, status);
+            k_grad_scatter<MODE_U128><<<grd, blk, 0, st>>>(Hp, Wp, pitch, P, H, W, C, scales, gout, hbuf, ascale,
+                                                            status);
     }
     return cudaGetLastError();
 }

@@ -531,6 +531,46 @@ bsf_status bsf_structure_cov(bsf_ctx* c, const void* image, int dtype, int64_t B
     return BSF_OK;
 }
 
+// One backward pass of the filter with widths a * ascale on the input x
+// (dtype): the image gradient into gimage (nullable) and the scale gradient,
+// multiplied by ascale, added into gscales (nullable; zeroed by the caller).
+static bsf_status backward_pass(bsf_ctx* c, const void* x, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                                const float* scales, const float* gout, float* gimage, float* gscales, int P,
+                                float ascale, cudaStream_t st) {
+    const int64_t HW = H * W;
+    const int mode = mode_of(dtype, BSF_PREC_EXACT);
+    const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P, pitch = Wp;
+    const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
+    const size_t per_h = (size_t)Hp * pitch * sizeof(double);
+    const size_t budget = (size_t)16 << 30;
+    int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / ((per_img + per_h) * (size_t)C)));
+    bchunk = std::min<int64_t>(bchunk, B);
+    const size_t esz = (dtype == BSF_U8) ? 1 : 4;
+    for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
+        const int64_t nbat = std::min<int64_t>(bchunk, B - b0);
+        const int nimg = (int)(nbat * C);
+        const scan_plan plan = make_scan_plan(Hp, Wp, nimg, elem_bytes(mode));
+        BSF_TRY(grow(&c->buf, &c->buf_bytes, per_img * nimg));
+        BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
+        double* hb = nullptr;
+        if (gimage) {
+            BSF_TRY(grow(&c->hbuf, &c->hbuf_bytes, per_h * nimg));
+            hb = (double*)c->hbuf;
+            BSF_TRY(cudaMemsetAsync(hb, 0, per_h * nimg, st));
+        }
+        const char* img0 = (const char*)x + (size_t)(b0 * C) * HW * esz;
+        BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf, (long long)Hp * pitch,
+                         pitch, c->work, st));
+        BSF_TRY(launch_grad4(mode, c->buf, (long long)Hp * pitch, Hp, Wp, pitch, P, (int)H, (int)W, (int)C, nimg,
+                             scales + (size_t)b0 * 4 * HW, gout + (size_t)(b0 * C) * HW,
+                             gscales ? gscales + (size_t)b0 * 4 * HW : nullptr, hb, ascale, c->d_status, st));
+        if (gimage)
+            BSF_TRY(launch_transpose_scans(hb, nimg, Hp, Wp, pitch, P, (int)H, (int)W, gimage + (size_t)(b0 * C) * HW,
+                                           st));
+    }
+    return BSF_OK;
+}
+
 bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
                                int N, const float* scales, const float* grad_out, float* grad_image,
                                float* grad_scales, const bsf_opts* opts, void* stream) {
@@ -543,6 +583,7 @@ bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t
     bsf_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != BSF_PREC_EXACT) return BSF_EUNSUPPORTED;
+    if (o.iterations < 1 || o.iterations > 64) return BSF_EINVAL;
     std::lock_guard<std::mutex> lock(c->mu);
     BSF_TRY(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -550,38 +591,47 @@ bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t
     int P = 0;
     bsf_status s = resolve_halo(c, scales, BSF_PARAM_SCALES, B, HW, o, st, &P);
     if (s != BSF_OK) return s;
-    const int mode = mode_of(dtype, o.precision);
-    const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P, pitch = Wp;
-    const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
-    const size_t per_h = (size_t)Hp * pitch * sizeof(double);
-    const size_t budget = (size_t)16 << 30;
-    int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / ((per_img + per_h) * (size_t)C)));
-    bchunk = std::min<int64_t>(bchunk, B);
-    const size_t esz = (dtype == BSF_U8) ? 1 : 4;
     // rows wider than one band CTA holds are rejected before anything runs (the adjoint has no strips)
-    if (!make_scan_plan(Hp, Wp, (int)(bchunk * C), elem_bytes(mode)).ok) return BSF_EINVAL;
+    {
+        const int mode = mode_of(dtype, o.precision);
+        const int Hp = (int)H + 2 * P, Wp = (int)W + 2 * P;
+        const size_t per = (size_t)Hp * Wp * (elem_bytes(mode) + sizeof(double)) * (size_t)C;
+        const int64_t bchunk = std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(((size_t)16 << 30) / per)));
+        if (!make_scan_plan(Hp, Wp, (int)(bchunk * C), elem_bytes(mode)).ok) return BSF_EINVAL;
+        if (dtype == BSF_U8 && o.iterations > 1 &&
+            !make_scan_plan(Hp, Wp, (int)(bchunk * C), elem_bytes(MODE_U128)).ok)
+            return BSF_EINVAL;  // later passes run on float32 intermediates
+    }
     if (grad_scales) BSF_TRY(cudaMemsetAsync(grad_scales, 0, (size_t)B * 4 * HW * sizeof(float), st));
-    for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
-        const int64_t nbat = std::min<int64_t>(bchunk, B - b0);
-        const int nimg = (int)(nbat * C);
-        const scan_plan plan = make_scan_plan(Hp, Wp, nimg, elem_bytes(mode));
-        BSF_TRY(grow(&c->buf, &c->buf_bytes, per_img * nimg));
-        BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
-        double* hb = nullptr;
-        if (grad_image) {
-            BSF_TRY(grow(&c->hbuf, &c->hbuf_bytes, per_h * nimg));
-            hb = (double*)c->hbuf;
-            BSF_TRY(cudaMemsetAsync(hb, 0, per_h * nimg, st));
-        }
-        const char* img0 = (const char*)image + (size_t)(b0 * C) * HW * esz;
-        BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf, (long long)Hp * pitch,
-                         pitch, c->work, st));
-        BSF_TRY(launch_grad4(mode, c->buf, (long long)Hp * pitch, Hp, Wp, pitch, P, (int)H, (int)W, (int)C, nimg,
-                             scales + (size_t)b0 * 4 * HW, grad_out + (size_t)(b0 * C) * HW,
-                             grad_scales ? grad_scales + (size_t)b0 * 4 * HW : nullptr, hb, c->d_status, st));
-        if (grad_image)
-            BSF_TRY(launch_transpose_scans(hb, nimg, Hp, Wp, pitch, P, (int)H, (int)W,
-                                           grad_image + (size_t)(b0 * C) * HW, st));
+    if (o.iterations == 1)
+        return backward_pass(c, image, dtype, B, C, H, W, scales, grad_out, grad_image, grad_scales, P, 1.f, st);
+    // iterated filter (Sec. 3.3): m passes with the widths a / sqrt(m).  The
+    // forward intermediates f_1 .. f_{m-1} are recomputed and kept; the passes
+    // are then differentiated in reverse, each image gradient feeding the next
+    // and every pass adding its scale gradient (times 1/sqrt(m)).
+    const int m = o.iterations;
+    const float asc = 1.f / sqrtf((float)m);
+    const size_t n = (size_t)(B * C * HW);
+    BSF_TRY(grow(&c->iter, &c->iter_bytes, (size_t)(m + 1) * n * sizeof(float)));
+    float* fk = (float*)c->iter;          // f_1 .. f_{m-1}
+    float* g0 = fk + (size_t)(m - 1) * n;  // gradient ping-pong
+    float* g1 = g0 + n;
+    bsf_opts of = o;
+    of.iterations = 1;
+    if (o.max_scale > 0.f) of.max_scale = o.max_scale * asc;
+    of.halo = P;
+    for (int k = 1; k < m; ++k) {
+        s = filter_pass(c, k == 1 ? image : (const void*)(fk + (size_t)(k - 2) * n), k == 1 ? dtype : BSF_F32, B, C,
+                        H, W, scales, BSF_PARAM_SCALES, of, fk + (size_t)(k - 1) * n, st, asc);
+        if (s != BSF_OK) return s;
+    }
+    const float* g = grad_out;
+    for (int k = m; k >= 1; --k) {
+        const void* x = k == 1 ? image : (const void*)(fk + (size_t)(k - 2) * n);
+        float* gi = k == 1 ? grad_image : (g == g0 ? g1 : g0);
+        s = backward_pass(c, x, k == 1 ? dtype : BSF_F32, B, C, H, W, scales, g, gi, grad_scales, P, asc, st);
+        if (s != BSF_OK) return s;
+        g = gi;
     }
     return BSF_OK;
 }

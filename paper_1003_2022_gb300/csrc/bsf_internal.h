@@ -51,9 +51,11 @@ cudaError_t launch_extent4(const float* params, int kind, long long npix, float 
                            cudaStream_t st);
 
 // Adjoint (adjoint4.cu).
+// ascale multiplies the widths (1/sqrt(m) in a pass of the m-fold iterated
+// filter) and, by the chain rule, the scale gradient
 cudaError_t launch_grad4(int mode, const void* buf, long long buf_stride, int Hp, int Wp, int pitch, int P, int H,
                          int W, int C, int nimg, const float* scales, const float* gout, float* gscales, double* hbuf,
-                         unsigned* status, cudaStream_t st);
+                         float ascale, unsigned* status, cudaStream_t st);
 cudaError_t launch_transpose_scans(double* hbuf, int nimg, int Hp, int Wp, int pitch, int P, int H, int W,
                                    float* gimage, cudaStream_t st);
 

@@ -97,3 +97,39 @@ def test_autograd_learnable_scales_workload():
         got_s = np.stack([[gsc[b, k][y0 + (p // wwid - M), x0 + (p % wwid - M)] for p in loc[:40]]
                           for k in range(4)])
         assert _nerr(got_s, fd) < 1e-4
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_iterated_filter_gradients(m):
+    """The m-fold iterated filter (Sec. 3.3) through autograd: the image gradient
+    equals the transpose applied m times (each pass with a / sqrt(m)), the
+    scale gradient the central differences of the iterated plain definition."""
+    dev = _cuda()
+    H, W = 26, 30
+    rng = np.random.default_rng(50 + m)
+    f = synth.image(H, W, seed=50 + m, dtype="f32")
+    a = rng.uniform(1.0, 5.0, size=(4, H, W)).astype(np.float32)
+    g = rng.standard_normal((H, W)).astype(np.float32)
+    fi = torch.from_numpy(f).to(dev).requires_grad_(True)
+    sc = torch.from_numpy(a).to(dev).requires_grad_(True)
+    (api.box_spline_filter(fi, sc, max_scale=5.0, iterations=m) * torch.from_numpy(g).to(dev)).sum().backward()
+    assert api.device_status(dev) == 0
+    a64 = a.astype(np.float64) / np.sqrt(m)
+    gref = g.astype(np.float64)
+    allpx = np.arange(H * W)
+    for _ in range(m):
+        gref = O.adjoint4(gref, a64, allpx).reshape(H, W)
+    assert _nerr(fi.grad.cpu().numpy(), gref) < 1e-5
+    # scale gradient on sampled pixels: central differences of sum(g * K^m f)
+    idx = rng.choice(H * W, size=12, replace=False)
+    h = 1e-3
+    f64, g64, a0 = f.astype(np.float64), g.astype(np.float64), a.astype(np.float64)
+    fd = np.empty((4, idx.size))
+    for k in range(4):
+        for j, pix in enumerate(idx):
+            ap, am = a0.copy(), a0.copy()
+            ap[k].flat[pix] += h
+            am[k].flat[pix] -= h
+            fd[k, j] = (np.sum(g64 * O.direct4_iterated(f64, ap, m)) - np.sum(g64 * O.direct4_iterated(f64, am, m))) / (2 * h)
+    got = sc.grad.cpu().numpy().reshape(4, -1)[:, idx]
+    assert _nerr(got, fd) < 1e-4
