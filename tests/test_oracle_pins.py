@@ -491,3 +491,20 @@ def test_iterated_splines_approach_the_gaussian():
     assert 0.93 < worst[1] < 0.975, worst
     assert worst[2] > 0.985, worst
     assert worst[2] > worst[1]
+
+
+def test_beta4_is_c1_but_not_c2():
+    """Smoothness C^{N-3} = C^1 (Sec. 2.2.1): along a line through the support the
+    first differences change by O(h) between neighbouring steps everywhere,
+    while the second differences jump by O(1) where the line crosses a knot."""
+    a = np.array([2.3, 1.7, 3.1, 2.6])
+    h = 1e-3
+    t = np.arange(-4.0, 4.0, h)
+    # a line in a generic direction, so that it crosses knot lines transversally
+    x1, x2 = 0.83 * t + 0.11, 0.56 * t - 0.07
+    b = O.beta4_grid(a, x1, x2)
+    d1 = np.diff(b) / h
+    d2 = np.diff(d1) / h
+    assert np.abs(np.diff(d1)).max() < 50 * h          # first derivative continuous
+    assert np.abs(np.diff(d2)).max() > 1e-2            # second derivative jumps somewhere
+    assert np.abs(b).max() > 0.05
