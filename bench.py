@@ -572,6 +572,49 @@ def run_smooth(args):
     return 0
 
 
+def run_sizes(args):
+    """Run time against kernel size (the paper's computation-time table): one
+    2048x2048 u8 image filtered with a constant (sigma, rho, theta) field for
+    sigma = 1 .. 32 px; the halo of the pre-integrated buffer grows with sigma,
+    the per-pixel work of the finite difference does not."""
+    import torch
+    from paper_1003_2022_gb300 import _lib as L
+    from paper_1003_2022_gb300 import api, synth
+    dev = torch.device("cuda:0")
+    H = W = args.size or 2048
+    f = torch.from_numpy(synth.image(H, W, seed=0, dtype="u8")).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ctx = api.context(dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for rho, theta in ((1.0, 0.0), (4.0, 0.4)):
+        for sigma in (1.0, 2.0, 4.0, 8.0, 16.0, 32.0):
+            prm = torch.from_numpy(synth.constant_srt(H, W, sigma, rho, theta)).to(dev)
+            out = torch.empty((H, W), dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                api.filter(f, prm, kind="srt", max_scale=sigma, out=out)
+            torch.cuda.synchronize(dev)
+            L.bsf_profile_begin(ctx)
+            evs = []
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                api.filter(f, prm, kind="srt", max_scale=sigma, out=out)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            ms_pre, ms_st, nl = L.bsf_profile_end(ctx)
+            rows.append({"sigma": sigma, "rho": rho, "theta": theta, "halo": api.halo_for(sigma),
+                         "ms_per_step": sum(a.elapsed_time(b) for a, b in evs) / args.steps,
+                         "stencil_ms": ms_st / nl, "preintegrate_ms": ms_pre / nl})
+    if api.device_status(dev) & ~(1 << L.BSF_EINFEASIBLE):
+        raise RuntimeError("device status error")
+    print(json.dumps({"mode": "sizes", "workload": f"{H}x{W} u8, constant (sigma, rho, theta) fields",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,7 +625,7 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")
-    ap.add_argument("--mode", default="filter", choices=["filter", "serve", "smooth"])
+    ap.add_argument("--mode", default="filter", choices=["filter", "serve", "smooth", "sizes"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(BENCH_WORKLOADS))
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--slots", type=int, default=4)
@@ -599,6 +642,8 @@ def main():
         return run_serve(args)
     if args.mode == "smooth":
         return run_smooth(args)
+    if args.mode == "sizes":
+        return run_sizes(args)
     return run_ours(args)
 
 

@@ -33,6 +33,7 @@ class Request:
     N: int = 4
     arrival: float = 0.0         # seconds after the stream start
     max_scale: float = 0.0       # largest sigma of the field (0: take it from params)
+    cancel_at: float = math.inf  # withdrawn at this time (seconds) if not admitted by then
 
 
 @dataclass
@@ -54,6 +55,16 @@ class Result:
 def halo_for_sigma(max_sigma: float) -> int:
     # the library's rule for COV/SRT fields: ext <= 8.364 sigma_max, P = ceil(ext/2) + 4
     return int(math.ceil(0.5 * 8.3640 * max_sigma)) + 4
+
+
+def _max_sigma(params) -> float:
+    """Largest finite sigma of a (sigma, rho, theta) field (NaN pixels ignored)."""
+    s0 = params[0]
+    if hasattr(s0, "nan_to_num"):
+        return float(s0.nan_to_num(nan=0.0, posinf=0.0).max())
+    s0 = np.asarray(s0)
+    fin = s0[np.isfinite(s0)]
+    return float(fin.max()) if fin.size else 0.0
 
 
 def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: float) -> int:
@@ -114,6 +125,14 @@ class Scheduler:
         self.pending.extendleft(reversed(skipped))
         return out
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a queued request; False if it is not queued (admitted or unknown)."""
+        for i, (r, _) in enumerate(self.pending):
+            if r == rid:
+                del self.pending[i]
+                return True
+        return False
+
     def complete(self, rid: int) -> int:
         """Release a finished request's memory and slot; returns the slot."""
         self._used -= self.inflight.pop(rid)
@@ -167,7 +186,7 @@ class Server:
                 prm = prm_h.to(self.dev, non_blocking=True)
             out = torch.empty((C, H, W), dtype=torch.float32, device=self.dev)
             opts = L.default_opts()
-            opts.max_scale = float(req.max_scale or float(req.params[0].max()))
+            opts.max_scale = float(req.max_scale or _max_sigma(req.params))
             dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
             rc = L.bsf_filter(self.ctxs[slot], img.data_ptr(), dtype, 1, C, H, W, req.N, prm.data_ptr(),
                               L.BSF_PARAM_SRT, opts, out.data_ptr(), int(st.cuda_stream))
@@ -187,6 +206,9 @@ class Server:
         results = {r.rid: Result(r.rid, "pending", t_arrival=r.arrival, samples=int(np.prod(tuple(r.image.shape))))
                    for r in reqs}
         running: dict[int, tuple] = {}
+        # withdrawals in time order; one that falls before its own arrival is applied at arrival
+        cancels = sorted((max(r.cancel_at, r.arrival), r.rid) for r in reqs if r.cancel_at < math.inf)
+        ci = 0
         nxt = 0
         t0 = time.perf_counter()
         max_depth = 0
@@ -197,19 +219,35 @@ class Server:
                 nxt += 1
                 C, H, W = r.image.shape
                 isz = r.image.element_size() if self.torch.is_tensor(r.image) else r.image.dtype.itemsize
-                nb = footprint_bytes(C, H, W, isz, r.max_scale or float(r.params[0].max()))
+                nb = footprint_bytes(C, H, W, isz, r.max_scale or _max_sigma(r.params))
                 results[r.rid].nbytes = nb
                 why = self.sched.offer(r.rid, nb, r.N)
                 if why is not None:
                     results[r.rid].status = why
                     results[r.rid].t_done = now
+            while ci < len(cancels) and cancels[ci][0] <= now:
+                rid = cancels[ci][1]
+                ci += 1
+                if results[rid].status == "pending" and self.sched.cancel(rid):
+                    results[rid].status = "cancelled"
+                    results[rid].t_done = now
             for rid in list(running):
                 rc, ev, keep = running[rid]
                 if ev.query():
                     t = time.perf_counter() - t0
                     res = results[rid]
                     res.t_done = t
-                    res.status = "ok" if rc == self.L.BSF_OK else f"bsf status {rc}"
+                    slot = self.sched.slot_of[rid]
+                    # per-pixel conditions of this request (the slot's context serves one request at a time)
+                    dev_st = self.L.bsf_get_device_status(self.ctxs[slot], int(self.streams[slot].cuda_stream))
+                    bad = dev_st & ~(1 << self.L.BSF_EINFEASIBLE)
+                    if rc != self.L.BSF_OK:
+                        res.status = f"bsf status {rc}"
+                    elif bad:
+                        codes = [c for c in range(1, 32) if bad & (1 << c)]
+                        res.status = "invalid pixels: " + "; ".join(self.L.status_string(c) for c in codes)
+                    else:
+                        res.status = "ok"
                     if keep[5] is not None:
                         res.out = keep[5].numpy()
                     self.sched.complete(rid)
@@ -223,8 +261,11 @@ class Server:
         makespan = time.perf_counter() - t0
         done = [r for r in results.values() if r.status == "ok"]
         samples = sum(r.samples for r in done)
+        n_cancel = sum(r.status == "cancelled" for r in results.values())
+        n_invalid = sum(r.status.startswith("invalid") for r in results.values())
         stats = {"requests": len(reqs), "completed": len(done),
-                 "rejected": len(reqs) - len(done), "makespan_s": makespan,
+                 "rejected": len(reqs) - len(done) - n_cancel - n_invalid, "cancelled": n_cancel,
+                 "invalid": n_invalid, "makespan_s": makespan,
                  "gpixels_per_s": samples / makespan / 1e9, "peak_bytes": self.sched.peak_bytes,
                  "max_queue_depth": max_depth}
         stats.update(percentiles([r.latency for r in done]))

@@ -50,3 +50,33 @@ def test_results_same_alone_and_in_the_mix():
         err = np.abs(r.out - alone).max() / np.abs(alone).max()
         assert err <= 1e-5, (r.rid, err)
     assert stats["p50_ms"] is not None and stats["p99_ms"] >= stats["p50_ms"]
+
+
+def test_malformed_and_cancelled_requests():
+    """A request whose field holds NaN is served with its pixels flagged (the
+    device status names the condition), a request withdrawn before admission
+    never runs, and the others are unaffected."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(8)
+    reqs = []
+    for i in range(6):
+        img = synth.image(64, 72, seed=200 + i, dtype="f32")[None]
+        prm = synth.srt_field(64, 72, seed=200 + i, sigma=(1.0, 4.0), rho=(1.0, 3.0))
+        if i == 2:
+            prm[0, 10:20, 10:20] = np.nan
+        reqs.append(Request(i, img, prm, N=4, arrival=0.0, max_scale=4.0))
+    reqs[5].cancel_at = 0.0   # withdrawn at once: one slot, so it cannot have been admitted
+    srv = Server(slots=1, budget_bytes=64 << 20, device=0)
+    try:
+        results, stats = srv.run(reqs)
+    finally:
+        srv.close()
+    assert results[2].status.startswith("invalid pixels"), results[2].status
+    out = results[2].out
+    nan = np.isnan(out)
+    assert nan[0, 10:20, 10:20].all() and nan.sum() == 100
+    assert np.isfinite(out[~nan]).all()
+    assert results[5].status == "cancelled" and results[5].out is None
+    assert all(results[i].status == "ok" for i in (0, 1, 3, 4))
+    assert stats["cancelled"] == 1 and stats["invalid"] == 1 and stats["completed"] == 4

@@ -76,3 +76,15 @@ def test_footprint_grows_with_size_channels_and_sigma():
     assert footprint_bytes(1, 512, 512, 4, 2.0) > 3.5 * f1
     assert footprint_bytes(1, 256, 256, 4, 40.0) > f1
     assert footprint_bytes(1, 256, 256, 1, 2.0) < f1
+
+
+def test_cancel_only_queued_requests():
+    s = Scheduler(slots=1, budget_bytes=100)
+    assert s.offer(1, 10, 4) is None and s.offer(2, 10, 4) is None and s.offer(3, 10, 4) is None
+    assert s.admit() == [(1, 0)]
+    assert s.cancel(2) is True          # queued: withdrawn
+    assert s.cancel(2) is False         # already gone
+    assert s.cancel(1) is False         # in flight: runs to completion
+    assert s.cancel(99) is False        # unknown
+    s.complete(1)
+    assert s.admit() == [(3, 0)]
