@@ -30,6 +30,11 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
   smoothing application (Sec. 4.2): structure tensor J = w * (g g^T) with the
   plain-definition window, C = sigma0^2 adj(J + tau I) / sqrt(det(J + tau I)).
 
+* ``n6`` (module): the six-directional spline (pointwise by two independent
+  methods), its filter on the hexagonal lattice that the six directions need
+  (the transfer of the image, the plain definition on it, Algorithm 1 on the
+  lattice) and the N-directional map solved through its optimality conditions.
+
 The C source is ``bsf_oracle.c``; it is compiled with gcc on first use (or by
 ``__graft_entry__.build()``) into ``oracle/_build/``.
 """
@@ -396,3 +401,6 @@ def gaussian_correlation(theta, a, C, m: int = 1, half_width: float | None = Non
     b = box_spline_hat(theta, np.asarray(a, float) / np.sqrt(m), W1, W2) ** m
     gh = np.exp(-0.5 * (C[0, 0] * W1 * W1 + 2 * C[0, 1] * W1 * W2 + C[1, 1] * W2 * W2))
     return float(np.sum(b * gh) / np.sqrt(np.sum(b * b) * np.sum(gh * gh)))
+
+
+from . import n6  # noqa: E402,F401  (six-directional oracle)
