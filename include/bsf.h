@@ -39,7 +39,31 @@
  *     (a tap outside the pre-integrated buffer, an invalid scale) are OR-ed
  *     into a device status word read by bsf_get_device_status; the affected
  *     output pixels are NaN.
- *   - Only N = 4 is implemented; other N return BSF_EUNSUPPORTED.
+ *   - N = 4 (theta_k = 0, 45, 90, 135 degrees) is implemented by every entry
+ *     point.  N = 6 (theta_k = 0, 30, ..., 150 degrees) is implemented by
+ *     bsf_filter, bsf_filter_host and bsf_scales_from_cov; the other entry
+ *     points return BSF_EUNSUPPORTED for it, and any other N returns
+ *     BSF_EUNSUPPORTED everywhere.
+ *
+ * N = 6.  Algorithm 1 needs every running-sum direction b_k u_k to be a
+ * lattice vector, which on the pixel lattice holds for N = 2, 4 only; for
+ * more directions the paper notes that the image has to be interpolated
+ * (Sec. 3.3).  The reading implemented: the image f = sum_k f[k] delta(x - k)
+ * is transferred once to the hexagonal lattice Lambda_h = { h (i + j/2,
+ * j sqrt3/2) } (opts.hex_spacing = h), each pixel's mass shared among the
+ * vertices of the lattice triangle that holds it in proportion to its
+ * barycentric coordinates (mass and centre of mass of every pixel kept).  All
+ * six directions are lattice vectors of Lambda_h, so Algorithm 1 is exact
+ * there: the filter computed is (1) with the pixel comb replaced by that
+ * measure, fbar[n] = sum_{m in Lambda_h} mu[m] beta^6_{a(n)}(n - m), in FP64
+ * (opts.precision is ignored).  Its difference from (1) itself -- the method
+ * error of the transfer -- falls like h^2 (about 4e-4 relative for a 2 px
+ * kernel at h = 0.5 on a smooth image).  The scale map for six directions is
+ * the criterion of Sec. 3.2.2 with the kurtosis norm written for six
+ * directions, sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m), under the same
+ * eps, eta and flags; elongations are clamped at the six-directional bound
+ * (1 + r)/(1 - r), r = cos(pi/6)/cos(psi - pi/6), psi = 2 theta mod pi/3
+ * (at least 13.93; unbounded along the six directions).
  */
 #ifndef BSF_H
 #define BSF_H
@@ -54,7 +78,7 @@ extern "C" {
 typedef int bsf_status;
 #define BSF_OK 0
 #define BSF_EINVAL 1          /* bad argument (null pointer, size, kind, dtype) */
-#define BSF_EUNSUPPORTED 2    /* N other than 4 */
+#define BSF_EUNSUPPORTED 2    /* N not implemented by this entry point (see above) */
 #define BSF_ENOMEM 3          /* device allocation of scratch failed */
 #define BSF_ECUDA 4           /* a CUDA runtime call failed */
 #define BSF_EHALO 5           /* device: a tap fell outside the pre-integrated buffer */
@@ -96,6 +120,9 @@ typedef struct {
                          i.e. run the path m times with the scale vector a/sqrt(m) (the
                          covariance of each pass is C/m, of the m passes together C).
                          Passes after the first take the float32 output of the previous one. */
+    float hex_spacing;  /* N = 6 only: spacing h (px) of the hexagonal lattice the image is
+                         transferred to, in [0.125, 1]; default 0.5.  The method error of the
+                         transfer falls like h^2, the pre-integration work grows like 1/h^2. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -116,7 +143,12 @@ bsf_status bsf_destroy(bsf_ctx* ctx);
  * image: B*C*H*W elements of `dtype`; params: B*K*H*W floats of `kind`;
  * out: B*C*H*W floats.  Runs the scale map (Sec. 3.2.2, for COV/SRT), the
  * pre-integration (Algorithm 1 step 2) and the finite difference with ZP
- * interpolation (Algorithm 1 step 3).  opts may be NULL (defaults). */
+ * interpolation (Algorithm 1 step 3).  opts may be NULL (defaults).
+ * N = 6 (see the top of this file): each 64 x 64 tile of output pixels gets
+ * its own window of the hexagonal lattice, sized from the tile's largest
+ * footprint; the call synchronises the stream once (after the scale map) to
+ * plan the windows.  Footprints wider than about 1000 px along x
+ * (hex_spacing 0.5) return BSF_EINVAL. */
 bsf_status bsf_filter(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                       int64_t W, int N, const float* params, int kind, const bsf_opts* opts,
                       float* out, void* stream);
@@ -162,9 +194,10 @@ bsf_status bsf_structure_cov(bsf_ctx* ctx, const void* image, int dtype, int64_t
                              int64_t W, float sigma_w, float sigma0, float tau, float* cov, void* stream);
 
 /* Step (b), Sec. 3.2.2: covariance (COV) or (sigma, rho, theta) (SRT) planes
- * (3*npix floats) -> scale planes a_1..a_4 (4*npix floats, Eq. const widths).
- * flags (nullable, npix bytes): bit0 elongation clamped (Prop. 3.1), bit1
- * p >= eps infeasible (p raised to eps), bit2 invalid input (scales NaN). */
+ * (3*npix floats) -> scale planes a_1..a_N (N*npix floats, Eq. const widths),
+ * N = 4 or 6.  flags (nullable, npix bytes): bit0 elongation clamped (Prop.
+ * 3.1; for N = 6 the six-directional bound), bit1 p >= eps infeasible (the
+ * minimiser over p >= 0 raised to eps), bit2 invalid input (scales NaN). */
 bsf_status bsf_scales_from_cov(bsf_ctx* ctx, const float* params, int kind, int64_t npix, int N,
                                const bsf_opts* opts, float* scales, uint8_t* flags, void* stream);
 

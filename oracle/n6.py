@@ -201,16 +201,18 @@ def hex_position(i, j, h: float):
     return h * (i + 0.5 * j), h * j * (SQRT3 / 2.0)
 
 
-def hex_splat(f, h: float):
+def hex_splat(f, h: float, origin=(0, 0)):
     """Transfer of the image f[y, x] (zero outside) to Lambda_h: the mass f[k]
     of pixel k = (x, y) is shared between the vertices of the lattice triangle
-    that contains k, in proportion to its barycentric coordinates.  Returns
+    that contains k, in proportion to its barycentric coordinates.  With
+    ``origin`` = (ox, oy), pixel (x, y) of f sits at (x + ox, y + oy) of the
+    plane that holds the lattice (f is a crop of a larger image).  Returns
     (I, J, mass) for the lattice points that receive mass."""
     f = np.asarray(f, float)
     H, W = f.shape
     yy, xx = np.mgrid[0:H, 0:W]
-    t = 2.0 * yy / (h * SQRT3)
-    s = xx / h - 0.5 * t
+    t = 2.0 * (yy + origin[1]) / (h * SQRT3)
+    s = (xx + origin[0]) / h - 0.5 * t
     i = np.floor(s).astype(np.int64)
     j = np.floor(t).astype(np.int64)
     sg = s - i
@@ -256,14 +258,18 @@ def direct6(f, a, idx=None) -> np.ndarray:
     return out
 
 
-def direct6_hex(f, a, idx=None, h: float = 0.5) -> np.ndarray:
+def direct6_hex(f, a, idx=None, h: float = 0.5, origin=(0, 0)) -> np.ndarray:
     """The six-directional filter as defined on the hexagonal lattice: the
-    plain definition applied to the transferred measure (module docstring)."""
+    plain definition applied to the transferred measure (module docstring).
+    ``origin``: as in ``hex_splat`` (f and a are crops whose pixel (0, 0) sits
+    at origin; the result is exact for pixels whose footprint the crop holds)."""
     f = np.asarray(f, float)
     H, W = f.shape
     th = directions(6)
-    I, J, mass = hex_splat(f, h)
+    I, J, mass = hex_splat(f, h, origin)
     PX, PY = hex_position(I, J, h)
+    PX = PX - origin[0]
+    PY = PY - origin[1]
     idx, nx, ny = _pixels(idx, H, W)
     out = np.empty(idx.size)
     for o, (x, y, p) in enumerate(zip(nx, ny, idx)):
@@ -344,18 +350,20 @@ def alg1_hex(f, a, idx=None, h: float = 0.5) -> np.ndarray:
 # covariance -> scales for N directions
 # ----------------------------------------------------------------------------
 
-def U_boundN(phi: float, N: int) -> float:
+def U_boundN(phi: float, N: int, shrink: float = 1.0) -> float:
     """Largest elongation of an N-directional box spline oriented at phi.  The
     covariance (1/12) sum p_k u_k u_k^T with p >= 0, divided by its trace, has
     the traceless part (1/2) z R, R the reflection at angle 2 phi, where z runs
     over the convex hull of the points exp(2 i theta_k): a regular N-gon
     inscribed in the unit circle.  At the angle 2 phi its boundary is at radius
     r = cos(pi/N) / cos(psi - pi/N), psi = 2 phi mod 2 pi/N, and the elongation
-    is (1 + r)/(1 - r).  For N = 4 this is Prop. 3.1's U(theta)."""
+    is (1 + r)/(1 - r).  For N = 4 this is Prop. 3.1's U(theta).  With
+    ``shrink`` < 1 the polygon is scaled by it: the bound when every p_k must
+    keep a share (1 - shrink)/N of the trace."""
     psi = math.fmod(2.0 * phi, 2.0 * math.pi / N)
     if psi < 0:
         psi += 2.0 * math.pi / N
-    r = math.cos(math.pi / N) / math.cos(psi - math.pi / N)
+    r = shrink * math.cos(math.pi / N) / math.cos(psi - math.pi / N)
     if r >= 1.0:
         return math.inf
     return (1.0 + r) / (1.0 - r)
@@ -458,9 +466,9 @@ def _cov_from_params(v0, v1, v2, kind):
     """(C11, C12, C22) and the descriptors (lmax, lmin, theta) of one pixel; kind 1
     = covariance, kind 2 = (sigma, rho, theta) with lmax = sigma^2, lmin = lmax/rho."""
     if kind == 2:
-        lmax = v0 * v0
-        lmin = lmax / v1
-        th = v2
+        lmax = float(v0) * float(v0)
+        lmin = lmax / float(v1) if v1 != 0 else math.inf
+        th = float(v2)
     else:
         tr = v0 + v2
         d = math.sqrt((v0 - v2) ** 2 + 4 * v1 * v1)
@@ -470,13 +478,21 @@ def _cov_from_params(v0, v1, v2, kind):
     return lmax, lmin, th
 
 
+REL_BOUND6 = 1e-3
+
+
 def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
     """Per-pixel scales for N = 6 from covariance planes (kind 1) or (sigma,
     rho, theta) planes (kind 2), shape (3, ...).  The same conventions as the
-    four-directional map: elongations beyond U_boundN are lowered to
+    four-directional map, except the lower bound: p_k >= max(eps, 1e-3 T),
+    T = sum_k p_k = 12 tr C (reading: the bound of Eq. opt1 is any small
+    positive number; taken relative to the size, it keeps the smallest width
+    at least 0.077 times the typical one, which the FP64 six-directional path
+    needs for its accuracy).  Elongations beyond the bound U of that
+    constraint (U_boundN with the hexagon scaled by 1 - 6e-3) are lowered to
     (1 - eta) U keeping lmax + lmin and the orientation (flag 1); when no
-    p >= eps reproduces the covariance, the minimiser over p >= 0 is raised to
-    eps (flag 2); invalid input gives NaN scales (flag 4).
+    p >= bound reproduces the covariance, the minimiser over p >= 0 is raised
+    to the bound (flag 2); invalid input gives NaN scales (flag 4).
     Returns (a of shape (6, ...), flags uint8)."""
     P = np.asarray(params, float)
     shp = P.shape[1:]
@@ -492,7 +508,7 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
             flags[p] = FLAG_INVALID
             continue
         fl = 0
-        U = U_boundN(th, 6)
+        U = U_boundN(th, 6, 1.0 - 6.0 * REL_BOUND6)
         if lmax / lmin > (1.0 - eta) * U:
             s = lmax + lmin
             lmin = s / (1.0 + (1.0 - eta) * U)
@@ -504,10 +520,11 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
             m, d = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
             C = np.array([[m + d * math.cos(2 * th), d * math.sin(2 * th)],
                           [d * math.sin(2 * th), m - d * math.cos(2 * th)]])
-        pk, ok = mapN_kkt(th6, C, eps)
+        bound = max(eps, REL_BOUND6 * 12.0 * (C[0, 0] + C[1, 1]))
+        pk, ok = mapN_kkt(th6, C, bound)
         if not ok:
             pk, ok = mapN_kkt(th6, C, 0.0)
-            pk = np.maximum(pk, eps)
+            pk = np.maximum(pk, bound)
             fl |= FLAG_INFEASIBLE
         a[:, p] = np.sqrt(pk)
         flags[p] = fl

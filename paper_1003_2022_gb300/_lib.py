@@ -52,6 +52,7 @@ class bsf_opts(ctypes.Structure):
         ("halo", ctypes.c_int),
         ("max_scale", ctypes.c_float),
         ("iterations", ctypes.c_int),
+        ("hex_spacing", ctypes.c_float),
     ]
 
 

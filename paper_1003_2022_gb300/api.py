@@ -41,9 +41,10 @@ def _stream_ptr(stream) -> int:
 
 
 def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False,
-              iterations=1) -> L.bsf_opts:
+              iterations=1, hex_spacing=0.5) -> L.bsf_opts:
     o = L.default_opts()
     o.iterations = int(iterations)
+    o.hex_spacing = float(hex_spacing)
     o.precision = _PREC[precision]
     o.halo = int(halo)
     o.max_scale = float(max_scale)
@@ -65,9 +66,12 @@ def _as4d(image: torch.Tensor) -> torch.Tensor:
 
 def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int = 4, precision: str = "exact",
            halo: int = 0, max_scale: float = 0.0, eps: float = 1e-3, eta: float = 1e-3, strict: bool = False,
-           out: torch.Tensor | None = None, stream=None, iterations: int = 1) -> torch.Tensor:
+           out: torch.Tensor | None = None, stream=None, iterations: int = 1,
+           hex_spacing: float = 0.5) -> torch.Tensor:
     """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k).
 
+    N = 4 or 6 directions; N = 6 runs on the hexagonal lattice of spacing
+    hex_spacing (the C header describes the transfer of the image to it).
     iterations = m > 1 applies the iterated box spline of Sec. 3.3 (m passes
     with the widths a / sqrt(m))."""
     img = _as4d(image)
@@ -81,13 +85,13 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
     if prm.dtype != torch.float32 or not prm.is_cuda:
         raise ValueError("params must be a float32 CUDA tensor")
     prm = prm.contiguous()
-    K = 4 if kind == "scales" else 3
+    K = N if kind == "scales" else 3
     if tuple(prm.shape) != (B, K, H, W):
         raise ValueError(f"params shape {tuple(prm.shape)} != {(B, K, H, W)}")
     if out is None:
         out = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device)
     dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
-    opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations)
+    opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations, hex_spacing)
     rc = L.bsf_filter(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), _KINDS[kind],
                       opts, out.data_ptr(), _stream_ptr(stream))
     L.check(rc, "bsf_filter")
@@ -96,12 +100,12 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
 
 def scales_from_cov(params: torch.Tensor, kind: str = "srt", N: int = 4, eps: float = 1e-3, eta: float = 1e-3,
                     stream=None):
-    """Per-pixel optimal scale vectors (Sec. 3.2.2): (3, ...) planes -> ((4, ...), flags uint8)."""
+    """Per-pixel optimal scale vectors (Sec. 3.2.2): (3, ...) planes -> ((N, ...), flags uint8)."""
     prm = params.contiguous()
     if prm.dtype != torch.float32 or not prm.is_cuda or prm.shape[0] != 3:
         raise ValueError("params must be a float32 CUDA tensor of shape (3, ...)")
     npix = prm[0].numel()
-    scales = torch.empty((4,) + tuple(prm.shape[1:]), dtype=torch.float32, device=prm.device)
+    scales = torch.empty((N,) + tuple(prm.shape[1:]), dtype=torch.float32, device=prm.device)
     flags = torch.empty(tuple(prm.shape[1:]), dtype=torch.uint8, device=prm.device)
     opts = make_opts(eps=eps, eta=eta)
     rc = L.bsf_scales_from_cov(context(prm.device), prm.data_ptr(), _KINDS[kind], npix, N, opts,

@@ -39,6 +39,16 @@ struct bsf_ctx {
     } hs[2];
     cudaStream_t s_h2d, s_comp, s_d2h;
     unsigned long long host_calls;
+    // six-directional path (hex6.cu): FP64 scales, per-tile footprint extents,
+    // window records and the lattice windows themselves
+    void* h6_scales = nullptr;
+    size_t h6_scales_bytes = 0;
+    void* h6_ext = nullptr;
+    size_t h6_ext_bytes = 0;
+    void* h6_tiles = nullptr;
+    size_t h6_tiles_bytes = 0;
+    void* h6_win = nullptr;
+    size_t h6_win_bytes = 0;
     bool profiling;
     size_t prof_used;                                // event triples recorded since begin
     std::vector<std::array<cudaEvent_t, 3>> prof;    // pool of event triples
@@ -107,13 +117,14 @@ void bsf_default_opts(bsf_opts* o) {
     o->halo = 0;
     o->max_scale = 0.f;
     o->iterations = 1;
+    o->hex_spacing = 0.5f;
 }
 
 const char* bsf_status_string(bsf_status s) {
     switch (s) {
         case BSF_OK: return "ok";
         case BSF_EINVAL: return "invalid argument";
-        case BSF_EUNSUPPORTED: return "unsupported N (only N = 4 is implemented)";
+        case BSF_EUNSUPPORTED: return "unsupported N (N = 4 everywhere; N = 6 in bsf_filter, bsf_filter_host and bsf_scales_from_cov)";
         case BSF_ENOMEM: return "device allocation failed";
         case BSF_ECUDA: return "CUDA runtime error";
         case BSF_EHALO: return "a finite-difference tap left the pre-integrated buffer (halo too small)";
@@ -175,6 +186,8 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->hbuf) cudaFree(c->hbuf);
     if (c->iter) cudaFree(c->iter);
     if (c->stbuf) cudaFree(c->stbuf);
+    for (void* p6 : {c->h6_scales, c->h6_ext, c->h6_tiles, c->h6_win})
+        if (p6) cudaFree(p6);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& h : c->hs) {
         if (h.img) cudaFree(h.img);
@@ -247,12 +260,15 @@ bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_
                                float* scales, uint8_t* flags, void* stream) {
     if (!c || !params || !scales || npix < 0) return BSF_EINVAL;
     if (kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
-    if (N != 4) return BSF_EUNSUPPORTED;
+    if (N != 4 && N != 6) return BSF_EUNSUPPORTED;
     bsf_opts o;
     bsf_default_opts(&o);
     if (opts) o = *opts;
     BSF_TRY(cudaSetDevice(c->device));
-    BSF_TRY(launch_map4(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
+    if (N == 6)
+        BSF_TRY(launch_map6_out(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
+    else
+        BSF_TRY(launch_map4(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
     return BSF_OK;
 }
 
@@ -375,6 +391,113 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
     return BSF_OK;
 }
 
+// the six-directional filter on the hexagonal lattice (hex6.cu); the caller
+// holds the context lock.  One synchronisation: the windows are planned on the
+// host from the largest footprint of every 16 x 16 block, which the scale map
+// reduces.  Output tiles are 64 x 64 pixels, or 16 x 16 where the footprints
+// are small: the window of a tile spans the tile plus the footprint, and the
+// FP64 running sums over it grow with its size to the sixth power, so small
+// kernels get small windows.
+static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                          const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
+                          float ascale = 1.f) {
+    const int fine = 16, coarse = 64, ratio = coarse / fine;
+    const float split_below = 48.f;  // px: largest half-extent for which a 64-tile is cut into 16-tiles
+    const double h = (double)o.hex_spacing;
+    const int64_t HW = H * W;
+    const int fx = (int)((W + fine - 1) / fine), fy = (int)((H + fine - 1) / fine);
+    const int64_t nfine = (int64_t)fx * fy;
+    const size_t ext_bytes = (size_t)B * nfine * 2 * sizeof(unsigned);
+    BSF_TRY(grow(&c->h6_scales, &c->h6_scales_bytes, (size_t)B * 6 * HW * sizeof(double)));
+    BSF_TRY(grow(&c->h6_ext, &c->h6_ext_bytes, ext_bytes));
+    BSF_TRY(cudaMemsetAsync(c->h6_ext, 0, ext_bytes, st));
+    BSF_TRY(prof_mark(c, 0, st));
+    BSF_TRY(launch_map6(params, kind, (int)B, (int)H, (int)W, fine, o.eps, o.eta, ascale, (double*)c->h6_scales,
+                        (unsigned*)c->h6_ext, c->d_status, st));
+    std::vector<unsigned> ext((size_t)B * nfine * 2);
+    BSF_TRY(cudaMemcpyAsync(ext.data(), c->h6_ext, ext_bytes, cudaMemcpyDeviceToHost, st));
+    BSF_TRY(cudaStreamSynchronize(st));
+    auto ext_of = [&](int64_t b, int bx, int by, float* ex, float* ey) {
+        const size_t t = (size_t)(b * nfine + (int64_t)by * fx + bx) * 2;
+        memcpy(ex, &ext[t], sizeof(float));
+        memcpy(ey, &ext[t + 1], sizeof(float));
+    };
+    // tile records: all 64-tiles first, then all 16-tiles (one launch shape per class)
+    std::vector<hex6_tile> big, small;
+    const int cx = (int)((W + coarse - 1) / coarse), cy = (int)((H + coarse - 1) / coarse);
+    for (int64_t b = 0; b < B; ++b)
+        for (int ty = 0; ty < cy; ++ty)
+            for (int tx = 0; tx < cx; ++tx) {
+                float ex = 0.f, ey = 0.f;
+                for (int by = ty * ratio; by < std::min(fy, (ty + 1) * ratio); ++by)
+                    for (int bx = tx * ratio; bx < std::min(fx, (tx + 1) * ratio); ++bx) {
+                        float a, e;
+                        ext_of(b, bx, by, &a, &e);
+                        ex = std::max(ex, a);
+                        ey = std::max(ey, e);
+                    }
+                if (!(ex >= 0.f && ey >= 0.f && ex < 1e5f && ey < 1e5f)) return BSF_EINVAL;
+                if (std::max(ex, ey) >= split_below) {
+                    hex6_tile t;
+                    hex6_window(tx, ty, coarse, (int)H, (int)W, ex, ey, h, &t);
+                    t.b = (int)b;
+                    big.push_back(t);
+                    continue;
+                }
+                for (int by = ty * ratio; by < std::min(fy, (ty + 1) * ratio); ++by)
+                    for (int bx = tx * ratio; bx < std::min(fx, (tx + 1) * ratio); ++bx) {
+                        float a, e;
+                        ext_of(b, bx, by, &a, &e);
+                        hex6_tile t;
+                        hex6_window(bx, by, fine, (int)H, (int)W, a, e, h, &t);
+                        t.b = (int)b;
+                        small.push_back(t);
+                    }
+            }
+    std::vector<hex6_tile> tl(big);
+    tl.insert(tl.end(), small.begin(), small.end());
+    // chunks of one tile size, at most 8 GiB of windows and 65535 tiles (a grid dimension)
+    const size_t budget = (size_t)8 << 30;
+    struct chunk {
+        size_t first, last;
+        int cols;
+        size_t bytes;
+    };
+    std::vector<chunk> chunks;
+    for (size_t t = 0; t < tl.size(); ++t) {
+        if (tl[t].ncol > hex6_max_cols()) return BSF_EINVAL;  // footprint too wide for one window
+        const size_t bytes = (size_t)C * tl[t].ncol * tl[t].nrow * sizeof(double);
+        if (bytes > budget) return BSF_EINVAL;
+        if (chunks.empty() || tl[t].size != tl[chunks.back().first].size || chunks.back().bytes + bytes > budget ||
+            t - chunks.back().first >= 65535)
+            chunks.push_back({t, t, 0, 0});
+        chunk& ch = chunks.back();
+        tl[t].off = (long long)(ch.bytes / sizeof(double));
+        ch.bytes += bytes;
+        ch.last = t + 1;
+        ch.cols = std::max(ch.cols, tl[t].ncol);
+    }
+    size_t win = 0;
+    for (auto& ch : chunks) win = std::max(win, ch.bytes);
+    if (tl.empty()) return BSF_OK;
+    BSF_TRY(grow(&c->h6_tiles, &c->h6_tiles_bytes, tl.size() * sizeof(hex6_tile)));
+    BSF_TRY(grow(&c->h6_win, &c->h6_win_bytes, win));
+    BSF_TRY(cudaMemcpyAsync(c->h6_tiles, tl.data(), tl.size() * sizeof(hex6_tile), cudaMemcpyHostToDevice, st));
+    const hex6_tile* dt = (const hex6_tile*)c->h6_tiles;
+    for (size_t i = 0; i < chunks.size(); ++i) {
+        const chunk& ch = chunks[i];
+        const int n = (int)(ch.last - ch.first);
+        BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
+                                   (double*)c->h6_win, st));
+        BSF_TRY(prof_mark(c, 1, st));
+        BSF_TRY(launch_hex6_stencil((const double*)c->h6_scales, (int)C, (int)H, (int)W, tl[ch.first].size, h,
+                                    dt + ch.first, n, (const double*)c->h6_win, out, c->d_status, st));
+        BSF_TRY(prof_mark(c, 2, st));
+        if (i + 1 < chunks.size()) BSF_TRY(prof_mark(c, 0, st));
+    }
+    return BSF_OK;
+}
+
 // argument checks shared by bsf_filter and bsf_filter_host
 static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
                               int N, const float* params, int kind, const bsf_opts* opts, const float* out,
@@ -383,21 +506,30 @@ static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t 
     if (B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
-    if (N != 4) return BSF_EUNSUPPORTED;
+    if (N != 4 && N != 6) return BSF_EUNSUPPORTED;
     bsf_default_opts(o);
     if (opts) *o = *opts;
     if (o->precision != BSF_PREC_EXACT && o->precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (o->iterations < 1 || o->iterations > 64) return BSF_EINVAL;
+    if (N == 6 && !(o->hex_spacing >= 0.125f && o->hex_spacing <= 1.f)) return BSF_EINVAL;
     return BSF_OK;
 }
 
 // the filter on device buffers, enqueued on st (the caller holds the context lock)
+static bsf_status any_pass(bsf_ctx* c, int N, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
+                           int64_t W, const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
+                           float ascale = 1.f) {
+    if (N == 6) return filter6(c, image, dtype, B, C, H, W, params, kind, o, out, st, ascale);
+    return filter_pass(c, image, dtype, B, C, H, W, params, kind, o, out, st, ascale);
+}
+
 static bsf_status filter_locked(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
-                                const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st) {
+                                const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
+                                int N = 4) {
     const int64_t HW = H * W;
     bsf_status s;
     if (o.iterations == 1) {
-        s = filter_pass(c, image, dtype, B, C, H, W, params, kind, o, out, st);
+        s = any_pass(c, N, image, dtype, B, C, H, W, params, kind, o, out, st);
     } else {
         // iterated box spline (Sec. 3.3): m passes, each with the widths a / sqrt(m)
         // of the optimal scale vector a (the mapped widths are scaled, so the
@@ -412,11 +544,11 @@ static bsf_status filter_locked(bsf_ctx* c, const void* image, int dtype, int64_
         // the halo of the unscaled field covers the scaled one; passes alternate
         // between tmp and out so that the last one lands in out
         float* dst = (m % 2 == 0) ? tmp : out;
-        s = filter_pass(c, image, dtype, B, C, H, W, params, kind, oi, dst, st, asc);
+        s = any_pass(c, N, image, dtype, B, C, H, W, params, kind, oi, dst, st, asc);
         for (int it = 1; it < m && s == BSF_OK; ++it) {
             float* src = dst;
             dst = (src == tmp) ? out : tmp;
-            s = filter_pass(c, src, BSF_F32, B, C, H, W, params, kind, oi, dst, st, asc);
+            s = any_pass(c, N, src, BSF_F32, B, C, H, W, params, kind, oi, dst, st, asc);
         }
     }
     if (s != BSF_OK) return s;
@@ -436,7 +568,7 @@ bsf_status bsf_filter(bsf_ctx* c, const void* image, int dtype, int64_t B, int64
     if (a != BSF_OK) return a;
     std::lock_guard<std::mutex> lock(c->mu);
     BSF_TRY(cudaSetDevice(c->device));
-    return filter_locked(c, image, dtype, B, C, H, W, params, kind, o, out, (cudaStream_t)stream);
+    return filter_locked(c, image, dtype, B, C, H, W, params, kind, o, out, (cudaStream_t)stream, N);
 }
 
 // Slot buffers grow only while no enqueued work of the pipeline is in flight.
@@ -467,7 +599,7 @@ bsf_status bsf_filter_host(bsf_ctx* c, const void* image_host, int dtype, int64_
         }
     }
     auto& h = c->hs[c->host_calls & 1];
-    const int K = (kind == BSF_PARAM_SCALES) ? 4 : 3;
+    const int K = (kind == BSF_PARAM_SCALES) ? N : 3;
     const size_t ib = (size_t)(B * C * H * W) * (dtype == BSF_U8 ? 1 : 4);
     const size_t pb = (size_t)(B * K * H * W) * sizeof(float);
     const size_t ob = (size_t)(B * C * H * W) * sizeof(float);
@@ -483,7 +615,7 @@ bsf_status bsf_filter_host(bsf_ctx* c, const void* image_host, int dtype, int64_
     BSF_TRY(cudaStreamWaitEvent(c->s_comp, h.in_ready, 0));
     BSF_TRY(cudaStreamWaitEvent(c->s_comp, h.out_done, 0));
     const bsf_status s = filter_locked(c, h.img, dtype, B, C, H, W, (const float*)h.prm, kind, o, (float*)h.out,
-                                       c->s_comp);
+                                       c->s_comp, N);
     if (s != BSF_OK) return s;
     BSF_TRY(cudaEventRecord(h.comp_done, c->s_comp));
     BSF_TRY(cudaStreamWaitEvent(c->s_d2h, h.comp_done, 0));

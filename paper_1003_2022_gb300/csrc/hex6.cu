@@ -1,0 +1,774 @@
+// Six-directional filter (N = 6: theta_k = k pi / 6, Sec. 2.2.1) on the
+// hexagonal lattice Lambda_h = { h (i + j/2, j sqrt3/2) }.
+//
+// Algorithm 1 (Sec. 3.1) needs every direction b_k u_k to be a lattice vector;
+// on the pixel lattice that holds for N = 2 and 4 only, and for more
+// directions the paper notes that the running sums would need an interpolated
+// image (Sec. 3.3).  Here the image is transferred once, mass-preservingly, to
+// Lambda_h, where all six directions are lattice vectors (1,0), (1,1), (0,1),
+// (-1,2), (-1,1), (-2,1) in lattice coordinates (i, j), with b_k = h |v_k| =
+// h (1, sqrt3, 1, sqrt3, 1, sqrt3).  Each pixel's mass goes to the vertices of
+// the lattice triangle that holds it, in proportion to its barycentric
+// coordinates; gathered per lattice point m, the weight of pixel k is the
+// piecewise-linear hat of m at k.  On Lambda_h the algorithm is exact:
+//   step 2: six running sums along the lattice vectors (Eq. 2DRS);
+//   step 3: Eq. keyeqn, 64 taps of Eq. FD_mesh, F(y) = sum_m g[m] beta^6_b(y - m)
+//           with the element's exact polynomial pieces (hex6_tables.h, 24
+//           lattice points per tap).
+// Sixth-order running sums of a whole image outgrow FP64 (they grow like L^6
+// and the 64-tap difference cancels them), so each tile of 64 x 64 output
+// pixels gets its own window of the lattice, sized from the tile's largest
+// footprint.  The window is a parallelogram with sides along 0 and 150
+// degrees, stored row by row (row r = j - j0, column c = i - i_left + 2r): in
+// those coordinates every lattice direction has non-negative components, so
+// each running sum enters the window through its bottom or left side, where
+// the sums over the whole plane are zero, and the window's sums equal the
+// whole-plane ones.  The scale map for six directions (Sec. 3.2.2 with the
+// kurtosis norm written for N directions) is solved per pixel in FP64 by a
+// primal active-set Newton method.
+#include <math.h>
+
+#include <algorithm>
+
+#include "bsf_common.cuh"
+#include "bsf_internal.h"
+#include "hex6_tables.h"
+
+namespace {
+
+#define BSF_QNAN64 (0.0 / 0.0)
+
+// cos / sin of 2 theta_k and of 4 theta_k, theta_k = k pi / 6; (-1)^k
+__host__ __device__ __forceinline__ double c2k(int k) {
+    const double t[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+    return t[k];
+}
+__host__ __device__ __forceinline__ double s2k(int k) {
+    const double r = 0.86602540378443864676;
+    const double t[6] = {0.0, r, r, 0.0, -r, -r};
+    return t[k];
+}
+// null-space basis of the covariance constraint: rows z_k = (cos 4theta_k, sin 4theta_k, (-1)^k)
+__host__ __device__ __forceinline__ void zrow(int k, double z[3]) {
+    const double r = 0.86602540378443864676;
+    const double c4[6] = {1.0, -0.5, -0.5, 1.0, -0.5, -0.5};
+    const double s4[6] = {0.0, r, -r, 0.0, r, -r};
+    z[0] = c4[k];
+    z[1] = s4[k];
+    z[2] = (k & 1) ? -1.0 : 1.0;
+}
+
+// ||K||^2 for six directions: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m)
+// = (S0^2 + |S1|^2) / 2, S0 = sum q_k, S1 = sum q_k exp(2 i theta_k), q = p^2
+__host__ __device__ double kurt6(const double p[6]) {
+    double s0 = 0.0, sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double q = p[k] * p[k];
+        s0 += q;
+        sr += q * c2k(k);
+        si += q * s2k(k);
+    }
+    return 0.5 * (s0 * s0 + sr * sr + si * si);
+}
+
+__host__ __device__ __forceinline__ void p_of_t(const double pbar[6], const double t[3], double p[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double z[3];
+        zrow(k, z);
+        p[k] = pbar[k] + z[0] * t[0] + z[1] * t[1] + z[2] * t[2];
+    }
+}
+
+// solve the symmetric positive definite d x d system A x = b (d <= 3) by Cholesky
+__host__ __device__ __forceinline__ bool spd_solve(int d, double A[3][3], const double b[3], double x[3]) {
+    double L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < d; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    double y[3];
+    for (int i = 0; i < d; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s / L[i][i];
+    }
+    for (int i = d - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < d; ++k) s -= L[k][i] * x[k];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+// minimise ||K||^2 over p = pbar + Z t with p >= lb: primal active set, the
+// start is a strictly feasible point built from the hexagon geometry of the
+// covariance (the traceless part, normalised, is a convex combination of the
+// centre and two neighbouring vertices exp(2 i theta_k)).  Returns false when
+// no p >= lb reproduces the covariance.
+struct map6_p {
+    double p[6];
+    bool ok;
+};
+
+// (returns its result by value: the scales must not travel through a pointer
+// to the caller's local array, which the device build of this function did
+// not write back reliably)
+__host__ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
+    map6_p res;
+    res.ok = true;
+    double* p = res.p;
+    const double PI3 = 1.04719755119659774615;
+    double pbar[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * c2k(k) + Zs * s2k(k))) / 6.0;
+    const double den = T - 6.0 * lb;
+    if (!(den > 0.0)) {
+        res.ok = false;
+        return res;
+    }
+    const double zr = Zc / den, zi = Zs / den;
+    double ang = atan2(zi, zr);
+    if (ang < 0.0) ang += 6.28318530717958647693;
+    int ka = (int)(ang / PI3);
+    ka = ka < 0 ? 0 : (ka > 5 ? 5 : ka);
+    const int kb = (ka + 1) % 6;
+    const double dt = c2k(ka) * s2k(kb) - s2k(ka) * c2k(kb);
+    const double la = (zr * s2k(kb) - zi * c2k(kb)) / dt;
+    const double lbb = (c2k(ka) * zi - s2k(ka) * zr) / dt;
+    double l0 = 1.0 - la - lbb;
+    if (l0 < -1e-12) {
+        res.ok = false;
+        return res;
+    }
+    l0 = fmax(l0, 0.0);
+    double ps[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ps[k] = lb + den * (l0 / 6.0 + (k == ka ? la : 0.0) + (k == kb ? lbb : 0.0));
+    double t[3] = {0.0, 0.0, 0.0};
+    const double nrm[3] = {3.0, 3.0, 6.0};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double z[3];
+        zrow(k, z);
+        for (int l = 0; l < 3; ++l) t[l] += z[l] * (ps[k] - pbar[k]) / nrm[l];
+    }
+    const double tiny = 1e-13 * T;
+    int W[3], nw = 0;
+    for (int k = 0; k < 6; ++k)
+        if (ps[k] <= lb + tiny) {
+            if (nw == 3) {  // the covariance is at a vertex of the feasible set: the only point
+                for (int j = 0; j < 6; ++j) p[j] = fmax(ps[j], lb);
+                return res;
+            }
+            W[nw++] = k;
+        }
+    for (int it = 0; it < 80; ++it) {
+        p_of_t(pbar, t, p);
+        // gradient and Hessian in t
+        double s0 = 0.0, sr = 0.0, si = 0.0;
+        for (int k = 0; k < 6; ++k) {
+            const double q = p[k] * p[k];
+            s0 += q;
+            sr += q * c2k(k);
+            si += q * s2k(k);
+        }
+        const double h0 = 0.5 * (s0 * s0 + sr * sr + si * si);
+        double g[3] = {0, 0, 0}, Hm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        double sg[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+        for (int k = 0; k < 6; ++k) {
+            double z[3];
+            zrow(k, z);
+            const double dq = 0.5 * (s0 + c2k(k) * sr + s2k(k) * si);
+            const double gp = 4.0 * p[k] * dq;
+            for (int l = 0; l < 3; ++l) {
+                g[l] += z[l] * gp;
+                const double y = p[k] * z[l];
+                sg[l] += y;
+                mr[l] += c2k(k) * y;
+                mi[l] += s2k(k) * y;
+                for (int m = 0; m <= l; ++m) Hm[l][m] += 4.0 * dq * z[l] * z[m];
+            }
+        }
+        for (int l = 0; l < 3; ++l)
+            for (int m = 0; m <= l; ++m) {
+                Hm[l][m] += 4.0 * (sg[l] * sg[m] + mr[l] * mr[m] + mi[l] * mi[m]);
+                Hm[m][l] = Hm[l][m];
+            }
+        // null space of the working set
+        double N[3][3];
+        int d = 3 - nw;
+        if (nw == 0) {
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) N[a][b] = (a == b) ? 1.0 : 0.0;
+        } else if (nw == 1) {
+            double z[3];
+            zrow(W[0], z);
+            const double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+            double n1[3] = {z[0] / zn, z[1] / zn, z[2] / zn};
+            int e = 0;
+            if (fabs(n1[1]) < fabs(n1[e])) e = 1;
+            if (fabs(n1[2]) < fabs(n1[e])) e = 2;
+            double u[3] = {0, 0, 0};
+            u[e] = 1.0;
+            const double dd = n1[e];
+            for (int a = 0; a < 3; ++a) u[a] -= dd * n1[a];
+            const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            for (int a = 0; a < 3; ++a) u[a] /= un;
+            const double v[3] = {n1[1] * u[2] - n1[2] * u[1], n1[2] * u[0] - n1[0] * u[2], n1[0] * u[1] - n1[1] * u[0]};
+            for (int a = 0; a < 3; ++a) {
+                N[a][0] = u[a];
+                N[a][1] = v[a];
+            }
+        } else if (nw == 2) {
+            double za[3], zb[3];
+            zrow(W[0], za);
+            zrow(W[1], zb);
+            double n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2], za[0] * zb[1] - za[1] * zb[0]};
+            const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (int a = 0; a < 3; ++a) N[a][0] = n[a] / nn;
+        }
+        double step[3] = {0, 0, 0}, dec = 0.0;
+        if (d > 0) {
+            double Hr[3][3], gr[3], u[3];
+            for (int a = 0; a < d; ++a) {
+                gr[a] = 0.0;
+                for (int l = 0; l < 3; ++l) gr[a] -= N[l][a] * g[l];
+                for (int b = 0; b < d; ++b) {
+                    double s = 0.0;
+                    for (int l = 0; l < 3; ++l)
+                        for (int m = 0; m < 3; ++m) s += N[l][a] * Hm[l][m] * N[m][b];
+                    Hr[a][b] = s;
+                }
+            }
+            if (!spd_solve(d, Hr, gr, u)) break;
+            for (int l = 0; l < 3; ++l) {
+                step[l] = 0.0;
+                for (int a = 0; a < d; ++a) step[l] += N[l][a] * u[a];
+            }
+            dec = -(g[0] * step[0] + g[1] * step[1] + g[2] * step[2]);
+        }
+        const double smax = fmax(fabs(step[0]), fmax(fabs(step[1]), fabs(step[2])));
+        if (d == 0 || dec <= 1e-22 * h0 || smax <= 1e-14 * T) {
+            // converged on the face: bound multipliers from g = sum_{k in W} lambda_k z_k
+            if (nw == 0) return res;
+            double G[3][3], rhs[3], lam[3];
+            for (int a = 0; a < nw; ++a) {
+                double za[3];
+                zrow(W[a], za);
+                rhs[a] = za[0] * g[0] + za[1] * g[1] + za[2] * g[2];
+                for (int b = 0; b < nw; ++b) {
+                    double zb[3];
+                    zrow(W[b], zb);
+                    G[a][b] = za[0] * zb[0] + za[1] * zb[1] + za[2] * zb[2];
+                }
+            }
+            if (!spd_solve(nw, G, rhs, lam)) return res;
+            int worst = -1;
+            const double gs = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+            double lw = -1e-10 * (gs + 1e-300);
+            for (int a = 0; a < nw; ++a)
+                if (lam[a] < lw) {
+                    lw = lam[a];
+                    worst = a;
+                }
+            if (worst < 0) {
+                for (int a = 0; a < nw; ++a) p[W[a]] = lb;
+                return res;
+            }
+            for (int a = worst; a < nw - 1; ++a) W[a] = W[a + 1];
+            --nw;
+            continue;
+        }
+        // longest step along the Newton direction that keeps p >= lb
+        double amax = 1.0;
+        int blk = -1;
+        for (int k = 0; k < 6; ++k) {
+            bool inw = false;
+            for (int a = 0; a < nw; ++a) inw |= (W[a] == k);
+            if (inw) continue;
+            double z[3];
+            zrow(k, z);
+            const double dp = z[0] * step[0] + z[1] * step[1] + z[2] * step[2];
+            if (dp < 0.0) {
+                const double a = fmax(p[k] - lb, 0.0) / (-dp);
+                if (a < amax) {
+                    amax = a;
+                    blk = k;
+                }
+            }
+        }
+        double alpha = amax;
+        for (int bt = 0; bt < 40; ++bt) {
+            double tn[3] = {t[0] + alpha * step[0], t[1] + alpha * step[1], t[2] + alpha * step[2]}, pn[6];
+            p_of_t(pbar, tn, pn);
+            if (kurt6(pn) <= h0 - 0.25 * alpha * dec) break;
+            alpha *= 0.5;
+        }
+        for (int l = 0; l < 3; ++l) t[l] += alpha * step[l];
+        if (blk >= 0 && alpha == amax && nw < 3) W[nw++] = blk;
+    }
+    p_of_t(pbar, t, p);
+    for (int a = 0; a < nw; ++a) p[W[a]] = lb;
+    for (int k = 0; k < 6; ++k) p[k] = fmax(p[k], lb);
+    return res;
+}
+
+struct map6_result {
+    double a[6];
+    int flag;
+};
+
+// the bound p_k >= 1e-3 T keeps the smallest width at least 0.077 times the
+// typical one: the 64-tap FP64 difference loses accuracy like the square of
+// that ratio for each width at the bound
+constexpr double MAP6_REL_BOUND = 1e-3;
+
+// covariance (kind COV) or (sigma, rho, theta) (kind SRT) -> six scales; the
+// flags and the elongation clamp follow the four-directional map
+__host__ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, double eps, double eta) {
+    map6_result R;
+    R.flag = 0;
+    const double v0 = v0f, v1 = v1f, v2 = v2f;
+    double lmax, lmin, c2, s2;
+    if (kind == BSF_PARAM_SRT) {
+        lmax = v0 * v0;
+        lmin = lmax / v1;
+        sincos(fmod(2.0 * v2, 6.283185307179586476925), &s2, &c2);
+        if (!(v2 == v2) || fabs(v2) > 1e30) c2 = s2 = BSF_QNAN64;
+    } else {
+        const double D = sqrt((v0 - v2) * (v0 - v2) + 4.0 * v1 * v1);
+        lmax = 0.5 * (v0 + v2 + D);
+        lmin = (v0 * v2 - v1 * v1) / lmax;
+        c2 = D > 0.0 ? (v0 - v2) / D : 1.0;
+        s2 = D > 0.0 ? 2.0 * v1 / D : 0.0;
+    }
+    if (!(isfinite(lmax) && isfinite(lmin) && isfinite(c2) && isfinite(s2)) || !(lmin > 0.0) || !(lmax >= lmin)) {
+        for (int k = 0; k < 6; ++k) R.a[k] = BSF_QNAN64;
+        R.flag = 4;
+        return R;
+    }
+    // elongation bound for six directions: the normalised traceless part lies in
+    // the regular hexagon with vertices exp(2 i theta_k), scaled by 1 - 6 delta so
+    // that every p_k can keep the share delta = 1e-3 of the trace
+    double psi = fmod(atan2(s2, c2), 1.04719755119659774615);
+    if (psi < 0.0) psi += 1.04719755119659774615;
+    const double r = (1.0 - 6.0 * MAP6_REL_BOUND) * 0.86602540378443864676 / cos(psi - 0.52359877559829887308);
+    bool clamp = false;
+    {
+        const double U = (1.0 + r) / (1.0 - r);
+        const double rc = (1.0 - eta) * U;
+        if (lmax / lmin > rc) {
+            const double s = lmax + lmin;
+            lmin = s / (1.0 + rc);
+            lmax = s - lmin;
+            clamp = true;
+            R.flag |= 1;
+        }
+    }
+    double T, Zc, Zs;
+    if (kind == BSF_PARAM_COV && !clamp) {
+        T = 12.0 * (v0 + v2);
+        Zc = 12.0 * (v0 - v2);
+        Zs = 24.0 * v1;
+    } else {
+        const double m = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+        T = 24.0 * m;
+        Zc = 24.0 * d * c2;
+        Zs = 24.0 * d * s2;
+    }
+    // lower bound of p: eps, or the share MAP6_REL_BOUND of the trace T = sum p
+    const double bound = fmax(eps, MAP6_REL_BOUND * T);
+    map6_p P = map6_active_set(T, Zc, Zs, bound);
+    if (!P.ok) {
+        R.flag |= 2;
+        P = map6_active_set(T, Zc, Zs, 0.0);
+        if (!P.ok) {
+            for (int k = 0; k < 6; ++k) R.a[k] = BSF_QNAN64;
+            R.flag = 4;
+            return R;
+        }
+        for (int k = 0; k < 6; ++k) P.p[k] = fmax(P.p[k], bound);
+    }
+    for (int k = 0; k < 6; ++k) R.a[k] = sqrt(fmax(P.p[k], 0.0));
+    return R;
+}
+
+__device__ __forceinline__ double cos_k(int k) {
+    const double t[6] = {1.0, 0.86602540378443864676, 0.5, 0.0, -0.5, -0.86602540378443864676};
+    return t[k];
+}
+__device__ __forceinline__ double sin_k(int k) {
+    const double t[6] = {0.0, 0.5, 0.86602540378443864676, 1.0, 0.86602540378443864676, 0.5};
+    return t[k];
+}
+
+// per pixel: scales (FP64, six planes per batch entry) and the largest
+// footprint half-extents of each tile
+__global__ void k_map6(const float* __restrict__ params, int kind, long long HW, int B, int W, int tile, int tiles_x,
+                       int ntile, double eps, double eta, double ascale, double* __restrict__ scales,
+                       unsigned* __restrict__ tile_ext, unsigned* __restrict__ status) {
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gid >= HW * B) return;
+    const long long b = gid / HW, p = gid - b * HW;
+    const int x = (int)(p % W), y = (int)(p / W);
+    double a[6];
+    int flag = 0;
+    if (kind == BSF_PARAM_SCALES) {
+        for (int k = 0; k < 6; ++k) {
+            const double v = (double)params[(b * 6 + k) * HW + p] * ascale;
+            a[k] = v;
+            if (!(v > 0.0) || !isfinite(v)) flag = 4;
+        }
+        if (flag) raise_status(status, BSF_EBADSCALE);
+    } else {
+        const float* q = params + b * 3 * HW + p;
+        const map6_result R = map6_solve(kind, q[0], q[HW], q[2 * HW], eps, eta);
+        for (int k = 0; k < 6; ++k) a[k] = R.a[k] * ascale;
+        flag = R.flag;
+        if (flag & 1) raise_status(status, BSF_EINFEASIBLE);
+        if (flag & 4) raise_status(status, BSF_EBADSCALE);
+    }
+    for (int k = 0; k < 6; ++k) scales[(b * 6 + k) * HW + p] = flag & 4 ? BSF_QNAN64 : a[k];
+    if (flag & 4) return;
+    double ex = 0.0, ey = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        ex += a[k] * fabs(cos_k(k));
+        ey += a[k] * sin_k(k);
+    }
+    const float fx = (float)(0.5 * ex) * 1.0001f + 1e-3f, fy = (float)(0.5 * ey) * 1.0001f + 1e-3f;
+    unsigned* te = tile_ext + ((size_t)b * ntile + (size_t)(y / tile) * tiles_x + (x / tile)) * 2;
+    atomicMax(te, __float_as_uint(fx));
+    atomicMax(te + 1, __float_as_uint(fy));
+}
+
+// the scales of bsf_scales_from_cov for N = 6 (float32, six planes, flags)
+__global__ void k_map6_out(const float* __restrict__ params, int kind, long long npix, double eps, double eta,
+                           float* __restrict__ scales, uint8_t* __restrict__ flags) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const map6_result R = map6_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta);
+    for (int k = 0; k < 6; ++k) scales[k * npix + p] = (float)R.a[k];
+    if (flags) flags[p] = (uint8_t)R.flag;
+}
+
+constexpr int PRE_THREADS = 1024;
+constexpr int PRE_CPT = 4;  // window columns per thread: at most 4096
+
+// step 2 on one window: transfer of the image and the six running sums, row by
+// row; the state of each sum (its last row, two for the 90-degree sum) stays
+// in shared memory
+template <class InT>
+__global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restrict__ img, int C, int H, int W,
+                                                             double h, const hex6_tile* __restrict__ tiles,
+                                                             double* __restrict__ scratch) {
+    extern __shared__ double sm6[];
+    const hex6_tile tl = tiles[blockIdx.x];
+    const int c = blockIdx.y;
+    const int ncol = tl.ncol, nrow = tl.nrow;
+    double* s30 = sm6;
+    double* s60 = s30 + ncol;
+    double* s90a = s60 + ncol;
+    double* s90b = s90a + ncol;
+    double* s120 = s90b + ncol;
+    double* s150 = s120 + ncol;
+    double* wt = s150 + ncol;  // 32 warp totals
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k < 6 * ncol; k += PRE_THREADS) sm6[k] = 0.0;
+    const InT* f = img + ((size_t)tl.b * C + c) * (size_t)H * W;
+    double* G = scratch + tl.off + (long long)c * ncol * nrow;
+    const double rs3 = 0.57735026918962576451;  // 1/sqrt3
+    const double hy = h * 0.86602540378443864676;
+    const int c0 = tid * PRE_CPT;
+    __syncthreads();
+    for (int r = 0; r < nrow; ++r) {
+        const int j = tl.j0w + r;
+        double x[PRE_CPT];
+        double run = 0.0;
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            double mu = 0.0;
+            if (cc < ncol) {
+                const int i = cc + tl.i_left - 2 * r;
+                const double px = h * ((double)i + 0.5 * (double)j), py = hy * (double)j;
+                const int kx0 = (int)floor(px), ky0 = (int)floor(py);
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const int ky = ky0 + dy;
+                    if (ky < 0 || ky >= H) continue;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int kx = kx0 + dx;
+                        if (kx < 0 || kx >= W) continue;
+                        // lattice coordinates of pixel - lattice point
+                        const double ddx = ((double)kx - px) / h, ddy = ((double)ky - py) / h;
+                        const double dt = 2.0 * rs3 * ddy, ds = ddx - rs3 * ddy;
+                        const double w = 1.0 - fmax(fabs(ds), fmax(fabs(dt), fabs(ds + dt)));
+                        if (w > 0.0) mu += w * (double)f[(size_t)ky * W + kx];
+                    }
+                }
+            }
+            run += mu;
+            x[e] = run;
+        }
+        // block-wide scan of the thread totals (the 0-degree sum along the row)
+        double v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wt[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            double u = lane < PRE_THREADS / 32 ? wt[lane] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double z = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += z;
+            }
+            if (lane < PRE_THREADS / 32) wt[lane] = u;
+        }
+        __syncthreads();
+        const double off = (v - run) + (warp > 0 ? wt[warp - 1] : 0.0);
+        // the other five sums read their previous rows, then the states advance;
+        // the 90-degree (two rows back) and 150-degree states of a column are
+        // read by its own thread only, the others also by the next columns' threads
+        double n30[PRE_CPT], n60[PRE_CPT], n120[PRE_CPT], o90[PRE_CPT];
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            if (cc >= ncol) continue;
+            double y = x[e] + off;
+            y += cc >= 3 ? s30[cc - 3] : 0.0;
+            n30[e] = y;
+            y += cc >= 2 ? s60[cc - 2] : 0.0;
+            n60[e] = y;
+            y += cc >= 3 ? s90b[cc - 3] : 0.0;
+            o90[e] = s90a[cc];
+            s90a[cc] = y;
+            y += cc >= 1 ? s120[cc - 1] : 0.0;
+            n120[e] = y;
+            y += s150[cc];
+            s150[cc] = y;
+            G[(long long)r * ncol + cc] = y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            if (cc >= ncol) continue;
+            s30[cc] = n30[e];
+            s60[cc] = n60[e];
+            s90b[cc] = o90[e];
+            s120[cc] = n120[e];
+        }
+    }
+}
+
+constexpr int ST_THREADS = 128;  // 32 x 4 pixels for 64-pixel tiles, 16 x 8 for 16-pixel tiles
+
+// step 3: the 64 taps of Eq. FD_mesh, each read from its window by the exact
+// piecewise-quartic element (24 lattice points), in FP64
+__global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
+                                                              double h, const hex6_tile* __restrict__ tiles,
+                                                              const double* __restrict__ scratch,
+                                                              float* __restrict__ out, unsigned* __restrict__ status) {
+    __shared__ double coef[HEX6_NREGION][HEX6_NSLOT][HEX6_NMONO];
+    __shared__ int soff[HEX6_NREGION][HEX6_NSLOT][2];
+    __shared__ int lut[16];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
+    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT * HEX6_NMONO; k += ST_THREADS)
+        (&coef[0][0][0])[k] = (&HEX6_COEF[0][0][0])[k];
+    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT; k += ST_THREADS) {
+        soff[k / HEX6_NSLOT][k % HEX6_NSLOT][0] = HEX6_DI[k / HEX6_NSLOT][k % HEX6_NSLOT];
+        soff[k / HEX6_NSLOT][k % HEX6_NSLOT][1] = HEX6_DJ[k / HEX6_NSLOT][k % HEX6_NSLOT];
+    }
+    __syncthreads();
+    const hex6_tile tl = tiles[blockIdx.y];
+    const int c = blockIdx.z;
+    const int tile = tl.size;
+    const int per_row = tile / (int)blockDim.x;
+    const int bx = blockIdx.x % per_row, by = blockIdx.x / per_row;
+    const int x = tl.tx * tile + bx * (int)blockDim.x + threadIdx.x;
+    const int y = tl.ty * tile + by * (int)blockDim.y + threadIdx.y;
+    if (x >= W || y >= H || x >= (tl.tx + 1) * tile || y >= (tl.ty + 1) * tile) return;
+    const long long HW = (long long)H * W, p = (long long)y * W + x;
+    float* o = out + ((size_t)tl.b * C + c) * HW + p;
+    double a[6], prod = 1.0;
+    bool bad = false;
+    for (int k = 0; k < 6; ++k) {
+        a[k] = scales[((size_t)tl.b * 6 + k) * HW + p];
+        bad |= !(a[k] > 0.0);
+        prod *= a[k];
+    }
+    if (bad) {
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    const double* G = scratch + tl.off + (long long)c * tl.ncol * tl.nrow;
+    const double SQ3 = 1.73205080756887729353;
+    // tau = (1/2) sum (a_k - b_k) u_k, b = h (1, sqrt3, 1, sqrt3, 1, sqrt3); taps at
+    // n + tau - sum_k q_k a_k u_k, each computed from the pixel (no running sum of
+    // positions, so no rounding accumulates along the 64 taps)
+    double tx0 = 0.0, ty0 = 0.0, ax[6], ay[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double bk = (k & 1) ? h * SQ3 : h;
+        tx0 += 0.5 * (a[k] - bk) * cos_k(k);
+        ty0 += 0.5 * (a[k] - bk) * sin_k(k);
+        ax[k] = a[k] * cos_k(k);
+        ay[k] = a[k] * sin_k(k);
+    }
+    const double it2 = 2.0 / (h * SQ3), ih = 1.0 / h;
+    const int ncol = tl.ncol;
+    double acc = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < 64; ++q) {
+        double dx = tx0, dy = ty0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if ((q >> k) & 1) {
+                dx -= ax[k];
+                dy -= ay[k];
+            }
+        const double yx = (double)x + dx, yy = (double)y + dy;
+        // lattice coordinates of the tap
+        const double t = yy * it2;
+        const double s = yx * ih - 0.5 * t;
+        const double fi = floor(s), fj = floor(t);
+        const double sg = s - fi, tg = t - fj;
+        int code;
+        if (sg + tg < 1.0)
+            code = (sg > tg) | ((2.0 * sg + tg > 1.0) << 1) | ((sg + 2.0 * tg > 1.0) << 2);
+        else
+            code = 8 | (sg > tg) | ((2.0 * sg + tg > 2.0) << 1) | ((sg + 2.0 * tg > 2.0) << 2);
+        const int reg = lut[code];
+        const int rr = (int)fj - tl.j0w;
+        const int cc = (int)fi - tl.i_left + 2 * rr;
+        if (rr < 2 || rr + 3 >= tl.nrow || cc < 6 || cc + 9 >= ncol) {
+            raise_status(status, BSF_EHALO);
+            *o = __int_as_float(0x7fc00000);
+            return;
+        }
+        double m[HEX6_NMONO];
+        const double s2 = sg * sg, t2 = tg * tg, st = sg * tg;
+        m[0] = 1.0;
+        m[1] = sg;
+        m[2] = tg;
+        m[3] = s2;
+        m[4] = st;
+        m[5] = t2;
+        m[6] = s2 * sg;
+        m[7] = s2 * tg;
+        m[8] = sg * t2;
+        m[9] = t2 * tg;
+        m[10] = s2 * s2;
+        m[11] = s2 * st;
+        m[12] = s2 * t2;
+        m[13] = st * t2;
+        m[14] = t2 * t2;
+        const double* base = G + (long long)rr * ncol + cc;
+        double F = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < HEX6_NSLOT; ++k) {
+            const double* cf = coef[reg][k];
+            double w = 0.0;
+#pragma unroll
+            for (int l = 0; l < HEX6_NMONO; ++l) w = fma(cf[l], m[l], w);
+            const int di = soff[reg][k][0], dj = soff[reg][k][1];
+            F = fma(__ldg(base - (long long)dj * (ncol + 2) - di), w, F);
+        }
+        acc += (__popc(q) & 1) ? -F : F;
+    }
+    // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.)
+    const double h2 = h * h;
+    *o = (float)(acc * 6.0 * h2 * h2 / prod);
+}
+
+}  // namespace
+
+// geometry of the window of one tile: every lattice point that the taps of
+// its pixels read (host side; ex, ey = the tile's largest footprint half-extents)
+void hex6_window(int tx, int ty, int tile, int H, int W, double ex, double ey, double h, hex6_tile* t) {
+    const double SQ3 = 1.7320508075688772935;
+    const int x0 = tx * tile, x1 = std::min(W, (tx + 1) * tile) - 1;
+    const int y0 = ty * tile, y1 = std::min(H, (ty + 1) * tile) - 1;
+    // taps: n + tau - x_q, in n + [-ex, ex] x [-ey, ey] - (h/2, 3 sqrt3 h / 2)
+    const double xl = x0 - ex - 0.5 * h, xh = x1 + ex - 0.5 * h;
+    const double yl = y0 - ey - 1.5 * SQ3 * h, yh = y1 + ey - 1.5 * SQ3 * h;
+    const double tl = 2.0 * yl / (h * SQ3), th = 2.0 * yh / (h * SQ3);
+    const int j0 = (int)floor(tl) - 4, j1 = (int)floor(th) + 5;
+    t->j0w = j0;
+    t->nrow = j1 - j0 + 1;
+    // row j is read by taps with t in [j - 3, j + 3); their cells' columns i0 run
+    // over floor(x/h - t/2) and the slots reach i0 - 2 .. i0 + 3
+    long long ileft = (1LL << 40), ncol = 0;
+    for (int r = 0; r < t->nrow; ++r) {
+        const int j = j0 + r;
+        const long long imin = (long long)floor(xl / h - 0.5 * (j + 3)) - 4;
+        ileft = std::min(ileft, imin + 2LL * r);
+    }
+    for (int r = 0; r < t->nrow; ++r) {
+        const int j = j0 + r;
+        const long long imax = (long long)floor(xh / h - 0.5 * (j - 3)) + 5;
+        ncol = std::max(ncol, imax - (ileft - 2LL * r) + 1);
+    }
+    t->i_left = (int)ileft;
+    t->ncol = (int)ncol;
+    t->tx = tx;
+    t->ty = ty;
+    t->size = tile;
+}
+
+int hex6_max_cols() { return PRE_THREADS * PRE_CPT; }
+
+cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
+                        double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st) {
+    const long long HW = (long long)H * W, n = HW * B;
+    const int tiles_x = (W + tile - 1) / tile, tiles_y = (H + tile - 1) / tile;
+    k_map6<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(params, kind, HW, B, W, tile, tiles_x, tiles_x * tiles_y, eps,
+                                                        eta, ascale, scales, tile_ext, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, float* scales,
+                            uint8_t* flags, cudaStream_t st) {
+    if (npix == 0) return cudaSuccess;
+    k_map6_out<<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(params, kind, npix, eps, eta, scales, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
+                               int ntiles, int ncol_max, double* scratch, cudaStream_t st) {
+    const size_t smem = (6 * (size_t)ncol_max + 32) * sizeof(double);
+    dim3 grid(ntiles, C);
+    if (dtype_u8) {
+        cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, scratch);
+    } else {
+        cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, scratch);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile, double h, const hex6_tile* tiles,
+                                int ntiles, const double* scratch, float* out, unsigned* status, cudaStream_t st) {
+    if (tile != 16 && tile != 64) return cudaErrorInvalidValue;
+    const dim3 blk = tile == 64 ? dim3(32, 4) : dim3(16, 8);
+    dim3 grid((tile / blk.x) * (tile / blk.y), ntiles, C);
+    k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, scratch, out, status);
+    return cudaGetLastError();
+}

@@ -1,0 +1,222 @@
+"""Parity of the six-directional CUDA path (N = 6 on the hexagonal lattice)
+with the FP64 oracle, through the C ABI.
+
+The oracle is the plain definition applied to the image transferred to the
+hexagonal lattice (oracle.n6.direct6_hex), with the scales of the oracle's
+KKT map (oracle.n6.map6) for covariance inputs.  Tolerance: 1e-5 normwise
+(max |gpu - ref| / max |ref|) over the sampled pixels, the bar of the workload
+statement; the map's float32 scales within 2e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from oracle import n6  # noqa: E402
+from paper_1003_2022_gb300 import _lib as L  # noqa: E402
+from paper_1003_2022_gb300 import api, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+DEV = "cuda:0"
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device(DEV)
+
+
+def _nerr(got, ref):
+    return float(np.abs(np.asarray(got, np.float64) - ref).max() / np.abs(ref).max())
+
+
+def _sample(H, W, n, seed, tile=16):
+    """Corners, pixels on both sides of tile borders, and random pixels."""
+    rng = np.random.default_rng(seed)
+    pts = {(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (H // 2, W // 2)}
+    for t in range(tile, max(H, W), tile):
+        for d in (-1, 0):
+            if t + d < H:
+                pts.add((t + d, int(rng.integers(0, W))))
+            if t + d < W:
+                pts.add((int(rng.integers(0, H)), t + d))
+    while len(pts) < n:
+        pts.add((int(rng.integers(0, H)), int(rng.integers(0, W))))
+    return np.array(sorted(y * W + x for y, x in pts))
+
+
+def _run(f, prm, kind, **kw):
+    dev = _cuda()
+    out = api.filter(torch.from_numpy(f).to(dev), torch.from_numpy(prm).to(dev), kind=kind, N=6, **kw)
+    st = api.device_status(dev)
+    return out.cpu().numpy().astype(np.float64), st
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_scales_kind_batch(dtype):
+    """Batch of 2 x 2 channels, 150 x 133 (ragged 64 x 64 tiles), scale planes in [0.8, 4] px."""
+    B, C, H, W = 2, 2, 150, 133
+    f = np.stack([np.stack([synth.image(H, W, seed=10 * b + c, dtype=dtype) for c in range(C)]) for b in range(B)])
+    a = np.stack([synth.scale_field(H, W, seed=20 + b, lo=0.8, hi=4.0) for b in range(B)])
+    a6 = np.concatenate([a, a[:, :2] * 0.9], axis=1).astype(np.float32)  # six planes
+    got, st = _run(f, a6, "scales")
+    assert st == 0
+    idx = _sample(H, W, 28, seed=1)
+    for b in range(B):
+        for c in range(C):
+            ref = n6.direct6_hex(f[b, c].astype(np.float64), a6[b].astype(np.float64), idx, 0.5)
+            assert _nerr(got[b, c].ravel()[idx], ref) < TOL
+
+
+@pytest.mark.parametrize("kind", ["srt", "cov"])
+def test_covariance_kinds(kind):
+    """Per-pixel (sigma, rho, theta) or covariance fields through the six-directional map."""
+    H, W = 97, 141
+    f = synth.image(H, W, seed=3, dtype="f32")
+    p = synth.srt_field(H, W, seed=4, sigma=(1.0, 5.0), rho=(1.0, 6.0))
+    if kind == "cov":
+        s, r, t = p.astype(np.float64)
+        l1, l2 = s * s, s * s / r
+        c, sn = np.cos(t), np.sin(t)
+        p = np.stack([l1 * c * c + l2 * sn * sn, (l1 - l2) * c * sn, l1 * sn * sn + l2 * c * c]).astype(np.float32)
+    got, st = _run(f, p, kind)
+    assert st == 0
+    idx = _sample(H, W, 22, seed=2)
+    a, fl = n6.map6(p.reshape(3, -1)[:, idx].astype(np.float64), 2 if kind == "srt" else 1)
+    A = np.zeros((6, H * W))
+    A[:, idx] = a
+    ref = n6.direct6_hex(f.astype(np.float64), A.reshape(6, H, W), idx, 0.5)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+
+
+def test_map6_scales_and_flags():
+    """bsf_scales_from_cov with N = 6 against the oracle's KKT map: ordinary,
+    clamped (rho beyond the six-directional bound), infeasible (tiny kernels)
+    and invalid pixels."""
+    dev = _cuda()
+    rng = np.random.default_rng(7)
+    n = 160
+    s = rng.uniform(0.5, 30.0, n)
+    r = rng.uniform(1.0, 8.0, n)
+    t = rng.uniform(0, math.pi, n)
+    r[:12] = rng.uniform(14.0, 40.0, 12)          # beyond the bound at most orientations
+    t[12:16] = np.array([0.0, math.pi / 6, math.pi / 3, math.pi / 2])  # along a direction: no bound
+    r[12:16] = 30.0
+    s[16:20] = rng.uniform(0.004, 0.015, 4)        # trace below 6 eps: p >= eps infeasible
+    s[20], r[21], t[22] = np.inf, 0.0, np.nan      # invalid
+    P = np.stack([s, r, t]).astype(np.float32)
+    sc, fl = api.scales_from_cov(torch.from_numpy(P).to(dev), kind="srt", N=6)
+    sc, fl = sc.cpu().numpy().astype(np.float64), fl.cpu().numpy()
+    ref, rfl = n6.map6(P.astype(np.float64), 2)
+    assert np.array_equal(fl, rfl)
+    ok = (rfl & 4) == 0
+    assert np.all(np.isnan(sc[:, ~ok]))
+    rel = np.abs(sc[:, ok] - ref[:, ok]) / np.maximum(ref[:, ok], 1e-12)
+    assert rel.max() < 2e-6, rel.max()
+
+
+@pytest.mark.parametrize("h", [1.0, 0.25])
+def test_other_lattice_spacings(h):
+    H, W = 70, 66
+    f = synth.image(H, W, seed=5, dtype="f32")
+    a6 = np.stack([synth.scale_field(H, W, seed=30 + k, lo=1.0, hi=3.5)[0] for k in range(6)]).astype(np.float32)
+    got, st = _run(f, a6, "scales", hex_spacing=h)
+    assert st == 0
+    idx = _sample(H, W, 16, seed=3)
+    ref = n6.direct6_hex(f.astype(np.float64), a6.astype(np.float64), idx, h)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+
+
+def test_edge_cases():
+    """1 x 1 and 1-row images, a small kernel (widths 0.6 px: the FP64 path is
+    built for widths of about half a pixel and more), invalid pixels (NaN
+    output and the status bit, the rest unaffected)."""
+    for H, W in [(1, 1), (1, 9), (7, 1)]:
+        f = synth.image(H, W, seed=H + W, dtype="f32")
+        a6 = np.full((6, H, W), 1.3, np.float32)
+        got, st = _run(f, a6, "scales")
+        assert st == 0
+        ref = n6.direct6_hex(f.astype(np.float64), a6.astype(np.float64), None, 0.5)
+        assert _nerr(got.ravel(), ref) < TOL
+    H, W = 40, 40
+    f = synth.image(H, W, seed=9, dtype="u8")
+    a6 = np.full((6, H, W), 2.0, np.float32)
+    a6[:, 5, 5] = 0.6
+    a6[2, 20, 20] = np.nan
+    a6[4, 30, 10] = -1.0
+    got, st = _run(f, a6, "scales")
+    assert st & (1 << L.BSF_EBADSCALE)
+    assert np.isnan(got[20, 20]) and np.isnan(got[30, 10])
+    idx = np.array([5 * W + 5, 0, 21 * W + 20, 39 * W + 39])
+    ref = n6.direct6_hex(f.astype(np.float64), a6.astype(np.float64), idx, 0.5)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+
+
+@pytest.mark.parametrize("lo,hi", [(1.0, 3.0), (20.0, 40.0)])
+def test_widths_at_the_relative_bound(lo, hi):
+    """Two widths at the six-directional map's lower bound sqrt(1e-3 T) (0.077
+    times the typical width): the conditioning the FP64 path is built for."""
+    H, W = 96, 96
+    f = synth.image(H, W, seed=16, dtype="f32")
+    a = synth.scale_field(H, W, seed=17, lo=lo, hi=hi)[0]
+    a6 = np.stack([a, a * 1.1, a * 0.9, a * 0.077, a * 0.077, a * 1.05]).astype(np.float32)
+    got, st = _run(f, a6, "scales")
+    assert st == 0
+    idx = _sample(H, W, 12, seed=4)
+    if hi > 10:  # large footprints: crops of the image hold them
+        idx = idx[:4]
+    ref = n6.direct6_hex(f.astype(np.float64), a6.astype(np.float64), idx, 0.5)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+
+
+def test_large_footprints_on_crops():
+    """sigma up to 48 px (the batch workload's largest kernels): windows of
+    more than 2000 lattice columns.  The oracle evaluates sampled pixels on
+    crops that hold their footprints."""
+    H, W = 448, 448
+    f = synth.image(H, W, seed=12, dtype="f32")
+    p = synth.srt_field(H, W, seed=13, sigma=(30.0, 48.0), rho=(1.0, 6.0))
+    got, st = _run(f, p, "srt")
+    assert st == 0
+    for y, x in [(224, 224), (60, 400), (447, 0)]:
+        a, _ = n6.map6(p[:, y, x].reshape(3, 1).astype(np.float64), 2)
+        ex, ey = n6.support_extent(n6.directions(6), a[:, 0])
+        x0, x1 = max(0, int(x - ex) - 2), min(W, int(x + ex) + 3)
+        y0, y1 = max(0, int(y - ey) - 2), min(H, int(y + ey) + 3)
+        A = np.zeros((6, y1 - y0, x1 - x0))
+        A[:, y - y0, x - x0] = a[:, 0]
+        ref = n6.direct6_hex(f[y0:y1, x0:x1].astype(np.float64), A, np.array([(y - y0) * (x1 - x0) + (x - x0)]),
+                             0.5, origin=(x0, y0))
+        assert abs(got[y, x] - ref[0]) < TOL * abs(ref[0])
+
+
+def test_host_pipeline_and_unsupported_entry_points():
+    dev = _cuda()
+    H, W = 80, 72
+    f = synth.image(H, W, seed=14, dtype="f32")
+    p = synth.srt_field(H, W, seed=15, sigma=(1.0, 4.0), rho=(1.0, 5.0))
+    ref, _ = _run(f, p, "srt")
+    ctx = api.context(dev)
+    o = api.make_opts()
+    fh = torch.from_numpy(f).pin_memory()
+    ph = torch.from_numpy(p).pin_memory()
+    oh = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    L.check(L.bsf_filter_host(ctx, fh.data_ptr(), L.BSF_F32, 1, 1, H, W, 6, ph.data_ptr(), L.BSF_PARAM_SRT, o,
+                              oh.data_ptr()), "bsf_filter_host")
+    L.check(L.bsf_host_sync(ctx), "bsf_host_sync")
+    assert np.array_equal(oh.numpy(), ref.astype(np.float32))
+    img = torch.from_numpy(f).to(dev)
+    with pytest.raises(L.BsfError) as e:
+        api.preintegrate(img, halo=8, N=6)
+    assert e.value.code == L.BSF_EUNSUPPORTED
+    with pytest.raises(L.BsfError) as e:
+        api.filter(img, torch.from_numpy(p).to(dev), kind="srt", N=5)
+    assert e.value.code == L.BSF_EUNSUPPORTED
+    with pytest.raises(L.BsfError) as e:
+        api.filter(img, torch.from_numpy(p).to(dev), kind="srt", N=6, hex_spacing=1.5)
+    assert e.value.code == L.BSF_EINVAL

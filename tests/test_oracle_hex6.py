@@ -155,6 +155,21 @@ def test_algorithm1_on_the_hexagonal_lattice_equals_the_definition():
         assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
 
 
+def test_definition_on_a_crop_equals_the_whole_image():
+    """The filter at a pixel depends only on the image inside its footprint:
+    evaluated on a crop placed at its origin in the plane, it is unchanged."""
+    rng = np.random.default_rng(8)
+    H, W = 26, 31
+    f = rng.uniform(0, 1, (H, W))
+    A = rng.uniform(0.8, 2.0, (6, H, W))
+    x, y = 17, 13
+    ref = n6.direct6_hex(f, A, np.array([y * W + x]), 0.5)
+    y0, x0 = 6, 9
+    crop = f[y0:, x0:]
+    got = n6.direct6_hex(crop, A[:, y0:, x0:], np.array([(y - y0) * (W - x0) + (x - x0)]), 0.5, origin=(x0, y0))
+    assert abs(got[0] - ref[0]) < 1e-13
+
+
 def test_transfer_error_falls_with_the_lattice_spacing():
     """Method error of the transfer against the definition on the pixel comb:
     second order in h on a smooth image."""
@@ -219,10 +234,12 @@ def test_map6_flags():
     assert fl[1] & n6.FLAG_CLAMPED
     assert fl[2] == 0
     assert fl[3] & n6.FLAG_INFEASIBLE and np.all(a[:, 3] >= math.sqrt(1e-3) * (1 - 1e-12))
+    # the bound is relative to the size: no width below sqrt(1e-3 T)
+    assert a[:, 2].min() >= math.sqrt(1e-3 * 12.0 * (4.0 + 4.0 / 3.0)) * (1 - 1e-9)
     assert fl[4] == n6.FLAG_INVALID and np.all(np.isnan(a[:, 4]))
     # clamped pixel: the target after clamping is reproduced, at the bound's elongation
     lmax, lmin = 4.0, 4.0 / 20.0
-    U = n6.U_boundN(0.2, 6)
+    U = n6.U_boundN(0.2, 6, 1 - 6 * n6.REL_BOUND6)
     s = lmax + lmin
     lmin2 = s / (1 + (1 - 1e-3) * U)
     C2 = _cov(math.sqrt(s - lmin2), (s - lmin2) / lmin2, 0.2)
