@@ -48,11 +48,15 @@ STENCIL_INT_OPS_PER_PX = 16 * 124
 # product (88), two words per product sum and accumulator (28), 32 for
 # position, truncation, bounds and addresses: 260 per tap
 STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
+# six directions: 64 taps x 24 lattice points x (15 weight FMAs + 1 accumulation FMA) x 2 flops
+HEX6_FLOPS_PER_PX = 64 * 24 * 16 * 2
+FP64_PEAK_TFLOPS = 1.25
 # Benchmarked workloads: (params kind, largest sigma or scale, forward+backward).
 BENCH_WORKLOADS = {
     "u2048_u8_n4": ("srt", 32.0, False),
     "u2048_f32_n4": ("srt", 32.0, False),
     "b4c3_4096_f32_n4": ("srt", 48.0, False),
+    "b4c3_4096_f32_n6": ("srt", 48.0, False),
     "b8_1024_f32_scales": ("scales", 24.0, True),
 }
 WORKLOAD_TEXT = {
@@ -61,7 +65,9 @@ WORKLOAD_TEXT = {
     "u2048_f32_n4": "2048x2048 f32 copy of the u8 image, N=4, sigma 1-32 px, rho 1-8, theta from a smooth "
                     "vector field, exact 128-bit fixed-point path",
     "b4c3_4096_f32_n4": "batch 4 x 3 channels x 4096x4096 f32 (uniform + 3 gratings), sigma 2-48 px, rho 1-6, "
-                        "theta uniform, filtered with N=4 (N=6 is not built), exact 128-bit fixed-point path",
+                        "theta uniform, filtered with N=4, exact 128-bit fixed-point path",
+    "b4c3_4096_f32_n6": "batch 4 x 3 channels x 4096x4096 f32 (uniform + 3 gratings), sigma 2-48 px, rho 1-6, "
+                        "theta uniform, N=6 (64-tap stencil) on the hexagonal lattice of spacing 0.5 px, FP64",
     "b8_1024_f32_scales": "batch 8 x 1024x1024 f32, learnable scale field a_k in [1,24]; one step = forward "
                           "filter + backward (gradients for image and scales)",
 }
@@ -256,7 +262,9 @@ def run_ours(args):
     from paper_1003_2022_gb300 import _lib as L
     from paper_1003_2022_gb300 import api
 
+    from paper_1003_2022_gb300 import synth as _synth
     kind_name, smax, train = BENCH_WORKLOADS[args.workload]
+    N = _synth.WORKLOADS[args.workload]["N"]
     f_np, p_np = _inputs(args.size, args.workload)
     B, C, H, W = f_np.shape
     u8 = f_np.dtype == np.uint8
@@ -276,7 +284,7 @@ def run_ours(args):
     sptr = int(stream.cuda_stream)
 
     def step(img=f, prm=p, o=out):
-        rc = L.bsf_filter(ctx, img.data_ptr(), dtype, B, C, H, W, 4, prm.data_ptr(), kind, opts, o.data_ptr(), sptr)
+        rc = L.bsf_filter(ctx, img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), kind, opts, o.data_ptr(), sptr)
         if rc != 0:
             raise L.BsfError(rc, "bsf_filter")
         if train:
@@ -354,7 +362,7 @@ def run_ours(args):
         # bsf_filter_host: the library's host-buffer entry point, copies of one step
         # overlapping the kernels of the previous one
         def e2e_step():
-            rc = L.bsf_filter_host(ctx, f_h.data_ptr(), dtype, B, C, H, W, 4, p_h.data_ptr(), kind, opts,
+            rc = L.bsf_filter_host(ctx, f_h.data_ptr(), dtype, B, C, H, W, N, p_h.data_ptr(), kind, opts,
                                    o_h.data_ptr())
             if rc != 0:
                 raise L.BsfError(rc, "bsf_filter_host")
@@ -421,11 +429,26 @@ def run_ours(args):
         per = (H + 2 * P) * (W + 2 * P) * ((8 if u8 else 16) + 8) * C
         chunks = -(-B // max(1, min(B, (16 << 30) // per)))
         launches += 13 * chunks * args.steps
+    if N == 6:
+        # six directions: FP64-bound stencil (64 taps x 24 lattice points, 15 weight FMAs
+        # and one accumulation FMA per point) against the nominal FP64 rate
+        fl_px = HEX6_FLOPS_PER_PX
+        achieved6 = fl_px * px_per_launch / (st_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved6, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved6 / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_hex6_stencil",
+                    "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
+                    "peak_note": "FP64 pipe: 1.25 TFLOP/s nominal dense FP64 of the GB300 (no FP64 figure is "
+                                 "measured on this pool); the stencil's FP64 flops per pixel are algorithmic",
+                    "fp64_flops_per_px": fl_px,
+                    "launches_per_step": n_st / args.steps,
+                    "preintegrate_note": "scale map + window transfer and six running sums (FP64), per chunk"}
+        launches = args.steps + 2 * nl
     line = {
         "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("int64" if u8 else "int128") if args.precision == "exact" else "f64", "data": "synthetic",
+        "dtype": "f64" if N == 6 else (("int64" if u8 else "int128") if args.precision == "exact" else "f64"),
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] if args.size is None else
                    f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
                    "workload_id": args.workload,
@@ -493,7 +516,7 @@ def run_serve(args):
             "steps": args.requests, "warmup": 8, "ms_per_step": 1e3 * st["makespan_s"] / args.requests,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128", "data": "synthetic",
             "config": {"workload": f"serving stream: {args.requests} requests, side log-uniform 256-{S}, 1 or 3 "
-                                   "channels f32, N in {4,6} (N=6 rejected: unsupported), sigma 1-40, rho 1-8, "
+                                   "channels f32, N in {4,6} (N=6 on the hexagonal lattice, FP64), sigma 1-40, rho 1-8, "
                                    "Poisson arrivals at 0.7x saturation", "slots": args.slots,
                        "hbm_budget_gb": args.hbm_gb, "arrival_rate_per_s": rate,
                        "saturation_gpixels_per_s": sat["gpixels_per_s"]},

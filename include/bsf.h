@@ -121,8 +121,8 @@ typedef struct {
                          covariance of each pass is C/m, of the m passes together C).
                          Passes after the first take the float32 output of the previous one. */
     float hex_spacing;  /* N = 6 only: spacing h (px) of the hexagonal lattice the image is
-                         transferred to, in [0.125, 1]; default 0.5.  The method error of the
-                         transfer falls like h^2, the pre-integration work grows like 1/h^2. */
+                         transferred to: 1, 0.5 (default), 0.25 or 0.125.  The method error of
+                         the transfer falls like h^2, the pre-integration work grows like 1/h^2. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -144,11 +144,14 @@ bsf_status bsf_destroy(bsf_ctx* ctx);
  * out: B*C*H*W floats.  Runs the scale map (Sec. 3.2.2, for COV/SRT), the
  * pre-integration (Algorithm 1 step 2) and the finite difference with ZP
  * interpolation (Algorithm 1 step 3).  opts may be NULL (defaults).
- * N = 6 (see the top of this file): each 64 x 64 tile of output pixels gets
- * its own window of the hexagonal lattice, sized from the tile's largest
- * footprint; the call synchronises the stream once (after the scale map) to
- * plan the windows.  Footprints wider than about 1000 px along x
- * (hex_spacing 0.5) return BSF_EINVAL. */
+ * N = 6 (see the top of this file): each 64 x 64 tile of output pixels (16 x
+ * 16 where the footprints are small) gets its own window of the hexagonal
+ * lattice, sized from the tile's largest footprint; the call synchronises the
+ * stream once (after the scale map) to plan the windows.  The FP64 form is
+ * accurate to 1e-5 for kernels whose widths are about half a pixel or more
+ * (the six-directional map keeps every width at least 0.077 times the
+ * typical one); footprints wider than about 1000 px along x (hex_spacing 0.5)
+ * return BSF_EINVAL. */
 bsf_status bsf_filter(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                       int64_t W, int N, const float* params, int kind, const bsf_opts* opts,
                       float* out, void* stream);

@@ -402,7 +402,7 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
                           const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
                           float ascale = 1.f) {
     const int fine = 16, coarse = 64, ratio = coarse / fine;
-    const float split_below = 48.f;  // px: largest half-extent for which a 64-tile is cut into 16-tiles
+    const float split_below = 16.f;  // px: largest half-extent for which a 64-tile is cut into 16-tiles
     const double h = (double)o.hex_spacing;
     const int64_t HW = H * W;
     const int fx = (int)((W + fine - 1) / fine), fy = (int)((H + fine - 1) / fine);
@@ -456,8 +456,8 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
             }
     std::vector<hex6_tile> tl(big);
     tl.insert(tl.end(), small.begin(), small.end());
-    // chunks of one tile size, at most 8 GiB of windows and 65535 tiles (a grid dimension)
-    const size_t budget = (size_t)8 << 30;
+    // chunks of one tile size, at most 2 GiB of windows and 65535 tiles (a grid dimension)
+    const size_t budget = (size_t)2 << 30;
     struct chunk {
         size_t first, last;
         int cols;
@@ -511,7 +511,9 @@ static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t 
     if (opts) *o = *opts;
     if (o->precision != BSF_PREC_EXACT && o->precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (o->iterations < 1 || o->iterations > 64) return BSF_EINVAL;
-    if (N == 6 && !(o->hex_spacing >= 0.125f && o->hex_spacing <= 1.f)) return BSF_EINVAL;
+    if (N == 6 && !(o->hex_spacing == 1.f || o->hex_spacing == 0.5f || o->hex_spacing == 0.25f ||
+                    o->hex_spacing == 0.125f))
+        return BSF_EINVAL;
     return BSF_OK;
 }
 

@@ -36,101 +36,94 @@
 
 namespace {
 
-#define BSF_QNAN64 (0.0 / 0.0)
+#define BSF_QNAN64 __longlong_as_double(0x7ff8000000000000LL)
 
-// cos / sin of 2 theta_k and of 4 theta_k, theta_k = k pi / 6; (-1)^k
-__host__ __device__ __forceinline__ double c2k(int k) {
-    const double t[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
-    return t[k];
-}
-__host__ __device__ __forceinline__ double s2k(int k) {
-    const double r = 0.86602540378443864676;
-    const double t[6] = {0.0, r, r, 0.0, -r, -r};
-    return t[k];
-}
-// null-space basis of the covariance constraint: rows z_k = (cos 4theta_k, sin 4theta_k, (-1)^k)
-__host__ __device__ __forceinline__ void zrow(int k, double z[3]) {
-    const double r = 0.86602540378443864676;
-    const double c4[6] = {1.0, -0.5, -0.5, 1.0, -0.5, -0.5};
-    const double s4[6] = {0.0, r, -r, 0.0, r, -r};
-    z[0] = c4[k];
-    z[1] = s4[k];
-    z[2] = (k & 1) ? -1.0 : 1.0;
-}
+// cos / sin of 2 theta_k, theta_k = k pi / 6, and the null-space basis of the
+// covariance constraint, rows z_k = (cos 4 theta_k, sin 4 theta_k, (-1)^k)
+// (orthogonal columns of norms^2 3, 3, 6).  In constant memory: the solver
+// indexes them with the (per-lane) active constraints.
+__constant__ double MAP6_C2[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+__constant__ double MAP6_S2[6] = {0.0, 0.86602540378443864676, 0.86602540378443864676, 0.0,
+                                  -0.86602540378443864676, -0.86602540378443864676};
+__constant__ double MAP6_Z[6][3] = {{1.0, 0.0, 1.0},
+                                    {-0.5, 0.86602540378443864676, -1.0},
+                                    {-0.5, -0.86602540378443864676, 1.0},
+                                    {1.0, 0.0, -1.0},
+                                    {-0.5, 0.86602540378443864676, 1.0},
+                                    {-0.5, -0.86602540378443864676, -1.0}};
 
 // ||K||^2 for six directions: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m)
 // = (S0^2 + |S1|^2) / 2, S0 = sum q_k, S1 = sum q_k exp(2 i theta_k), q = p^2
-__host__ __device__ double kurt6(const double p[6]) {
+__device__ __forceinline__ double kurt6(const double p[6]) {
     double s0 = 0.0, sr = 0.0, si = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const double q = p[k] * p[k];
         s0 += q;
-        sr += q * c2k(k);
-        si += q * s2k(k);
+        sr += q * MAP6_C2[k];
+        si += q * MAP6_S2[k];
     }
     return 0.5 * (s0 * s0 + sr * sr + si * si);
 }
 
-__host__ __device__ __forceinline__ void p_of_t(const double pbar[6], const double t[3], double p[6]) {
+__device__ __forceinline__ void p_of_t(const double pbar[6], const double t[3], double p[6]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        double z[3];
-        zrow(k, z);
-        p[k] = pbar[k] + z[0] * t[0] + z[1] * t[1] + z[2] * t[2];
-    }
+    for (int k = 0; k < 6; ++k) p[k] = pbar[k] + MAP6_Z[k][0] * t[0] + MAP6_Z[k][1] * t[1] + MAP6_Z[k][2] * t[2];
 }
 
-// solve the symmetric positive definite d x d system A x = b (d <= 3) by Cholesky
-__host__ __device__ __forceinline__ bool spd_solve(int d, double A[3][3], const double b[3], double x[3]) {
-    double L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int i = 0; i < d; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = A[i][j];
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            if (i == j) {
-                if (!(s > 0.0)) return false;
-                L[i][i] = sqrt(s);
-            } else {
-                L[i][j] = s / L[j][j];
-            }
-        }
+// A x = b for a symmetric positive definite d x d matrix, d = 1, 2, 3 (unrolled Cholesky)
+__device__ __forceinline__ bool spd_solve(int d, const double A[3][3], const double b[3], double x[3]) {
+    if (d == 1) {
+        if (!(A[0][0] > 0.0)) return false;
+        x[0] = b[0] / A[0][0];
+        return true;
     }
-    double y[3];
-    for (int i = 0; i < d; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-        y[i] = s / L[i][i];
+    if (d == 2) {
+        const double det = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+        if (!(A[0][0] > 0.0) || !(det > 0.0)) return false;
+        const double id = 1.0 / det;
+        x[0] = (A[1][1] * b[0] - A[0][1] * b[1]) * id;
+        x[1] = (A[0][0] * b[1] - A[0][1] * b[0]) * id;
+        return true;
     }
-    for (int i = d - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < d; ++k) s -= L[k][i] * x[k];
-        x[i] = s / L[i][i];
-    }
+    if (!(A[0][0] > 0.0)) return false;
+    const double l00 = sqrt(A[0][0]);
+    const double l10 = A[1][0] / l00, l20 = A[2][0] / l00;
+    const double d11 = A[1][1] - l10 * l10;
+    if (!(d11 > 0.0)) return false;
+    const double l11 = sqrt(d11);
+    const double l21 = (A[2][1] - l20 * l10) / l11;
+    const double d22 = A[2][2] - l20 * l20 - l21 * l21;
+    if (!(d22 > 0.0)) return false;
+    const double l22 = sqrt(d22);
+    const double y0 = b[0] / l00, y1 = (b[1] - l10 * y0) / l11, y2 = (b[2] - l20 * y0 - l21 * y1) / l22;
+    x[2] = y2 / l22;
+    x[1] = (y1 - l21 * x[2]) / l11;
+    x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
     return true;
 }
 
-// minimise ||K||^2 over p = pbar + Z t with p >= lb: primal active set, the
-// start is a strictly feasible point built from the hexagon geometry of the
-// covariance (the traceless part, normalised, is a convex combination of the
-// centre and two neighbouring vertices exp(2 i theta_k)).  Returns false when
-// no p >= lb reproduces the covariance.
 struct map6_p {
     double p[6];
     bool ok;
 };
 
-// (returns its result by value: the scales must not travel through a pointer
-// to the caller's local array, which the device build of this function did
-// not write back reliably)
-__host__ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
+// minimise ||K||^2 over p = pbar + Z t with p >= lb: primal active set.  The
+// start is a strictly feasible point built from the hexagon geometry of the
+// covariance (the traceless part, normalised, is a convex combination of the
+// centre and two neighbouring vertices exp(2 i theta_k)); the working set is a
+// bit mask of the bounds held at lb.  Returns ok = false when no p >= lb
+// reproduces the covariance.  (The result is returned by value: the scales
+// must not travel through a pointer to the caller's local array, which the
+// device build did not write back reliably.)
+__device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
+    const double PI3 = 1.04719755119659774615;
     map6_p res;
     res.ok = true;
     double* p = res.p;
-    const double PI3 = 1.04719755119659774615;
     double pbar[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * c2k(k) + Zs * s2k(k))) / 6.0;
+    for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * MAP6_C2[k] + Zs * MAP6_S2[k])) / 6.0;
     const double den = T - 6.0 * lb;
     if (!(den > 0.0)) {
         res.ok = false;
@@ -142,184 +135,221 @@ __host__ __device__ map6_p map6_active_set(double T, double Zc, double Zs, doubl
     int ka = (int)(ang / PI3);
     ka = ka < 0 ? 0 : (ka > 5 ? 5 : ka);
     const int kb = (ka + 1) % 6;
-    const double dt = c2k(ka) * s2k(kb) - s2k(ka) * c2k(kb);
-    const double la = (zr * s2k(kb) - zi * c2k(kb)) / dt;
-    const double lbb = (c2k(ka) * zi - s2k(ka) * zr) / dt;
+    const double dt = MAP6_C2[ka] * MAP6_S2[kb] - MAP6_S2[ka] * MAP6_C2[kb];
+    const double la = (zr * MAP6_S2[kb] - zi * MAP6_C2[kb]) / dt;
+    const double lbb = (MAP6_C2[ka] * zi - MAP6_S2[ka] * zr) / dt;
     double l0 = 1.0 - la - lbb;
     if (l0 < -1e-12) {
         res.ok = false;
         return res;
     }
     l0 = fmax(l0, 0.0);
-    double ps[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) ps[k] = lb + den * (l0 / 6.0 + (k == ka ? la : 0.0) + (k == kb ? lbb : 0.0));
     double t[3] = {0.0, 0.0, 0.0};
-    const double nrm[3] = {3.0, 3.0, 6.0};
+    const double tiny = 1e-13 * T;
+    int wmask = 0, nw = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        double z[3];
-        zrow(k, z);
-        for (int l = 0; l < 3; ++l) t[l] += z[l] * (ps[k] - pbar[k]) / nrm[l];
-    }
-    const double tiny = 1e-13 * T;
-    int W[3], nw = 0;
-    for (int k = 0; k < 6; ++k)
-        if (ps[k] <= lb + tiny) {
-            if (nw == 3) {  // the covariance is at a vertex of the feasible set: the only point
-                for (int j = 0; j < 6; ++j) p[j] = fmax(ps[j], lb);
-                return res;
-            }
-            W[nw++] = k;
+        const double ps = lb + den * (l0 / 6.0 + (k == ka ? la : 0.0) + (k == kb ? lbb : 0.0));
+        const double dps = ps - pbar[k];
+        t[0] += MAP6_Z[k][0] * dps / 3.0;
+        t[1] += MAP6_Z[k][1] * dps / 3.0;
+        t[2] += MAP6_Z[k][2] * dps / 6.0;
+        if (ps <= lb + tiny) {
+            wmask |= 1 << k;
+            ++nw;
         }
-    for (int it = 0; it < 80; ++it) {
+    }
+    if (nw > 3) {  // the covariance is at a vertex of the feasible set: the only point
         p_of_t(pbar, t, p);
-        // gradient and Hessian in t
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = fmax(p[k], lb);
+        return res;
+    }
+    for (int it = 0; it < 60; ++it) {
+        p_of_t(pbar, t, p);
         double s0 = 0.0, sr = 0.0, si = 0.0;
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
             const double q = p[k] * p[k];
             s0 += q;
-            sr += q * c2k(k);
-            si += q * s2k(k);
+            sr += q * MAP6_C2[k];
+            si += q * MAP6_S2[k];
         }
         const double h0 = 0.5 * (s0 * s0 + sr * sr + si * si);
+        // gradient and Hessian in t: H = 4 (sg sg^T + mr mr^T + mi mi^T) + 4 Z^T diag(Dq) Z
         double g[3] = {0, 0, 0}, Hm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         double sg[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
-            double z[3];
-            zrow(k, z);
-            const double dq = 0.5 * (s0 + c2k(k) * sr + s2k(k) * si);
+            const double dq = 0.5 * (s0 + MAP6_C2[k] * sr + MAP6_S2[k] * si);
             const double gp = 4.0 * p[k] * dq;
+#pragma unroll
             for (int l = 0; l < 3; ++l) {
-                g[l] += z[l] * gp;
-                const double y = p[k] * z[l];
-                sg[l] += y;
-                mr[l] += c2k(k) * y;
-                mi[l] += s2k(k) * y;
-                for (int m = 0; m <= l; ++m) Hm[l][m] += 4.0 * dq * z[l] * z[m];
+                const double z = MAP6_Z[k][l];
+                g[l] += z * gp;
+                sg[l] += p[k] * z;
+                mr[l] += MAP6_C2[k] * p[k] * z;
+                mi[l] += MAP6_S2[k] * p[k] * z;
+#pragma unroll
+                for (int m = 0; m <= l; ++m) Hm[l][m] += 4.0 * dq * z * MAP6_Z[k][m];
             }
         }
+#pragma unroll
         for (int l = 0; l < 3; ++l)
+#pragma unroll
             for (int m = 0; m <= l; ++m) {
                 Hm[l][m] += 4.0 * (sg[l] * sg[m] + mr[l] * mr[m] + mi[l] * mi[m]);
                 Hm[m][l] = Hm[l][m];
             }
-        // null space of the working set
-        double N[3][3];
-        int d = 3 - nw;
-        if (nw == 0) {
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) N[a][b] = (a == b) ? 1.0 : 0.0;
-        } else if (nw == 1) {
-            double z[3];
-            zrow(W[0], z);
-            const double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
-            double n1[3] = {z[0] / zn, z[1] / zn, z[2] / zn};
-            int e = 0;
-            if (fabs(n1[1]) < fabs(n1[e])) e = 1;
-            if (fabs(n1[2]) < fabs(n1[e])) e = 2;
+        // the first two bounds of the working set, and an orthonormal basis N of
+        // the directions that keep them
+        double za[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
+        int seen = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if ((wmask >> k) & 1) {
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    if (seen == 0) za[l] = MAP6_Z[k][l];
+                    if (seen == 1) zb[l] = MAP6_Z[k][l];
+                }
+                ++seen;
+            }
+        const int d = 3 - nw;
+        double N[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        if (nw == 1) {
+            const double zn = sqrt(za[0] * za[0] + za[1] * za[1] + za[2] * za[2]);
+            const double n1[3] = {za[0] / zn, za[1] / zn, za[2] / zn};
+            // u: the unit vector of the smallest component of n1, made orthogonal to n1
             double u[3] = {0, 0, 0};
-            u[e] = 1.0;
-            const double dd = n1[e];
-            for (int a = 0; a < 3; ++a) u[a] -= dd * n1[a];
+            const int e = (fabs(n1[1]) < fabs(n1[0])) ? ((fabs(n1[2]) < fabs(n1[1])) ? 2 : 1)
+                                                         : ((fabs(n1[2]) < fabs(n1[0])) ? 2 : 0);
+            const double dd = e == 0 ? n1[0] : (e == 1 ? n1[1] : n1[2]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) u[l] = (l == e ? 1.0 : 0.0) - dd * n1[l];
             const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            for (int a = 0; a < 3; ++a) u[a] /= un;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) u[l] /= un;
             const double v[3] = {n1[1] * u[2] - n1[2] * u[1], n1[2] * u[0] - n1[0] * u[2], n1[0] * u[1] - n1[1] * u[0]};
-            for (int a = 0; a < 3; ++a) {
-                N[a][0] = u[a];
-                N[a][1] = v[a];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                N[l][0] = u[l];
+                N[l][1] = v[l];
             }
         } else if (nw == 2) {
-            double za[3], zb[3];
-            zrow(W[0], za);
-            zrow(W[1], zb);
-            double n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2], za[0] * zb[1] - za[1] * zb[0]};
+            const double n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2],
+                                 za[0] * zb[1] - za[1] * zb[0]};
             const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-            for (int a = 0; a < 3; ++a) N[a][0] = n[a] / nn;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) N[l][0] = n[l] / nn;
         }
         double step[3] = {0, 0, 0}, dec = 0.0;
         if (d > 0) {
-            double Hr[3][3], gr[3], u[3];
-            for (int a = 0; a < d; ++a) {
-                gr[a] = 0.0;
+            double Hr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gr[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= d) continue;
+#pragma unroll
                 for (int l = 0; l < 3; ++l) gr[a] -= N[l][a] * g[l];
-                for (int b = 0; b < d; ++b) {
-                    double s = 0.0;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (b >= d) continue;
+                    double sab = 0.0;
+#pragma unroll
                     for (int l = 0; l < 3; ++l)
-                        for (int m = 0; m < 3; ++m) s += N[l][a] * Hm[l][m] * N[m][b];
-                    Hr[a][b] = s;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) sab += N[l][a] * Hm[l][m] * N[m][b];
+                    Hr[a][b] = sab;
                 }
             }
             if (!spd_solve(d, Hr, gr, u)) break;
-            for (int l = 0; l < 3; ++l) {
-                step[l] = 0.0;
-                for (int a = 0; a < d; ++a) step[l] += N[l][a] * u[a];
-            }
+#pragma unroll
+            for (int l = 0; l < 3; ++l) step[l] = N[l][0] * u[0] + (d > 1 ? N[l][1] * u[1] : 0.0) +
+                                                  (d > 2 ? N[l][2] * u[2] : 0.0);
             dec = -(g[0] * step[0] + g[1] * step[1] + g[2] * step[2]);
         }
+        // converged on the face when the Newton step is at the rounding level of t
+        // (the decrement alone cannot tell: near the optimum it is rounding noise)
         const double smax = fmax(fabs(step[0]), fmax(fabs(step[1]), fabs(step[2])));
-        if (d == 0 || dec <= 1e-22 * h0 || smax <= 1e-14 * T) {
+        if (d == 0 || dec <= 0.0 || smax <= 1e-12 * T) {
             // converged on the face: bound multipliers from g = sum_{k in W} lambda_k z_k
             if (nw == 0) return res;
-            double G[3][3], rhs[3], lam[3];
-            for (int a = 0; a < nw; ++a) {
-                double za[3];
-                zrow(W[a], za);
-                rhs[a] = za[0] * g[0] + za[1] * g[1] + za[2] * g[2];
-                for (int b = 0; b < nw; ++b) {
-                    double zb[3];
-                    zrow(W[b], zb);
-                    G[a][b] = za[0] * zb[0] + za[1] * zb[1] + za[2] * zb[2];
+            double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[3] = {0, 0, 0}, lam[3] = {0, 0, 0};
+            int idx[3] = {0, 0, 0}, a = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if ((wmask >> k) & 1) {
+                    if (a < 3) idx[a] = k;
+                    ++a;
+                }
+            for (int i = 0; i < nw; ++i) {
+                const int ki = idx[i];
+                rhs[i] = MAP6_Z[ki][0] * g[0] + MAP6_Z[ki][1] * g[1] + MAP6_Z[ki][2] * g[2];
+                for (int j2 = 0; j2 < nw; ++j2) {
+                    const int kj = idx[j2];
+                    G[i][j2] = MAP6_Z[ki][0] * MAP6_Z[kj][0] + MAP6_Z[ki][1] * MAP6_Z[kj][1] +
+                               MAP6_Z[ki][2] * MAP6_Z[kj][2];
                 }
             }
             if (!spd_solve(nw, G, rhs, lam)) return res;
             int worst = -1;
             const double gs = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
             double lw = -1e-10 * (gs + 1e-300);
-            for (int a = 0; a < nw; ++a)
-                if (lam[a] < lw) {
-                    lw = lam[a];
-                    worst = a;
+            for (int i = 0; i < nw; ++i)
+                if (lam[i] < lw) {
+                    lw = lam[i];
+                    worst = idx[i];
                 }
             if (worst < 0) {
-                for (int a = 0; a < nw; ++a) p[W[a]] = lb;
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if ((wmask >> k) & 1) p[k] = lb;
                 return res;
             }
-            for (int a = worst; a < nw - 1; ++a) W[a] = W[a + 1];
+            wmask &= ~(1 << worst);
             --nw;
             continue;
         }
         // longest step along the Newton direction that keeps p >= lb
         double amax = 1.0;
         int blk = -1;
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
-            bool inw = false;
-            for (int a = 0; a < nw; ++a) inw |= (W[a] == k);
-            if (inw) continue;
-            double z[3];
-            zrow(k, z);
-            const double dp = z[0] * step[0] + z[1] * step[1] + z[2] * step[2];
+            if ((wmask >> k) & 1) continue;
+            const double dp = MAP6_Z[k][0] * step[0] + MAP6_Z[k][1] * step[1] + MAP6_Z[k][2] * step[2];
             if (dp < 0.0) {
-                const double a = fmax(p[k] - lb, 0.0) / (-dp);
-                if (a < amax) {
-                    amax = a;
+                const double ak = fmax(p[k] - lb, 0.0) / (-dp);
+                if (ak < amax) {
+                    amax = ak;
                     blk = k;
                 }
             }
         }
+        // backtracking (Armijo) while far from the optimum; near it the full Newton
+        // step converges quadratically and the test would only see rounding noise
         double alpha = amax;
-        for (int bt = 0; bt < 40; ++bt) {
-            double tn[3] = {t[0] + alpha * step[0], t[1] + alpha * step[1], t[2] + alpha * step[2]}, pn[6];
-            p_of_t(pbar, tn, pn);
-            if (kurt6(pn) <= h0 - 0.25 * alpha * dec) break;
-            alpha *= 0.5;
+        if (dec > 1e-10 * h0) {
+            for (int bt = 0; bt < 40; ++bt) {
+                const double tn[3] = {t[0] + alpha * step[0], t[1] + alpha * step[1], t[2] + alpha * step[2]};
+                double pn[6];
+                p_of_t(pbar, tn, pn);
+                if (kurt6(pn) <= h0 - 0.25 * alpha * dec) break;
+                alpha *= 0.5;
+            }
         }
+#pragma unroll
         for (int l = 0; l < 3; ++l) t[l] += alpha * step[l];
-        if (blk >= 0 && alpha == amax && nw < 3) W[nw++] = blk;
+        if (blk >= 0 && alpha == amax && nw < 3) {
+            wmask |= 1 << blk;
+            ++nw;
+        }
     }
     p_of_t(pbar, t, p);
-    for (int a = 0; a < nw; ++a) p[W[a]] = lb;
-    for (int k = 0; k < 6; ++k) p[k] = fmax(p[k], lb);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if ((wmask >> k) & 1) p[k] = lb;
+        p[k] = fmax(p[k], lb);
+    }
     return res;
 }
 
@@ -335,7 +365,7 @@ constexpr double MAP6_REL_BOUND = 1e-3;
 
 // covariance (kind COV) or (sigma, rho, theta) (kind SRT) -> six scales; the
 // flags and the elongation clamp follow the four-directional map
-__host__ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, double eps, double eta) {
+__device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, double eps, double eta) {
     map6_result R;
     R.flag = 0;
     const double v0 = v0f, v1 = v1f, v2 = v2f;
@@ -461,117 +491,157 @@ __global__ void k_map6_out(const float* __restrict__ params, int kind, long long
     if (flags) flags[p] = (uint8_t)R.flag;
 }
 
-constexpr int PRE_THREADS = 1024;
-constexpr int PRE_CPT = 4;  // window columns per thread: at most 4096
+constexpr int PRE_THREADS = 512;
+constexpr int PRE_CPT = 8;  // window columns per thread
+constexpr int MU_FRAC_BITS = 24;  // fixed point of the transferred masses
 
 // step 2 on one window: transfer of the image and the six running sums, row by
-// row; the state of each sum (its last row, two for the 90-degree sum) stays
-// in shared memory
+// row.  The sums are exact: the masses are rounded once to fixed point with
+// 24 fractional bits (a change of the measure of at most 2^-25 per lattice
+// point) and summed in 128-bit integers (the largest windows need about 2^83),
+// so the only rounding of the pre-integrated values is the final conversion
+// to FP64, which stores them times 2^24.  The state of each sum (its last
+// row, two for the 90-degree sum) is kept per column: in shared memory for
+// the four sums whose rows shift by one to three columns (the neighbouring
+// threads read them), in registers for the two that do not shift.
+// Shared-memory index of window column c: one padding element after every
+// PRE_CPT, so that the 32 lanes of a warp, which own columns PRE_CPT apart,
+// touch every bank once per 128 bytes (without it, a 16-byte state access of
+// a warp is a 32-way bank conflict).
+__device__ __forceinline__ int pidx(int c) { return c + c / PRE_CPT; }
+
 template <class InT>
 __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restrict__ img, int C, int H, int W,
                                                              double h, const hex6_tile* __restrict__ tiles,
                                                              double* __restrict__ scratch) {
-    extern __shared__ double sm6[];
+    extern __shared__ u128 smq[];
     const hex6_tile tl = tiles[blockIdx.x];
     const int c = blockIdx.y;
     const int ncol = tl.ncol, nrow = tl.nrow;
-    double* s30 = sm6;
-    double* s60 = s30 + ncol;
-    double* s90a = s60 + ncol;
-    double* s90b = s90a + ncol;
-    double* s120 = s90b + ncol;
-    double* s150 = s120 + ncol;
-    double* wt = s150 + ncol;  // 32 warp totals
+    const int np = pidx(ncol) + 1;
+    u128* s30 = smq;
+    u128* s60 = s30 + np;
+    u128* s90b = s60 + np;
+    u128* s120 = s90b + np;
+    u128* wt = s120 + np;  // warp totals
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < 6 * ncol; k += PRE_THREADS) sm6[k] = 0.0;
+    for (int k = tid; k < 4 * np; k += PRE_THREADS) smq[k] = 0;
     const InT* f = img + ((size_t)tl.b * C + c) * (size_t)H * W;
     double* G = scratch + tl.off + (long long)c * ncol * nrow;
-    const double rs3 = 0.57735026918962576451;  // 1/sqrt3
+    // The transfer weights need only single precision: an error in a mass is a
+    // small change of the input measure, which the exact sums carry through
+    // without amplification.  With h a power of two the lattice x-coordinates
+    // h (i + j/2) are exact in FP32; the y-offset of a row is rounded once.
+    const float hf = (float)h, ih = 1.0f / hf;
+    const float rs3 = 0.57735026918962576451f;  // 1/sqrt3
     const double hy = h * 0.86602540378443864676;
+    const float qscale = (float)(1 << MU_FRAC_BITS);
     const int c0 = tid * PRE_CPT;
+    u128 s90a[PRE_CPT], s150[PRE_CPT], y[PRE_CPT];
+#pragma unroll
+    for (int e = 0; e < PRE_CPT; ++e) s90a[e] = s150[e] = 0;
     __syncthreads();
     for (int r = 0; r < nrow; ++r) {
         const int j = tl.j0w + r;
-        double x[PRE_CPT];
-        double run = 0.0;
+        const double pyd = hy * (double)j;
+        const double kyd = floor(pyd);
+        const int ky0 = (int)kyd;
+        const float dy0 = (float)(kyd - pyd);  // (pixel row ky0) - (lattice row), in (-1, 0]
+        u128 run = 0;
 #pragma unroll
         for (int e = 0; e < PRE_CPT; ++e) {
             const int cc = c0 + e;
-            double mu = 0.0;
+            float mu = 0.f;
             if (cc < ncol) {
                 const int i = cc + tl.i_left - 2 * r;
-                const double px = h * ((double)i + 0.5 * (double)j), py = hy * (double)j;
-                const int kx0 = (int)floor(px), ky0 = (int)floor(py);
+                const float px = hf * ((float)i + 0.5f * (float)j);
+                const float kxf = floorf(px);
+                const int kx0 = (int)kxf;
+                const float dx0 = kxf - px;
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
                     const int ky = ky0 + dy;
                     if (ky < 0 || ky >= H) continue;
+                    const float ddy = (dy0 + (float)dy) * ih;
+                    const float dt = 2.f * rs3 * ddy;
 #pragma unroll
                     for (int dx = 0; dx < 2; ++dx) {
                         const int kx = kx0 + dx;
                         if (kx < 0 || kx >= W) continue;
-                        // lattice coordinates of pixel - lattice point
-                        const double ddx = ((double)kx - px) / h, ddy = ((double)ky - py) / h;
-                        const double dt = 2.0 * rs3 * ddy, ds = ddx - rs3 * ddy;
-                        const double w = 1.0 - fmax(fabs(ds), fmax(fabs(dt), fabs(ds + dt)));
-                        if (w > 0.0) mu += w * (double)f[(size_t)ky * W + kx];
+                        // lattice coordinates of pixel - lattice point; weight = the hat of the point
+                        const float ds = (dx0 + (float)dx) * ih - rs3 * ddy;
+                        const float w = 1.f - fmaxf(fabsf(ds), fmaxf(fabsf(dt), fabsf(ds + dt)));
+                        if (w > 0.f) mu = fmaf(w, (float)f[(size_t)ky * W + kx], mu);
                     }
                 }
             }
-            run += mu;
-            x[e] = run;
+            run += (u128)(i128)__float2ll_rn(mu * qscale);
+            y[e] = run;
         }
         // block-wide scan of the thread totals (the 0-degree sum along the row)
-        double v = run;
+        u128 v = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const double u = __shfl_up_sync(0xffffffffu, v, o);
+            const u128 u = shfl_up_T(v, o);
             if (lane >= o) v += u;
         }
         if (lane == 31) wt[warp] = v;
         __syncthreads();
-        if (warp == 0) {
-            double u = lane < PRE_THREADS / 32 ? wt[lane] : 0.0;
+        // every warp scans the warp totals itself (no second barrier)
+        u128 wsum = lane < PRE_THREADS / 32 ? wt[lane] : (u128)0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double z = __shfl_up_sync(0xffffffffu, u, o);
-                if (lane >= o) u += z;
-            }
-            if (lane < PRE_THREADS / 32) wt[lane] = u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u128 u = shfl_up_T(wsum, o);
+            if (lane >= o) wsum += u;
         }
-        __syncthreads();
-        const double off = (v - run) + (warp > 0 ? wt[warp - 1] : 0.0);
-        // the other five sums read their previous rows, then the states advance;
-        // the 90-degree (two rows back) and 150-degree states of a column are
-        // read by its own thread only, the others also by the next columns' threads
-        double n30[PRE_CPT], n60[PRE_CPT], n120[PRE_CPT], o90[PRE_CPT];
+        const u128 wprev = shfl_idx_T(wsum, warp > 0 ? warp - 1 : 0);
+        const u128 off = (v - run) + (warp > 0 ? wprev : (u128)0);
+        // the other five sums, one after the other: a sum whose row shifts reads
+        // its neighbours' previous row, then (after a barrier) stores its own row
 #pragma unroll
         for (int e = 0; e < PRE_CPT; ++e) {
             const int cc = c0 + e;
-            if (cc >= ncol) continue;
-            double y = x[e] + off;
-            y += cc >= 3 ? s30[cc - 3] : 0.0;
-            n30[e] = y;
-            y += cc >= 2 ? s60[cc - 2] : 0.0;
-            n60[e] = y;
-            y += cc >= 3 ? s90b[cc - 3] : 0.0;
-            o90[e] = s90a[cc];
-            s90a[cc] = y;
-            y += cc >= 1 ? s120[cc - 1] : 0.0;
-            n120[e] = y;
-            y += s150[cc];
-            s150[cc] = y;
-            G[(long long)r * ncol + cc] = y;
+            y[e] += off;
+            if (cc < ncol && cc >= 3) y[e] += s30[pidx(cc - 3)];
         }
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < PRE_CPT; ++e) {
             const int cc = c0 + e;
             if (cc >= ncol) continue;
-            s30[cc] = n30[e];
-            s60[cc] = n60[e];
-            s90b[cc] = o90[e];
-            s120[cc] = n120[e];
+            s30[pidx(cc)] = y[e];
+            if (cc >= 2) y[e] += s60[pidx(cc - 2)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            if (cc >= ncol) continue;
+            s60[pidx(cc)] = y[e];
+            if (cc >= 3) y[e] += s90b[pidx(cc - 3)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            if (cc >= ncol) continue;
+            s90b[pidx(cc)] = s90a[e];  // the row before, for the row after next
+            s90a[e] = y[e];
+            if (cc >= 1) y[e] += s120[pidx(cc - 1)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PRE_CPT; ++e) {
+            const int cc = c0 + e;
+            if (cc >= ncol) continue;
+            s120[pidx(cc)] = y[e];
+            y[e] += s150[e];
+            s150[e] = y[e];
+            // exact 128-bit value -> FP64 (stored times 2^24)
+            const i128 v128 = (i128)y[e];
+            const long long hi = (long long)(v128 >> 64);
+            const unsigned long long lo = (unsigned long long)v128;
+            G[(long long)r * ncol + cc] = fma((double)hi, 18446744073709551616.0, (double)lo);
         }
     }
 }
@@ -692,9 +762,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
         }
         acc += (__popc(q) & 1) ? -F : F;
     }
-    // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.)
+    // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.); the
+    // window holds the running sums times 2^24
     const double h2 = h * h;
-    *o = (float)(acc * 6.0 * h2 * h2 / prod);
+    *o = (float)(acc * (6.0 * h2 * h2 / 16777216.0) / prod);
 }
 
 }  // namespace
@@ -732,7 +803,9 @@ void hex6_window(int tx, int ty, int tile, int H, int W, double ex, double ey, d
     t->size = tile;
 }
 
-int hex6_max_cols() { return PRE_THREADS * PRE_CPT; }
+// widest window: PRE_CPT columns per thread, and four 128-bit state rows plus the
+// warp totals in 227 KB of shared memory
+int hex6_max_cols() { return std::min(PRE_THREADS * PRE_CPT, (232448 - 32 * 16) / (4 * 16) * PRE_CPT / (PRE_CPT + 1) - 8); }
 
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st) {
@@ -752,7 +825,7 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
                                int ntiles, int ncol_max, double* scratch, cudaStream_t st) {
-    const size_t smem = (6 * (size_t)ncol_max + 32) * sizeof(double);
+    const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
     dim3 grid(ntiles, C);
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SUPPORTED_N = (4,)
+SUPPORTED_N = (4, 6)
 
 
 @dataclass
@@ -67,9 +67,21 @@ def _max_sigma(params) -> float:
     return float(fin.max()) if fin.size else 0.0
 
 
-def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: float) -> int:
-    """Device bytes one request holds while in flight: image, field, output,
-    pre-integrated buffers (8 B/elem for uint8, 16 B for float32) and carries."""
+def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: float, N: int = 4) -> int:
+    """Device bytes one request holds while in flight: image, field, output and
+    the library's scratch.  N = 4: pre-integrated buffers (8 B/elem for uint8,
+    16 B for float32) and scan carries.  N = 6: FP64 scales (48 B/px) and the
+    lattice windows of the 64-pixel tiles (spacing 0.5 px), at most 2 GiB of
+    them at a time."""
+    io = C * H * W * image_itemsize + 3 * H * W * 4 + C * H * W * 4
+    if N == 6:
+        # half-extent of a footprint: sum_k a_k |cos theta_k| / 2 <= sqrt(3 sum_k a_k^2) / 2
+        # = sqrt(36 tr C) / 2 <= 4.25 sigma; a window spans R = 64 + 2 ext + 10 px and holds
+        # about 5.46 R x 2.31 R lattice points of 8 B
+        R = 64 + 2 * 4.25 * max_sigma + 10
+        tiles = math.ceil(H / 64) * math.ceil(W / 64)
+        win = min(2 << 30, int(tiles * C * 8 * 5.46 * R * 2.31 * R))
+        return io + 48 * H * W + win
     P = halo_for_sigma(max_sigma)
     Hp, Wp = H + 2 * P, W + 2 * P
     elem = 8 if image_itemsize == 1 else 16
@@ -77,7 +89,6 @@ def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: floa
     nb = (Hp + bh - 1) // bh
     buf = C * Hp * Wp * elem
     carries = 10 * C * nb * Wp * elem
-    io = C * H * W * image_itemsize + 3 * H * W * 4 + C * H * W * 4
     return buf + carries + io
 
 
@@ -219,7 +230,7 @@ class Server:
                 nxt += 1
                 C, H, W = r.image.shape
                 isz = r.image.element_size() if self.torch.is_tensor(r.image) else r.image.dtype.itemsize
-                nb = footprint_bytes(C, H, W, isz, r.max_scale or _max_sigma(r.params))
+                nb = footprint_bytes(C, H, W, isz, r.max_scale or _max_sigma(r.params), r.N)
                 results[r.rid].nbytes = nb
                 why = self.sched.offer(r.rid, nb, r.N)
                 if why is not None:

@@ -141,8 +141,10 @@ WORKLOADS = {
     # same image as f32
     "u2048_f32_n4": dict(B=1, C=1, H=2048, W=2048, dtype="f32", N=4, sigma=(1.0, 32.0), rho=(1.0, 8.0),
                          theta="vector"),
-    # batch of 4 RGB 4096x4096 f32 U[0,1) + gratings, sigma 2-48, rho 1-6, theta uniform
-    # (the paper-shaped batch asks N=6; filtered here with N=4)
+    # batch of 4 RGB 4096x4096 f32 U[0,1) + gratings, sigma 2-48, rho 1-6, theta uniform,
+    # filtered with six directions (the paper-shaped batch) or with four
+    "b4c3_4096_f32_n6": dict(B=4, C=3, H=4096, W=4096, dtype="f32g", N=6, sigma=(2.0, 48.0), rho=(1.0, 6.0),
+                             theta="uniform"),
     "b4c3_4096_f32_n4": dict(B=4, C=3, H=4096, W=4096, dtype="f32g", N=4, sigma=(2.0, 48.0), rho=(1.0, 6.0),
                              theta="uniform"),
     # batch of 8 1024x1024 f32 U[0,1) with a learnable scale field a_k in [1, 24]

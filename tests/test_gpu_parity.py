@@ -245,9 +245,10 @@ def test_unsupported_n_and_bad_args():
     dev = _cuda()
     f = torch.zeros((8, 8), dtype=torch.uint8, device=dev)
     p = torch.ones((3, 8, 8), dtype=torch.float32, device=dev)
-    with pytest.raises(L.BsfError) as e:
-        api.filter(f, p, kind="srt", N=6, halo=8)
-    assert e.value.code == L.BSF_EUNSUPPORTED
+    for N in (2, 5, 8):
+        with pytest.raises(L.BsfError) as e:
+            api.filter(f, p, kind="srt", N=N, halo=8)
+        assert e.value.code == L.BSF_EUNSUPPORTED
     rc = L.bsf_filter(api.context(dev), 0, L.BSF_U8, 1, 1, 8, 8, 4, p.data_ptr(), L.BSF_PARAM_SRT, None,
                       p.data_ptr(), 0)
     assert rc == L.BSF_EINVAL

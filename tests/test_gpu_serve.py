@@ -1,6 +1,6 @@
-"""Serving loop on the GPU: requests of mixed sizes and channel counts that
-arrive while others run are admitted as slots and memory free up, overlap on
-the device, and each result equals the same request filtered alone."""
+"""Serving loop on the GPU: requests of mixed sizes, channel counts and N (4
+and 6) that arrive while others run are admitted as slots and memory free up,
+overlap on the device, and each result equals the same request filtered alone."""
 import numpy as np
 import pytest
 
@@ -25,19 +25,19 @@ def test_results_same_alone_and_in_the_mix():
         dtype = "u8" if i % 3 == 0 else "f32"
         img = np.stack([synth.image(side, side, seed=100 + i, dtype=dtype, sub=c) for c in range(C)])
         prm = synth.srt_field(side, side, seed=100 + i, sigma=(1.0, 12.0), rho=(1.0, 8.0))
-        N = 6 if i == 7 else 4
+        N = 6 if i % 4 == 1 else (5 if i == 7 else 4)
         reqs.append(Request(i, img, prm, N=N, arrival=t, max_scale=12.0))
         # a burst of six at t = 0 fills the slots together; the rest arrive over time
         if i >= 5:
             t += float(rng.exponential(0.002))
-    srv = Server(slots=3, budget_bytes=96 << 20, device=0)
+    srv = Server(slots=3, budget_bytes=1 << 30, device=0)
     try:
         results, stats = srv.run(reqs)
     finally:
         srv.close()
     assert stats["completed"] == 23 and stats["rejected"] == 1
     assert results[7].status.startswith("unsupported N")
-    assert stats["peak_bytes"] <= 96 << 20
+    assert stats["peak_bytes"] <= 1 << 30
     overlapped = sum(1 for a in results for b in results
                      if a.rid < b.rid and a.status == b.status == "ok"
                      and a.t_admit < b.t_done and b.t_admit < a.t_done)
@@ -46,7 +46,7 @@ def test_results_same_alone_and_in_the_mix():
         if r.status != "ok":
             continue
         alone = api.filter(torch.from_numpy(q.image).to(dev), torch.from_numpy(q.params).to(dev), kind="srt",
-                           max_scale=12.0).cpu().numpy()
+                           N=q.N, max_scale=12.0).cpu().numpy()
         err = np.abs(r.out - alone).max() / np.abs(alone).max()
         assert err <= 1e-5, (r.rid, err)
     assert stats["p50_ms"] is not None and stats["p99_ms"] >= stats["p50_ms"]

@@ -66,7 +66,8 @@ def test_continuous_admission_while_others_run():
 def test_rejections_have_reasons():
     sch = Scheduler(2, 1000)
     assert "budget" in sch.offer(0, 5000, 4)
-    assert "N=6" in sch.offer(1, 10, 6)
+    assert sch.offer(1, 10, 6) is None
+    assert "N=5" in sch.offer(2, 10, 5)
     assert sch.offer(2, 10, 4) is None
 
 
@@ -76,6 +77,10 @@ def test_footprint_grows_with_size_channels_and_sigma():
     assert footprint_bytes(1, 512, 512, 4, 2.0) > 3.5 * f1
     assert footprint_bytes(1, 256, 256, 4, 40.0) > f1
     assert footprint_bytes(1, 256, 256, 1, 2.0) < f1
+    # six directions: FP64 scales and lattice windows, growing with the footprint
+    g1 = footprint_bytes(1, 256, 256, 4, 2.0, 6)
+    assert g1 > 48 * 256 * 256 and footprint_bytes(1, 256, 256, 4, 20.0, 6) > 4 * g1
+    assert footprint_bytes(3, 4096, 4096, 4, 48.0, 6) < (2 << 30) + 4096 * 4096 * (48 + 40)
 
 
 def test_cancel_only_queued_requests():
