@@ -161,3 +161,49 @@ def test_image_gradient_large(side, accuracy_record):
     fig = _figures(np.concatenate(gots), np.concatenate(refs))
     accuracy_record[f"grad_image_{side}_f32_scales/exact"] = fig
     assert fig["max_norm"] < TOL
+
+
+def _direct6_on_crop(f, a_px, y, x, h=0.5, definition=False):
+    """The six-directional oracle at one pixel, on a crop that holds its footprint."""
+    from oracle import n6
+    H, W = f.shape
+    ex, ey = n6.support_extent(n6.directions(6), a_px)
+    x0, x1 = max(0, int(x - ex) - 3), min(W, int(x + ex) + 4)
+    y0, y1 = max(0, int(y - ey) - 3), min(H, int(y + ey) + 4)
+    A = np.zeros((6, y1 - y0, x1 - x0))
+    A[:, y - y0, x - x0] = a_px
+    loc = np.array([(y - y0) * (x1 - x0) + (x - x0)])
+    crop = f[y0:y1, x0:x1].astype(np.float64)
+    if definition:
+        return float(n6.direct6(crop, A, loc)[0])
+    return float(n6.direct6_hex(crop, A, loc, h, origin=(x0, y0))[0])
+
+
+def test_batched_rgb_4096_workload_six_directions(accuracy_record):
+    """The paper-shaped batch with N = 6 (4 x 3 x 4096 x 4096, sigma 2-48, rho
+    1-6) in one call, against the oracle's definition on the transferred image
+    at sampled pixels of every (image, channel).  The method error of the
+    transfer (against the definition on the pixel comb) is recorded beside it."""
+    from oracle import n6
+    dev = _cuda()
+    imgs, prm = synth.batch_inputs("b4c3_4096_f32_n6")
+    B, C, H, W = imgs.shape
+    out = api.filter(torch.from_numpy(imgs).to(dev), torch.from_numpy(prm).to(dev), kind="srt", N=6)
+    st = api.device_status(dev)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    out = out.cpu().numpy()
+    gots, refs, mg, mr = [], [], [], []
+    for b in range(B):
+        for c in range(C):
+            for p in _samples(H, W, 1, seed=300 + 10 * b + c)[:2]:
+                y, x = divmod(int(p), W)
+                a, _ = n6.map6(prm[b][:, y, x].reshape(3, 1).astype(np.float64), 2)
+                refs.append(_direct6_on_crop(imgs[b, c], a[:, 0], y, x))
+                gots.append(out[b, c, y, x])
+                if c == 0 and len(mr) < 4:
+                    mg.append(refs[-1])
+                    mr.append(_direct6_on_crop(imgs[b, c], a[:, 0], y, x, definition=True))
+    fig = _figures(np.array(gots), np.array(refs))
+    accuracy_record["b4c3_4096_f32_n6/fp64_hex"] = fig
+    accuracy_record["b4c3_4096_f32_n6/method_error_vs_pixel_comb"] = _figures(np.array(mg), np.array(mr))
+    assert fig["max_norm"] < TOL
