@@ -1,9 +1,9 @@
-"""Why the six-directional spline is not built: the oracle's any-N pieces
-(Fourier transform of Eq. const, the kurtosis criterion of Sec. 3.2.2 for N
-directions) pinned against the four-directional ones, and the comparison the
-paper makes in Sec. 3.3 -- more directions bring the spline closer to the
-Gaussian, but the twice-iterated four-directional spline (built) is closer
-still, at every target tried."""
+"""The oracle's any-N pieces in the Fourier domain (transform of Eq. const,
+the kurtosis criterion of Sec. 3.2.2 for N directions, solved by SLSQP)
+pinned against the four-directional ones, and the comparison the paper makes
+in Sec. 3.3: more directions bring the spline closer to the Gaussian, and the
+twice-iterated four-directional spline is closer still, at every target
+tried."""
 import numpy as np
 import pytest
 
