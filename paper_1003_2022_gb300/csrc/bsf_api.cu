@@ -466,13 +466,13 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     std::vector<chunk> chunks;
     for (size_t t = 0; t < tl.size(); ++t) {
         if (tl[t].ncol > hex6_max_cols()) return BSF_EINVAL;  // footprint too wide for one window
-        const size_t bytes = (size_t)C * tl[t].ncol * tl[t].nrow * sizeof(double);
+        const size_t bytes = (size_t)C * tl[t].ncol * tl[t].nrow * 16;
         if (bytes > budget) return BSF_EINVAL;
         if (chunks.empty() || tl[t].size != tl[chunks.back().first].size || chunks.back().bytes + bytes > budget ||
             t - chunks.back().first >= 65535)
             chunks.push_back({t, t, 0, 0});
         chunk& ch = chunks.back();
-        tl[t].off = (long long)(ch.bytes / sizeof(double));
+        tl[t].off = (long long)(ch.bytes / 16);
         ch.bytes += bytes;
         ch.last = t + 1;
         ch.cols = std::max(ch.cols, tl[t].ncol);
@@ -488,10 +488,10 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
         const chunk& ch = chunks[i];
         const int n = (int)(ch.last - ch.first);
         BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
-                                   (double*)c->h6_win, st));
+                                   c->h6_win, st));
         BSF_TRY(prof_mark(c, 1, st));
         BSF_TRY(launch_hex6_stencil((const double*)c->h6_scales, (int)C, (int)H, (int)W, tl[ch.first].size, h,
-                                    dt + ch.first, n, (const double*)c->h6_win, out, c->d_status, st));
+                                    dt + ch.first, n, c->h6_win, out, c->d_status, st));
         BSF_TRY(prof_mark(c, 2, st));
         if (i + 1 < chunks.size()) BSF_TRY(prof_mark(c, 0, st));
     }

@@ -69,9 +69,9 @@ cudaError_t launch_adaptive_cov(const float* J, long long HW, int B, float s0sq,
 // Six-directional filter on the hexagonal lattice (hex6.cu).
 // One lattice window per (batch entry, output tile of 64 x 64 or, where the
 // footprints are small, 16 x 16 pixels); channel c of the tile's image has its
-// window at off + c * ncol * nrow doubles.
+// window at off + c * ncol * nrow elements (exact 128-bit running sums).
 struct hex6_tile {
-    long long off;   // doubles from the chunk's window base
+    long long off;   // 16-byte elements from the chunk's window base
     int i_left;      // lattice column i of storage column 0 in row 0
     int j0w;         // lattice row j of storage row 0
     int ncol, nrow;  // storage size; column c of row r is lattice point (c + i_left - 2 r, j0w + r)
@@ -86,6 +86,6 @@ cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int 
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, float* scales,
                             uint8_t* flags, cudaStream_t st);
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, double* scratch, cudaStream_t st);
+                               int ntiles, int ncol_max, void* scratch, cudaStream_t st);
 cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile, double h, const hex6_tile* tiles,
-                                int ntiles, const double* scratch, float* out, unsigned* status, cudaStream_t st);
+                                int ntiles, const void* scratch, float* out, unsigned* status, cudaStream_t st);

@@ -499,8 +499,8 @@ constexpr int MU_FRAC_BITS = 24;  // fixed point of the transferred masses
 // row.  The sums are exact: the masses are rounded once to fixed point with
 // 24 fractional bits (a change of the measure of at most 2^-25 per lattice
 // point) and summed in 128-bit integers (the largest windows need about 2^83),
-// so the only rounding of the pre-integrated values is the final conversion
-// to FP64, which stores them times 2^24.  The state of each sum (its last
+// and the windows hold them exactly, times 2^24, as 128-bit integers.  The
+// state of each sum (its last
 // row, two for the 90-degree sum) is kept per column: in shared memory for
 // the four sums whose rows shift by one to three columns (the neighbouring
 // threads read them), in registers for the two that do not shift.
@@ -513,7 +513,7 @@ __device__ __forceinline__ int pidx(int c) { return c + c / PRE_CPT; }
 template <class InT>
 __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restrict__ img, int C, int H, int W,
                                                              double h, const hex6_tile* __restrict__ tiles,
-                                                             double* __restrict__ scratch) {
+                                                             u128* __restrict__ scratch) {
     extern __shared__ u128 smq[];
     const hex6_tile tl = tiles[blockIdx.x];
     const int c = blockIdx.y;
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < 4 * np; k += PRE_THREADS) smq[k] = 0;
     const InT* f = img + ((size_t)tl.b * C + c) * (size_t)H * W;
-    double* G = scratch + tl.off + (long long)c * ncol * nrow;
+    u128* G = scratch + tl.off + (long long)c * ncol * nrow;
     // The transfer weights need only single precision: an error in a mass is a
     // small change of the input measure, which the exact sums carry through
     // without amplification.  With h a power of two the lattice x-coordinates
@@ -637,36 +637,94 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
             s120[pidx(cc)] = y[e];
             y[e] += s150[e];
             s150[e] = y[e];
-            // exact 128-bit value -> FP64 (stored times 2^24)
-            const i128 v128 = (i128)y[e];
-            const long long hi = (long long)(v128 >> 64);
-            const unsigned long long lo = (unsigned long long)v128;
-            G[(long long)r * ncol + cc] = fma((double)hi, 18446744073709551616.0, (double)lo);
+            G[(long long)r * ncol + cc] = y[e];  // exact, times 2^24
         }
     }
 }
 
 constexpr int ST_THREADS = 128;  // 32 x 4 pixels for 64-pixel tiles, 16 x 8 for 16-pixel tiles
 
+// ---- double-float (a pair of FP32 numbers, about 48 bits) ----
+struct dflt {
+    float hi, lo;
+};
+__device__ __forceinline__ dflt df_norm(float s, float e) {
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+    // two-sum of the high parts, then the low parts
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return df_norm(s, e);
+}
+// the nearest FP32 value of a 128-bit integer, and that value as an integer
+__device__ __forceinline__ float f_of_i128(i128 v, i128* rounded) {
+    const i128 mag = v ^ (v >> 127);  // |v| (one less for negative v): enough for the bit length
+    const unsigned long long mh = (unsigned long long)(mag >> 64), ml = (unsigned long long)mag;
+    const int n = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
+    const int sh = n > 62 ? n - 62 : 0;
+    const float f = __ll2float_rn((long long)(v >> sh));
+    *rounded = (i128)__float2ll_rn(f) << sh;
+    return f * __int_as_float((127 + sh) << 23);  // times 2^sh, exact
+}
+// a 128-bit integer as a double-float (to about 48 bits): its nearest FP32
+// value, then the exact remainder's
+__device__ __forceinline__ dflt df_of_i128(i128 v) {
+    i128 r, r2;
+    const float hi = f_of_i128(v, &r);
+    const float lo = f_of_i128(v - r, &r2);
+    return df_norm(hi, lo);
+}
+// the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact)
+__device__ __forceinline__ dflt df_of_frac48(long long x) {
+    return {(float)(x >> 24) * 5.9604644775390625e-8f, (float)(x & 0xFFFFFF) * 3.552713678800501e-15f};
+}
+
 // step 3: the 64 taps of Eq. FD_mesh, each read from its window by the exact
-// piecewise-quartic element (24 lattice points), in FP64
+// piecewise-quartic element (24 lattice points).  Exact where it matters:
+//   - tap positions in 48-bit fixed point relative to the pixel's lattice cell
+//     (each direction's step a_k u_k rounded once, so the 64 taps form an
+//     exact affine mesh for scales perturbed by 2^-48 lattice units);
+//   - the quartic of a tap's piece, F = sum_ab A_ab sigma^a tau^b / 432, has
+//     integer coefficients A_ab = sum_k c_abk g[m_k] (c from hex6_tables.h),
+//     computed exactly from the exact window sums in 31-bit limbs;
+//   - the constant terms A_00, which carry the size of the sums, are added over
+//     the 64 taps exactly, in 128-bit integers;
+// and only the remaining terms (derivatives of the sums, smaller by the
+// window size) are evaluated in double-float arithmetic.  No FP64 in the loop.
 __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
                                                               double h, const hex6_tile* __restrict__ tiles,
-                                                              const double* __restrict__ scratch,
+                                                              const u128* __restrict__ scratch,
                                                               float* __restrict__ out, unsigned* __restrict__ status) {
-    __shared__ double coef[HEX6_NREGION][HEX6_NSLOT][HEX6_NMONO];
-    __shared__ int soff[HEX6_NREGION][HEX6_NSLOT][2];
+    // coefficients: 16 shorts per (piece, slot); pieces 24 * 32 + 16 bytes apart (bank spread)
+    __shared__ __align__(16) short coef[HEX6_NREGION][HEX6_NSLOT * 16 + 8];
+    __shared__ int soff[HEX6_NREGION][HEX6_NSLOT];
     __shared__ int lut[16];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
-    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT * HEX6_NMONO; k += ST_THREADS)
-        (&coef[0][0][0])[k] = (&HEX6_COEF[0][0][0])[k];
-    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT; k += ST_THREADS) {
-        soff[k / HEX6_NSLOT][k % HEX6_NSLOT][0] = HEX6_DI[k / HEX6_NSLOT][k % HEX6_NSLOT];
-        soff[k / HEX6_NSLOT][k % HEX6_NSLOT][1] = HEX6_DJ[k / HEX6_NSLOT][k % HEX6_NSLOT];
+    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT * 16; k += ST_THREADS) {
+        const int r = k / (HEX6_NSLOT * 16), rest = k % (HEX6_NSLOT * 16);
+        coef[r][rest] = (&HEX6_ICOEF[0][0][0])[k];
     }
     __syncthreads();
     const hex6_tile tl = tiles[blockIdx.y];
+    const int ncol = tl.ncol;
+    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT; k += ST_THREADS) {
+        const int r = k / HEX6_NSLOT, sl = k % HEX6_NSLOT;
+        // linear offset of the slot's lattice point from the tap's cell corner
+        soff[r][sl] = -(int)HEX6_DJ[r][sl] * (ncol + 2) - (int)HEX6_DI[r][sl];
+    }
+    __syncthreads();
     const int c = blockIdx.z;
     const int tile = tl.size;
     const int per_row = tile / (int)blockDim.x;
@@ -687,85 +745,119 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
         *o = __int_as_float(0x7fc00000);
         return;
     }
-    const double* G = scratch + tl.off + (long long)c * tl.ncol * tl.nrow;
+    const u128* G = scratch + tl.off + (long long)c * ncol * tl.nrow;
     const double SQ3 = 1.73205080756887729353;
-    // tau = (1/2) sum (a_k - b_k) u_k, b = h (1, sqrt3, 1, sqrt3, 1, sqrt3); taps at
-    // n + tau - sum_k q_k a_k u_k, each computed from the pixel (no running sum of
-    // positions, so no rounding accumulates along the 64 taps)
-    double tx0 = 0.0, ty0 = 0.0, ax[6], ay[6];
+    const double it2 = 2.0 / (h * SQ3), ih = 1.0 / h;
+    const double SC = 281474976710656.0;  // 2^48
+    // the first tap, n + tau, tau = (1/2) sum (a_k - b_k) u_k, b = h (1, sqrt3, 1, sqrt3, 1, sqrt3),
+    // in lattice coordinates s = x/h - t/2, t = 2y/(h sqrt3): cell (ib, jb) and a 48-bit fraction
+    double yx = (double)x, yy = (double)y;
+    long long ds[6], dtt[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const double bk = (k & 1) ? h * SQ3 : h;
-        tx0 += 0.5 * (a[k] - bk) * cos_k(k);
-        ty0 += 0.5 * (a[k] - bk) * sin_k(k);
-        ax[k] = a[k] * cos_k(k);
-        ay[k] = a[k] * sin_k(k);
+        yx += 0.5 * (a[k] - bk) * cos_k(k);
+        yy += 0.5 * (a[k] - bk) * sin_k(k);
+        // the step -a_k u_k in lattice coordinates, rounded once to 48 fractional bits
+        ds[k] = __double2ll_rn(-a[k] * (cos_k(k) * ih - 0.5 * it2 * sin_k(k)) * SC);
+        dtt[k] = __double2ll_rn(-a[k] * sin_k(k) * it2 * SC);
     }
-    const double it2 = 2.0 / (h * SQ3), ih = 1.0 / h;
-    const int ncol = tl.ncol;
-    double acc = 0.0;
+    const double t0 = yy * it2, s0 = yx * ih - 0.5 * t0;
+    const double fib = floor(s0), fjb = floor(t0);
+    const int ib = (int)fib, jb = (int)fjb;
+    const long long bs = __double2ll_rn((s0 - fib) * SC), bt = __double2ll_rn((t0 - fjb) * SC);
+    const long long M48 = (1LL << 48) - 1, ONE = 1LL << 48;
+    i128 e00 = 0;          // exact sum over the taps of +-A_00
+    dflt rest = {0.f, 0.f};  // the other terms
 #pragma unroll 1
     for (int q = 0; q < 64; ++q) {
-        double dx = tx0, dy = ty0;
+        long long sf = bs, tf = bt;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             if ((q >> k) & 1) {
-                dx -= ax[k];
-                dy -= ay[k];
+                sf += ds[k];
+                tf += dtt[k];
             }
-        const double yx = (double)x + dx, yy = (double)y + dy;
-        // lattice coordinates of the tap
-        const double t = yy * it2;
-        const double s = yx * ih - 0.5 * t;
-        const double fi = floor(s), fj = floor(t);
-        const double sg = s - fi, tg = t - fj;
+        const int i0 = ib + (int)(sf >> 48), j0 = jb + (int)(tf >> 48);
+        sf &= M48;
+        tf &= M48;
         int code;
-        if (sg + tg < 1.0)
-            code = (sg > tg) | ((2.0 * sg + tg > 1.0) << 1) | ((sg + 2.0 * tg > 1.0) << 2);
+        if (sf + tf < ONE)
+            code = (sf > tf) | ((2 * sf + tf > ONE) << 1) | ((sf + 2 * tf > ONE) << 2);
         else
-            code = 8 | (sg > tg) | ((2.0 * sg + tg > 2.0) << 1) | ((sg + 2.0 * tg > 2.0) << 2);
+            code = 8 | (sf > tf) | ((2 * sf + tf > 2 * ONE) << 1) | ((sf + 2 * tf > 2 * ONE) << 2);
         const int reg = lut[code];
-        const int rr = (int)fj - tl.j0w;
-        const int cc = (int)fi - tl.i_left + 2 * rr;
+        const int rr = j0 - tl.j0w;
+        const int cc = i0 - tl.i_left + 2 * rr;
         if (rr < 2 || rr + 3 >= tl.nrow || cc < 6 || cc + 9 >= ncol) {
             raise_status(status, BSF_EHALO);
             *o = __int_as_float(0x7fc00000);
             return;
         }
-        double m[HEX6_NMONO];
-        const double s2 = sg * sg, t2 = tg * tg, st = sg * tg;
-        m[0] = 1.0;
+        const bool neg = __popc(q) & 1;
+        // monomials sigma^a tau^b (a + b = 1..4) as double-floats
+        const dflt sg = df_of_frac48(sf), tg = df_of_frac48(tf);
+        dflt m[HEX6_NMONO];
         m[1] = sg;
         m[2] = tg;
-        m[3] = s2;
-        m[4] = st;
-        m[5] = t2;
-        m[6] = s2 * sg;
-        m[7] = s2 * tg;
-        m[8] = sg * t2;
-        m[9] = t2 * tg;
-        m[10] = s2 * s2;
-        m[11] = s2 * st;
-        m[12] = s2 * t2;
-        m[13] = st * t2;
-        m[14] = t2 * t2;
-        const double* base = G + (long long)rr * ncol + cc;
-        double F = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < HEX6_NSLOT; ++k) {
-            const double* cf = coef[reg][k];
-            double w = 0.0;
+        m[3] = df_mul(sg, sg);
+        m[4] = df_mul(sg, tg);
+        m[5] = df_mul(tg, tg);
+        m[6] = df_mul(m[3], sg);
+        m[7] = df_mul(m[3], tg);
+        m[8] = df_mul(sg, m[5]);
+        m[9] = df_mul(m[5], tg);
+        m[10] = df_mul(m[3], m[3]);
+        m[11] = df_mul(m[3], m[4]);
+        m[12] = df_mul(m[3], m[5]);
+        m[13] = df_mul(m[4], m[5]);
+        m[14] = df_mul(m[5], m[5]);
+        const u128* base = G + (long long)rr * ncol + cc;
+        // two groups of coefficients (monomials 0-7, 8-14): A = sum_k c_k g[m_k] in
+        // 31-bit limbs of g, int64 partial sums per limb
 #pragma unroll
-            for (int l = 0; l < HEX6_NMONO; ++l) w = fma(cf[l], m[l], w);
-            const int di = soff[reg][k][0], dj = soff[reg][k][1];
-            F = fma(__ldg(base - (long long)dj * (ncol + 2) - di), w, F);
+        for (int grp = 0; grp < 2; ++grp) {
+            long long P0[8], P1[8], P2[8];
+#pragma unroll
+            for (int l = 0; l < 8; ++l) P0[l] = P1[l] = P2[l] = 0;
+#pragma unroll 2
+            for (int k = 0; k < HEX6_NSLOT; ++k) {
+                const ulonglong2 gv = __ldg(reinterpret_cast<const ulonglong2*>(base + soff[reg][k]));
+                const i128 g = (i128)(((u128)gv.y << 64) | (u128)gv.x);
+                const int x0 = (int)((unsigned)(unsigned long long)g & 0x7FFFFFFFu);
+                const int x1 = (int)((unsigned)(unsigned long long)(g >> 31) & 0x7FFFFFFFu);
+                const int x2 = (int)(long long)(g >> 62);
+                const int4 cw = *reinterpret_cast<const int4*>(&coef[reg][k * 16 + grp * 8]);
+                const int cws[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    const int cl = (int)(short)((l & 1) ? (cws[l >> 1] >> 16) : (cws[l >> 1] & 0xFFFF));
+                    P0[l] += (long long)cl * x0;
+                    P1[l] += (long long)cl * x1;
+                    P2[l] += (long long)cl * x2;
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const int mono = grp * 8 + l;
+                if (mono >= HEX6_NMONO) continue;
+                const i128 A = ((i128)P2[l] << 62) + ((i128)P1[l] << 31) + (i128)P0[l];
+                if (mono == 0) {
+                    e00 += neg ? -A : A;
+                } else {
+                    dflt ad = df_of_i128(A);
+                    if (neg) ad = {-ad.hi, -ad.lo};
+                    rest = df_add(rest, df_mul(ad, m[mono]));
+                }
+            }
         }
-        acc += (__popc(q) & 1) ? -F : F;
     }
-    // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.); the
-    // window holds the running sums times 2^24
+    // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.) / 432 with
+    // the window holding the running sums times 2^24
+    const long long ehi = (long long)(e00 >> 64);
+    const double ev = fma((double)ehi, 18446744073709551616.0, (double)(unsigned long long)e00);
     const double h2 = h * h;
-    *o = (float)(acc * (6.0 * h2 * h2 / 16777216.0) / prod);
+    *o = (float)((ev + (double)rest.hi + (double)rest.lo) * (6.0 * h2 * h2 / (16777216.0 * HEX6_DEN)) / prod);
 }
 
 }  // namespace
@@ -824,24 +916,24 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 }
 
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, double* scratch, cudaStream_t st) {
+                               int ntiles, int ncol_max, void* scratch, cudaStream_t st) {
     const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
     dim3 grid(ntiles, C);
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, scratch);
+        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch);
     } else {
         cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, scratch);
+        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile, double h, const hex6_tile* tiles,
-                                int ntiles, const double* scratch, float* out, unsigned* status, cudaStream_t st) {
+                                int ntiles, const void* scratch, float* out, unsigned* status, cudaStream_t st) {
     if (tile != 16 && tile != 64) return cudaErrorInvalidValue;
     const dim3 blk = tile == 64 ? dim3(32, 4) : dim3(16, 8);
     dim3 grid((tile / blk.x) * (tile / blk.y), ntiles, C);
-    k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, scratch, out, status);
+    k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, (const u128*)scratch, out, status);
     return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ import itertools
 import os
 import sys
 from fractions import Fraction as Fr
+from math import gcd
 
 XI = ((1, 0), (1, 1), (0, 1), (-1, 2), (-1, 1), (-2, 1))
 DEG = 4
@@ -235,7 +236,7 @@ def emit(path):
              "// Pieces of the six-directional interpolation element on the hexagonal",
              "// lattice: weight of lattice point (floor(s) - di, floor(t) - dj) at the",
              "// fractional position (sigma, tau) of a point in piece r is",
-             "// sum_k HEX6_COEF[r][slot][k] * sigma^a_k tau^b_k (monomial order below).",
+             "// sum_k HEX6_ICOEF[r][slot][k] * sigma^a_k tau^b_k / HEX6_DEN (monomial order below).",
              "#pragma once", "",
              f"#define HEX6_NREGION 12", f"#define HEX6_NSLOT {nslot}", f"#define HEX6_NMONO {len(MONOS)}", "",
              "// monomial exponents (a, b) of sigma^a tau^b",
@@ -256,13 +257,27 @@ def emit(path):
     for slots in tables:
         lines.append("    {" + ", ".join(str(s[1]) for s in slots) + ", 0" * (nslot - len(slots)) + "},")
     lines.append("};")
-    lines.append("static __device__ const double HEX6_COEF[HEX6_NREGION][HEX6_NSLOT][HEX6_NMONO] = {")
+    # integer coefficients: every coefficient times the common denominator
+    den = 1
+    for slots in tables:
+        for _, _, p in slots:
+            for v in p.values():
+                den = den * v.denominator // gcd(den, v.denominator)
+    lines.append("")
+    lines.append("// the weight polynomials times HEX6_DEN are integer polynomials; their")
+    lines.append("// coefficients, per piece and slot, monomials padded to 16 (the 16th is 0)")
+    lines.append(f"#define HEX6_DEN {den}")
+    lines.append("static __device__ const short HEX6_ICOEF[HEX6_NREGION][HEX6_NSLOT][16] = {")
     for slots in tables:
         lines.append("  {")
         for k in range(nslot):
             p = slots[k][2] if k < len(slots) else {}
-            vals = [p.get(m, Fr(0)) for m in MONOS]
-            lines.append("    {" + ", ".join(repr(float(v)) for v in vals) + "},")
+            vals = []
+            for m in MONOS:
+                v = p.get(m, Fr(0)) * den
+                assert v.denominator == 1 and abs(v.numerator) < (1 << 15)
+                vals.append(str(v.numerator))
+            lines.append("    {" + ", ".join(vals) + ", 0},")
         lines.append("  },")
     lines.append("};")
     text = "\n".join(lines) + "\n"
