@@ -48,9 +48,8 @@ STENCIL_INT_OPS_PER_PX = 16 * 124
 # product (88), two words per product sum and accumulator (28), 32 for
 # position, truncation, bounds and addresses: 260 per tap
 STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
-# six directions: 64 taps x 24 lattice points x (15 weight FMAs + 1 accumulation FMA) x 2 flops
-HEX6_FLOPS_PER_PX = 64 * 24 * 16 * 2
-FP64_PEAK_TFLOPS = 1.25
+# six directions: 64 taps x 24 lattice points x 15 coefficients x 3 limb multiply-adds
+HEX6_IMAD_PER_PX = 64 * 24 * 15 * 3
 # Benchmarked workloads: (params kind, largest sigma or scale, forward+backward).
 BENCH_WORKLOADS = {
     "u2048_u8_n4": ("srt", 32.0, False),
@@ -430,18 +429,21 @@ def run_ours(args):
         chunks = -(-B // max(1, min(B, (16 << 30) // per)))
         launches += 13 * chunks * args.steps
     if N == 6:
-        # six directions: FP64-bound stencil (64 taps x 24 lattice points, 15 weight FMAs
-        # and one accumulation FMA per point) against the nominal FP64 rate
-        fl_px = HEX6_FLOPS_PER_PX
-        achieved6 = fl_px * px_per_launch / (st_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved6, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved6 / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_hex6_stencil",
+        # six directions: the stencil's exact integer part is 64 taps x 24 lattice points x 15
+        # coefficients, each a 31-bit-limb product (3 int32 x int32 -> int64 multiply-adds),
+        # against the int32 multiply-add rate (152 SMs x 64 per clock x 2070 MHz)
+        ops_px6 = HEX6_IMAD_PER_PX
+        achieved6 = ops_px6 * px_per_launch / (st_ms / 1e3) / 1e12
+        peak6 = 152 * 64 * 2.070e9 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved6, "peak": peak6, "unit": "Tops/s",
+                    "frac": achieved6 / peak6, "traffic": None, "kernel": "k_hex6_stencil",
                     "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
-                    "peak_note": "FP64 pipe: 1.25 TFLOP/s nominal dense FP64 of the GB300 (no FP64 figure is "
-                                 "measured on this pool); the stencil's FP64 flops per pixel are algorithmic",
-                    "fp64_flops_per_px": fl_px,
+                    "peak_note": "int32 multiply-add rate, 152 SMs x 64 per clock x 2070 MHz (derived; a "
+                                 "multiply-add chain probe reached 19.1 Tops/s); algorithmic limb multiply-adds "
+                                 "of the exact coefficient sums, 64 taps x 24 points x 15 coefficients x 3 limbs",
+                    "int_madds_per_px": ops_px6,
                     "launches_per_step": n_st / args.steps,
-                    "preintegrate_note": "scale map + window transfer and six running sums (FP64), per chunk"}
+                    "preintegrate_note": "scale map + window transfer and six exact running sums, per chunk"}
         launches = args.steps + 2 * nl
     line = {
         "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": ws, "steps": args.steps,
