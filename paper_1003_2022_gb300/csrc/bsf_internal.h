@@ -67,8 +67,9 @@ cudaError_t launch_adaptive_cov(const float* J, long long HW, int B, float s0sq,
                                 cudaStream_t st);
 
 // Six-directional filter on the hexagonal lattice (hex6.cu).
-// One lattice window per (batch entry, output tile of 64 x 64 or, where the
-// footprints are small, 16 x 16 pixels); channel c of the tile's image has its
+// One lattice window per (batch entry, output tile of 64 x 64 pixels; 16 x 16
+// where the footprints are small, 256 x 64 where four neighbouring 64-tiles all
+// have large footprints); channel c of the tile's image has its
 // window at off + c * ncol * nrow elements (exact 128-bit running sums).
 struct hex6_tile {
     long long off;   // 16-byte elements from the chunk's window base
@@ -76,10 +77,10 @@ struct hex6_tile {
     int j0w;         // lattice row j of storage row 0
     int ncol, nrow;  // storage size; column c of row r is lattice point (c + i_left - 2 r, j0w + r)
     int b;           // batch entry
-    int tx, ty;      // tile position (units of the tile size)
-    int size;        // tile size in pixels (16 or 64)
+    int x0, y0;      // first output pixel of the tile
+    int w, hh;       // tile shape in pixels: 16 x 16, 64 x 64 or 256 x 64
 };
-void hex6_window(int tx, int ty, int tile, int H, int W, double ex, double ey, double h, hex6_tile* t);
+void hex6_window(int x0, int y0, int w, int hh, int H, int W, double ex, double ey, double h, hex6_tile* t);
 int hex6_max_cols();
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st);
@@ -87,5 +88,6 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
                             uint8_t* flags, cudaStream_t st);
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
                                int ntiles, int ncol_max, void* scratch, cudaStream_t st);
-cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile, double h, const hex6_tile* tiles,
-                                int ntiles, const void* scratch, float* out, unsigned* status, cudaStream_t st);
+cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile_w, int tile_h, double h,
+                                const hex6_tile* tiles, int ntiles, const void* scratch, float* out, unsigned* status,
+                                cudaStream_t st);

@@ -726,12 +726,11 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
     }
     __syncthreads();
     const int c = blockIdx.z;
-    const int tile = tl.size;
-    const int per_row = tile / (int)blockDim.x;
+    const int per_row = tl.w / (int)blockDim.x;
     const int bx = blockIdx.x % per_row, by = blockIdx.x / per_row;
-    const int x = tl.tx * tile + bx * (int)blockDim.x + threadIdx.x;
-    const int y = tl.ty * tile + by * (int)blockDim.y + threadIdx.y;
-    if (x >= W || y >= H || x >= (tl.tx + 1) * tile || y >= (tl.ty + 1) * tile) return;
+    const int x = tl.x0 + bx * (int)blockDim.x + threadIdx.x;
+    const int y = tl.y0 + by * (int)blockDim.y + threadIdx.y;
+    if (x >= W || y >= H || x >= tl.x0 + tl.w || y >= tl.y0 + tl.hh) return;
     const long long HW = (long long)H * W, p = (long long)y * W + x;
     float* o = out + ((size_t)tl.b * C + c) * HW + p;
     double a[6], prod = 1.0;
@@ -864,10 +863,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
 
 // geometry of the window of one tile: every lattice point that the taps of
 // its pixels read (host side; ex, ey = the tile's largest footprint half-extents)
-void hex6_window(int tx, int ty, int tile, int H, int W, double ex, double ey, double h, hex6_tile* t) {
+void hex6_window(int tx0, int ty0, int tw, int th_, int H, int W, double ex, double ey, double h, hex6_tile* t) {
     const double SQ3 = 1.7320508075688772935;
-    const int x0 = tx * tile, x1 = std::min(W, (tx + 1) * tile) - 1;
-    const int y0 = ty * tile, y1 = std::min(H, (ty + 1) * tile) - 1;
+    const int x0 = tx0, x1 = std::min(W, tx0 + tw) - 1;
+    const int y0 = ty0, y1 = std::min(H, ty0 + th_) - 1;
     // taps: n + tau - x_q, in n + [-ex, ex] x [-ey, ey] - (h/2, 3 sqrt3 h / 2)
     const double xl = x0 - ex - 0.5 * h, xh = x1 + ex - 0.5 * h;
     const double yl = y0 - ey - 1.5 * SQ3 * h, yh = y1 + ey - 1.5 * SQ3 * h;
@@ -890,9 +889,10 @@ void hex6_window(int tx, int ty, int tile, int H, int W, double ex, double ey, d
     }
     t->i_left = (int)ileft;
     t->ncol = (int)ncol;
-    t->tx = tx;
-    t->ty = ty;
-    t->size = tile;
+    t->x0 = tx0;
+    t->y0 = ty0;
+    t->w = tw;
+    t->hh = th_;
 }
 
 // widest window: PRE_CPT columns per thread, and four 128-bit state rows plus the
@@ -929,11 +929,15 @@ cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile, double h, const hex6_tile* tiles,
-                                int ntiles, const void* scratch, float* out, unsigned* status, cudaStream_t st) {
-    if (tile != 16 && tile != 64) return cudaErrorInvalidValue;
-    const dim3 blk = tile == 64 ? dim3(32, 4) : dim3(16, 8);
-    dim3 grid((tile / blk.x) * (tile / blk.y), ntiles, C);
+cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile_w, int tile_h, double h,
+                                const hex6_tile* tiles, int ntiles, const void* scratch, float* out, unsigned* status,
+                                cudaStream_t st) {
+    // 16 x 16 tiles, or 64-pixel tiles and their groups (64 x 64 up to 256 x 128)
+    const bool fine = tile_w == 16 && tile_h == 16;
+    const bool coarse = (tile_w == 64 || tile_w == 128 || tile_w == 256) && (tile_h == 64 || tile_h == 128);
+    if (!fine && !coarse) return cudaErrorInvalidValue;
+    const dim3 blk = tile_w == 16 ? dim3(16, 8) : dim3(32, 4);
+    dim3 grid((tile_w / blk.x) * (tile_h / blk.y), ntiles, C);
     k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, (const u128*)scratch, out, status);
     return cudaGetLastError();
 }

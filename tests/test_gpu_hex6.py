@@ -176,8 +176,8 @@ def test_widths_at_the_relative_bound(lo, hi):
 
 def test_large_footprints_on_crops():
     """sigma up to 48 px (the batch workload's largest kernels): windows of
-    more than 2000 lattice columns.  The oracle evaluates sampled pixels on
-    crops that hold their footprints."""
+    more than 2000 lattice columns, shared by groups of 64-pixel tiles.  The
+    oracle evaluates sampled pixels on crops that hold their footprints."""
     H, W = 448, 448
     f = synth.image(H, W, seed=12, dtype="f32")
     p = synth.srt_field(H, W, seed=13, sigma=(30.0, 48.0), rho=(1.0, 6.0))
@@ -185,14 +185,36 @@ def test_large_footprints_on_crops():
     assert st == 0
     for y, x in [(224, 224), (60, 400), (447, 0)]:
         a, _ = n6.map6(p[:, y, x].reshape(3, 1).astype(np.float64), 2)
-        ex, ey = n6.support_extent(n6.directions(6), a[:, 0])
-        x0, x1 = max(0, int(x - ex) - 2), min(W, int(x + ex) + 3)
-        y0, y1 = max(0, int(y - ey) - 2), min(H, int(y + ey) + 3)
-        A = np.zeros((6, y1 - y0, x1 - x0))
-        A[:, y - y0, x - x0] = a[:, 0]
-        ref = n6.direct6_hex(f[y0:y1, x0:x1].astype(np.float64), A, np.array([(y - y0) * (x1 - x0) + (x - x0)]),
-                             0.5, origin=(x0, y0))
-        assert abs(got[y, x] - ref[0]) < TOL * abs(ref[0])
+        ref = _ref_on_crop(f, a[:, 0], y, x)
+        assert abs(got[y, x] - ref) < TOL * abs(ref)
+
+
+def _ref_on_crop(f, a, y, x, h=0.5):
+    """The oracle at pixel (y, x) with widths a, on a crop of f that holds the footprint."""
+    H, W = f.shape
+    ex, ey = n6.support_extent(n6.directions(6), a)
+    x0, x1 = max(0, int(x - ex) - 2), min(W, int(x + ex) + 3)
+    y0, y1 = max(0, int(y - ey) - 2), min(H, int(y + ey) + 3)
+    A = np.zeros((6, y1 - y0, x1 - x0))
+    A[:, y - y0, x - x0] = a
+    return n6.direct6_hex(f[y0:y1, x0:x1].astype(np.float64), A, np.array([(y - y0) * (x1 - x0) + (x - x0)]), h,
+                          origin=(x0, y0))[0]
+
+
+def test_grouped_tiles_with_widths_at_the_bound():
+    """Footprint half-extents of 33-50 px over 4 x 4 tiles of 64 px: the tiles
+    share windows of 256 x 128 pixels.  Two widths at the relative bound (the
+    worst conditioning of the configs' kernels) on pixels on both sides of
+    tile and group borders."""
+    H, W = 256, 256
+    f = synth.image(H, W, seed=18, dtype="f32")
+    a = synth.scale_field(H, W, seed=19, lo=20.0, hi=30.0)[0]
+    a6 = np.stack([a, a * 1.1, a * 0.9, a * 0.077, a * 0.077, a * 1.05]).astype(np.float32)
+    got, st = _run(f, a6, "scales")
+    assert st == 0
+    for y, x in [(0, 0), (63, 64), (127, 128), (128, 127), (200, 255), (255, 17)]:
+        ref = _ref_on_crop(f, a6[:, y, x].astype(np.float64), y, x)
+        assert abs(got[y, x] - ref) < TOL * abs(ref), (y, x)
 
 
 def test_host_pipeline_and_unsupported_entry_points():
