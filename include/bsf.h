@@ -55,7 +55,9 @@
  * barycentric coordinates (mass and centre of mass of every pixel kept).  All
  * six directions are lattice vectors of Lambda_h, so Algorithm 1 is exact
  * there: the filter computed is (1) with the pixel comb replaced by that
- * measure, fbar[n] = sum_{m in Lambda_h} mu[m] beta^6_{a(n)}(n - m), in FP64
+ * measure, fbar[n] = sum_{m in Lambda_h} mu[m] beta^6_{a(n)}(n - m): masses in
+ * fixed point (24 fractional bits), running sums and the stencil's coefficient
+ * sums exact in integers, the stencil's remaining terms in double-float
  * (opts.precision is ignored).  Its difference from (1) itself -- the method
  * error of the transfer -- falls like h^2 (about 4e-4 relative for a 2 px
  * kernel at h = 0.5 on a smooth image).  The scale map for six directions is
@@ -84,7 +86,7 @@ typedef int bsf_status;
 #define BSF_EHALO 5           /* device: a tap fell outside the pre-integrated buffer */
 #define BSF_EINFEASIBLE 6     /* strict mode: a covariance needed the elongation clamp */
 #define BSF_EBADSCALE 7       /* device: a scale or covariance was not finite/positive */
-#define BSF_ERANGE 8          /* device: a kernel too large for the exact integer form */
+#define BSF_ERANGE 8          /* device: a kernel (N=4) or image values (N=6) too large for the exact integer form */
 #define BSF_ENOSCRATCH 9      /* bsf_filter_noalloc: the image needs more than its fixed scratch */
 
 /* image element types */
@@ -145,13 +147,17 @@ bsf_status bsf_destroy(bsf_ctx* ctx);
  * pre-integration (Algorithm 1 step 2) and the finite difference with ZP
  * interpolation (Algorithm 1 step 3).  opts may be NULL (defaults).
  * N = 6 (see the top of this file): each 64 x 64 tile of output pixels (16 x
- * 16 where the footprints are small) gets its own window of the hexagonal
- * lattice, sized from the tile's largest footprint; the call synchronises the
- * stream once (after the scale map) to plan the windows.  The FP64 form is
- * accurate to 1e-5 for kernels whose widths are about half a pixel or more
- * (the six-directional map keeps every width at least 0.077 times the
- * typical one); footprints wider than about 1000 px along x (hex_spacing 0.5)
- * return BSF_EINVAL. */
+ * 16 where the footprints are small, groups of up to 4 x 2 tiles where they
+ * are large) gets its own window of the hexagonal lattice, sized from the
+ * tile's largest footprint; the call synchronises the stream once (after the
+ * scale map) to plan the windows.  The result is accurate to 1e-5 for kernels
+ * whose widths are about half a pixel or more (the six-directional map keeps
+ * every width at least 0.077 times the typical one); footprints wider than
+ * about 1000 px along x (hex_spacing 0.5) return BSF_EINVAL.  Windows whose
+ * running sums leave the exact range (|sum| < 2^95: u8 images, and f32 images
+ * up to about 1e4 in magnitude, stay within it at every footprint the map
+ * produces for sigma <= 48) or hold non-finite image values give NaN and the
+ * device status BSF_ERANGE. */
 bsf_status bsf_filter(bsf_ctx* ctx, const void* image, int dtype, int64_t B, int64_t C, int64_t H,
                       int64_t W, int N, const float* params, int kind, const bsf_opts* opts,
                       float* out, void* stream);

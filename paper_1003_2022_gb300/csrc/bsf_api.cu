@@ -49,6 +49,8 @@ struct bsf_ctx {
     size_t h6_tiles_bytes = 0;
     void* h6_win = nullptr;
     size_t h6_win_bytes = 0;
+    void* h6_flag = nullptr;  // per (tile, channel) of a chunk: window values beyond the exact range
+    size_t h6_flag_bytes = 0;
     bool profiling;
     size_t prof_used;                                // event triples recorded since begin
     std::vector<std::array<cudaEvent_t, 3>> prof;    // pool of event triples
@@ -186,7 +188,7 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->hbuf) cudaFree(c->hbuf);
     if (c->iter) cudaFree(c->iter);
     if (c->stbuf) cudaFree(c->stbuf);
-    for (void* p6 : {c->h6_scales, c->h6_ext, c->h6_tiles, c->h6_win})
+    for (void* p6 : {c->h6_scales, c->h6_ext, c->h6_tiles, c->h6_win, c->h6_flag})
         if (p6) cudaFree(p6);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& h : c->hs) {
@@ -525,16 +527,20 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     if (tl.empty()) return BSF_OK;
     BSF_TRY(grow(&c->h6_tiles, &c->h6_tiles_bytes, tl.size() * sizeof(hex6_tile)));
     BSF_TRY(grow(&c->h6_win, &c->h6_win_bytes, win));
+    size_t most = 0;
+    for (auto& ch : chunks) most = std::max(most, ch.last - ch.first);
+    BSF_TRY(grow(&c->h6_flag, &c->h6_flag_bytes, most * (size_t)C * sizeof(unsigned)));
     BSF_TRY(cudaMemcpyAsync(c->h6_tiles, tl.data(), tl.size() * sizeof(hex6_tile), cudaMemcpyHostToDevice, st));
     const hex6_tile* dt = (const hex6_tile*)c->h6_tiles;
     for (size_t i = 0; i < chunks.size(); ++i) {
         const chunk& ch = chunks[i];
         const int n = (int)(ch.last - ch.first);
         BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
-                                   c->h6_win, st));
+                                   c->h6_win, (unsigned*)c->h6_flag, st));
         BSF_TRY(prof_mark(c, 1, st));
         BSF_TRY(launch_hex6_stencil((const double*)c->h6_scales, (int)C, (int)H, (int)W, tl[ch.first].w,
-                                    tl[ch.first].hh, h, dt + ch.first, n, c->h6_win, out, c->d_status, st));
+                                    tl[ch.first].hh, h, dt + ch.first, n, c->h6_win, (const unsigned*)c->h6_flag, out,
+                                    c->d_status, st));
         BSF_TRY(prof_mark(c, 2, st));
         if (i + 1 < chunks.size()) BSF_TRY(prof_mark(c, 0, st));
     }

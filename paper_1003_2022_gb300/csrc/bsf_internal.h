@@ -87,7 +87,7 @@ cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int 
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, float* scales,
                             uint8_t* flags, cudaStream_t st);
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, void* scratch, cudaStream_t st);
+                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st);
 cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile_w, int tile_h, double h,
-                                const hex6_tile* tiles, int ntiles, const void* scratch, float* out, unsigned* status,
-                                cudaStream_t st);
+                                const hex6_tile* tiles, int ntiles, const void* scratch, const unsigned* wflag,
+                                float* out, unsigned* status, cudaStream_t st);

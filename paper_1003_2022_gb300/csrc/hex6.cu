@@ -510,10 +510,16 @@ constexpr int MU_FRAC_BITS = 24;  // fixed point of the transferred masses
 // a warp is a 32-way bank conflict).
 __device__ __forceinline__ int pidx(int c) { return c + c / PRE_CPT; }
 
+// The stencil reads the window values as three 32-bit limbs of g + 2^95, so
+// every value must lie in [-2^95, 2^95).  The kernel checks that and that no
+// running sum can have wrapped around 128 bits (each partial sum is at most
+// the largest |mass| times the product of the six line lengths in the
+// window), and sets the window's flag otherwise (image values too large for
+// the exact form; the stencil then writes NaN and raises BSF_ERANGE).
 template <class InT>
 __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restrict__ img, int C, int H, int W,
                                                              double h, const hex6_tile* __restrict__ tiles,
-                                                             u128* __restrict__ scratch) {
+                                                             u128* __restrict__ scratch, unsigned* __restrict__ wflag) {
     extern __shared__ u128 smq[];
     const hex6_tile tl = tiles[blockIdx.x];
     const int c = blockIdx.y;
@@ -540,6 +546,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
     u128 s90a[PRE_CPT], s150[PRE_CPT], y[PRE_CPT];
 #pragma unroll
     for (int e = 0; e < PRE_CPT; ++e) s90a[e] = s150[e] = 0;
+    unsigned qbits = 0, big = 0;  // largest |mass| (FP32 bits; NaN above all); OR of |stored value| >> 95
     __syncthreads();
     for (int r = 0; r < nrow; ++r) {
         const int j = tl.j0w + r;
@@ -575,7 +582,8 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
                     }
                 }
             }
-            run += (u128)(i128)__float2ll_rn(mu * qscale);
+            run += (u128)(i128)__float2ll_rn(mu * qscale);  // saturates: at most 2^63 in magnitude
+            qbits = max(qbits, __float_as_uint(fabsf(mu)));
             y[e] = run;
         }
         // block-wide scan of the thread totals (the 0-degree sum along the row)
@@ -638,7 +646,31 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
             y[e] += s150[e];
             s150[e] = y[e];
             G[(long long)r * ncol + cc] = y[e];  // exact, times 2^24
+            const unsigned long long hi = (unsigned long long)(y[e] >> 64);
+            big |= (unsigned)((hi ^ (unsigned long long)((long long)hi >> 63)) >> 31);
         }
+    }
+    // the window's flag: a value outside [-2^95, 2^95), or sums that may have wrapped
+    __syncthreads();
+    const unsigned wbad = __reduce_or_sync(0xffffffffu, big);
+    const unsigned wq = __reduce_max_sync(0xffffffffu, qbits);
+    unsigned* red = reinterpret_cast<unsigned*>(wt);
+    if (lane == 0) {
+        red[warp] = wbad;
+        red[32 + warp] = wq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned bad = 0, qb = 0;
+        for (int k = 0; k < PRE_THREADS / 32; ++k) {
+            bad |= red[k];
+            qb = max(qb, red[32 + k]);
+        }
+        const double n30 = min(nrow - 1, (ncol - 1) / 3) + 1, n60 = min(nrow - 1, (ncol - 1) / 2) + 1;
+        const double n90 = min((nrow - 1) / 2, (ncol - 1) / 3) + 1, n120 = min(nrow - 1, ncol - 1) + 1;
+        const double bound = ((double)__uint_as_float(qb) * (double)qscale + 1.0) * (double)ncol * n30 * n60 * n90 *
+                             n120 * (double)nrow;
+        wflag[blockIdx.x * C + c] = (bad || !(bound < 0x1p126)) ? 1u : 0u;
     }
 }
 
@@ -694,27 +726,33 @@ __device__ __forceinline__ dflt df_of_frac48(long long x) {
 // piecewise-quartic element (24 lattice points).  Exact where it matters:
 //   - tap positions in 48-bit fixed point relative to the pixel's lattice cell
 //     (each direction's step a_k u_k rounded once, so the 64 taps form an
-//     exact affine mesh for scales perturbed by 2^-48 lattice units);
+//     exact affine mesh for scales perturbed by 2^-48 lattice units); the taps
+//     are visited in Gray-code order, one step added or removed per tap;
 //   - the quartic of a tap's piece, F = sum_ab A_ab sigma^a tau^b / 432, has
 //     integer coefficients A_ab = sum_k c_abk g[m_k] (c from hex6_tables.h),
-//     computed exactly from the exact window sums in 31-bit limbs;
+//     computed exactly from the exact window sums in 16-bit limbs with 32-bit
+//     multiply-adds, all 15 in one pass over the 24 points;
 //   - the constant terms A_00, which carry the size of the sums, are added over
 //     the 64 taps exactly, in 128-bit integers;
 // and only the remaining terms (derivatives of the sums, smaller by the
-// window size) are evaluated in double-float arithmetic.  No FP64 in the loop.
-__global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
+// window size) are evaluated in double-float arithmetic, summed as a tree.
+// No FP64 in the loop.
+__global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
                                                               double h, const hex6_tile* __restrict__ tiles,
                                                               const u128* __restrict__ scratch,
+                                                              const unsigned* __restrict__ wflag,
                                                               float* __restrict__ out, unsigned* __restrict__ status) {
-    // coefficients: 16 shorts per (piece, slot); pieces 24 * 32 + 16 bytes apart (bank spread)
-    __shared__ __align__(16) short coef[HEX6_NREGION][HEX6_NSLOT * 16 + 8];
+    // coefficients minus HEX6_CMIN (all non-negative): 16 per (piece, slot);
+    // pieces 24 * 64 + 16 bytes apart (bank spread)
+    __shared__ __align__(16) unsigned coef[HEX6_NREGION][HEX6_NSLOT * 16 + 4];
     __shared__ int soff[HEX6_NREGION][HEX6_NSLOT];
     __shared__ int lut[16];
+    __shared__ long long stp[2][6][ST_THREADS];  // per thread: the six steps of the tap mesh
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
     for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT * 16; k += ST_THREADS) {
         const int r = k / (HEX6_NSLOT * 16), rest = k % (HEX6_NSLOT * 16);
-        coef[r][rest] = (&HEX6_ICOEF[0][0][0])[k];
+        coef[r][rest] = (unsigned)((int)(&HEX6_ICOEF[0][0][0])[k] - HEX6_CMIN);
     }
     __syncthreads();
     const hex6_tile tl = tiles[blockIdx.y];
@@ -744,6 +782,11 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
         *o = __int_as_float(0x7fc00000);
         return;
     }
+    if (wflag[blockIdx.y * C + c]) {  // window values beyond the exact range
+        raise_status(status, BSF_ERANGE);
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
     const u128* G = scratch + tl.off + (long long)c * ncol * tl.nrow;
     const double SQ3 = 1.73205080756887729353;
     const double it2 = 2.0 / (h * SQ3), ih = 1.0 / h;
@@ -766,20 +809,30 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
     const int ib = (int)fib, jb = (int)fjb;
     const long long bs = __double2ll_rn((s0 - fib) * SC), bt = __double2ll_rn((t0 - fjb) * SC);
     const long long M48 = (1LL << 48) - 1, ONE = 1LL << 48;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        stp[0][k][tid] = ds[k];
+        stp[1][k][tid] = dtt[k];
+    }
     i128 e00 = 0;          // exact sum over the taps of +-A_00
     dflt rest = {0.f, 0.f};  // the other terms
+    long long sp = bs, tp = bt;  // the tap's position (Gray-code order: one step changes per tap)
 #pragma unroll 1
     for (int q = 0; q < 64; ++q) {
-        long long sf = bs, tf = bt;
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if ((q >> k) & 1) {
-                sf += ds[k];
-                tf += dtt[k];
+        const int gq = q ^ (q >> 1);
+        if (q) {
+            const int k = __ffs(q) - 1;
+            const long long dsk = stp[0][k][tid], dtk = stp[1][k][tid];
+            if ((gq >> k) & 1) {
+                sp += dsk;
+                tp += dtk;
+            } else {
+                sp -= dsk;
+                tp -= dtk;
             }
-        const int i0 = ib + (int)(sf >> 48), j0 = jb + (int)(tf >> 48);
-        sf &= M48;
-        tf &= M48;
+        }
+        const int i0 = ib + (int)(sp >> 48), j0 = jb + (int)(tp >> 48);
+        const long long sf = sp & M48, tf = tp & M48;
         int code;
         if (sf + tf < ONE)
             code = (sf > tf) | ((2 * sf + tf > ONE) << 1) | ((sf + 2 * tf > ONE) << 2);
@@ -793,63 +846,69 @@ __global__ void __launch_bounds__(ST_THREADS) k_hex6_stencil(const double* __res
             *o = __int_as_float(0x7fc00000);
             return;
         }
-        const bool neg = __popc(q) & 1;
-        // monomials sigma^a tau^b (a + b = 1..4) as double-floats
-        const dflt sg = df_of_frac48(sf), tg = df_of_frac48(tf);
-        dflt m[HEX6_NMONO];
-        m[1] = sg;
-        m[2] = tg;
-        m[3] = df_mul(sg, sg);
-        m[4] = df_mul(sg, tg);
-        m[5] = df_mul(tg, tg);
-        m[6] = df_mul(m[3], sg);
-        m[7] = df_mul(m[3], tg);
-        m[8] = df_mul(sg, m[5]);
-        m[9] = df_mul(m[5], tg);
-        m[10] = df_mul(m[3], m[3]);
-        m[11] = df_mul(m[3], m[4]);
-        m[12] = df_mul(m[3], m[5]);
-        m[13] = df_mul(m[4], m[5]);
-        m[14] = df_mul(m[5], m[5]);
+        const bool neg = __popc(gq) & 1;
         const u128* base = G + (long long)rr * ncol + cc;
-        // two groups of coefficients (monomials 0-7, 8-14): A = sum_k c_k g[m_k] in
-        // 31-bit limbs of g, int64 partial sums per limb
+        // With u = g + 2^95 in six unsigned 16-bit limbs u_m (|g| < 2^95, checked
+        // by the pre-integration) and c' = c - HEX6_CMIN in [0, 624]:
+        //   A = sum_k c_k g[m_k] = sum_m 2^(16 m) (P_m - (-HEX6_CMIN) Q_m) - 2^95 sum_k c_k,
+        // P_m = sum_k c'_k u_km < 24 * 624 * 2^16 < 2^30 and Q_m = sum_k u_km in 32
+        // bits, and sum_k c_k = HEX6_DEN for the constant term, 0 for the others.
+        unsigned Q[6] = {0, 0, 0, 0, 0, 0};
+        unsigned P[6][HEX6_NMONO];
 #pragma unroll
-        for (int grp = 0; grp < 2; ++grp) {
-            long long P0[8], P1[8], P2[8];
+        for (int l = 0; l < HEX6_NMONO; ++l)
 #pragma unroll
-            for (int l = 0; l < 8; ++l) P0[l] = P1[l] = P2[l] = 0;
+            for (int m = 0; m < 6; ++m) P[m][l] = 0;
 #pragma unroll 2
-            for (int k = 0; k < HEX6_NSLOT; ++k) {
-                const ulonglong2 gv = __ldg(reinterpret_cast<const ulonglong2*>(base + soff[reg][k]));
-                const i128 g = (i128)(((u128)gv.y << 64) | (u128)gv.x);
-                const int x0 = (int)((unsigned)(unsigned long long)g & 0x7FFFFFFFu);
-                const int x1 = (int)((unsigned)(unsigned long long)(g >> 31) & 0x7FFFFFFFu);
-                const int x2 = (int)(long long)(g >> 62);
-                const int4 cw = *reinterpret_cast<const int4*>(&coef[reg][k * 16 + grp * 8]);
-                const int cws[4] = {cw.x, cw.y, cw.z, cw.w};
+        for (int k = 0; k < HEX6_NSLOT; ++k) {
+            const ulonglong2 gv = __ldg(reinterpret_cast<const ulonglong2*>(base + soff[reg][k]));
+            const unsigned lo = (unsigned)gv.x, mi = (unsigned)(gv.x >> 32);
+            const unsigned hi = (unsigned)gv.y ^ 0x80000000u;  // bits 64-95 of g + 2^95
+            const unsigned w[6] = {lo & 0xFFFFu, lo >> 16, mi & 0xFFFFu, mi >> 16, hi & 0xFFFFu, hi >> 16};
 #pragma unroll
-                for (int l = 0; l < 8; ++l) {
-                    const int cl = (int)(short)((l & 1) ? (cws[l >> 1] >> 16) : (cws[l >> 1] & 0xFFFF));
-                    P0[l] += (long long)cl * x0;
-                    P1[l] += (long long)cl * x1;
-                    P2[l] += (long long)cl * x2;
-                }
-            }
+            for (int m = 0; m < 6; ++m) Q[m] += w[m];
 #pragma unroll
-            for (int l = 0; l < 8; ++l) {
-                const int mono = grp * 8 + l;
-                if (mono >= HEX6_NMONO) continue;
-                const i128 A = ((i128)P2[l] << 62) + ((i128)P1[l] << 31) + (i128)P0[l];
-                if (mono == 0) {
-                    e00 += neg ? -A : A;
-                } else {
-                    dflt ad = df_of_i128(A);
-                    if (neg) ad = {-ad.hi, -ad.lo};
-                    rest = df_add(rest, df_mul(ad, m[mono]));
+            for (int h4 = 0; h4 < 4; ++h4) {
+                const uint4 cq = *reinterpret_cast<const uint4*>(&coef[reg][k * 16 + h4 * 4]);
+                const unsigned cw[4] = {cq.x, cq.y, cq.z, cq.w};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    if (h4 * 4 + l >= HEX6_NMONO) continue;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) P[m][h4 * 4 + l] += cw[l] * w[m];
                 }
             }
         }
+        dflt ad[HEX6_NMONO];
+#pragma unroll
+        for (int mono = 0; mono < HEX6_NMONO; ++mono) {
+            int D[6];  // sum_k c_k u_km, at most 24 * 360 * 2^16 < 2^30 in magnitude
+#pragma unroll
+            for (int m = 0; m < 6; ++m) D[m] = (int)(P[m][mono] - Q[m] * (unsigned)(-HEX6_CMIN));
+            const long long E0 = (long long)D[0] + ((long long)D[1] << 16);
+            const long long E1 = (long long)D[2] + ((long long)D[3] << 16);
+            const long long E2 = (long long)D[4] + ((long long)D[5] << 16);
+            i128 A = ((i128)E2 << 64) + ((i128)E1 << 32) + (i128)E0;
+            if (mono == 0) {
+                A -= (i128)HEX6_DEN << 95;
+                e00 += neg ? -A : A;
+            } else {
+                ad[mono] = df_of_i128(neg ? -A : A);
+            }
+        }
+        // the monomials sigma^a tau^b (a + b = 1..4) and the terms, summed as a tree
+        const dflt sg = df_of_frac48(sf), tg = df_of_frac48(tf);
+        const dflt s2 = df_mul(sg, sg), st = df_mul(sg, tg), t2 = df_mul(tg, tg);
+        const dflt a1 = df_add(df_mul(ad[1], sg), df_mul(ad[2], tg));
+        const dflt a2 = df_add(df_mul(ad[3], s2), df_mul(ad[4], st));
+        const dflt a3 = df_add(df_mul(ad[5], t2), df_mul(ad[6], df_mul(s2, sg)));
+        const dflt b1 = df_add(df_add(a1, a2), df_add(a3, df_mul(ad[7], df_mul(s2, tg))));
+        const dflt c1 = df_add(df_mul(ad[8], df_mul(sg, t2)), df_mul(ad[9], df_mul(t2, tg)));
+        const dflt c2 = df_add(df_mul(ad[10], df_mul(s2, s2)), df_mul(ad[11], df_mul(s2, st)));
+        const dflt c3 = df_add(df_mul(ad[12], df_mul(s2, t2)), df_mul(ad[13], df_mul(st, t2)));
+        const dflt b2 = df_add(df_add(c1, c2), df_add(c3, df_mul(ad[14], df_mul(t2, t2))));
+        rest = df_add(rest, b1);
+        rest = df_add(rest, b2);
     }
     // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.) / 432 with
     // the window holding the running sums times 2^24
@@ -916,28 +975,30 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 }
 
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, void* scratch, cudaStream_t st) {
+                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st) {
     const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
     dim3 grid(ntiles, C);
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch);
+        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch,
+                                                                 wflag);
     } else {
         cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch);
+        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch,
+                                                               wflag);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile_w, int tile_h, double h,
-                                const hex6_tile* tiles, int ntiles, const void* scratch, float* out, unsigned* status,
-                                cudaStream_t st) {
+                                const hex6_tile* tiles, int ntiles, const void* scratch, const unsigned* wflag,
+                                float* out, unsigned* status, cudaStream_t st) {
     // 16 x 16 tiles, or 64-pixel tiles and their groups (64 x 64 up to 256 x 128)
     const bool fine = tile_w == 16 && tile_h == 16;
     const bool coarse = (tile_w == 64 || tile_w == 128 || tile_w == 256) && (tile_h == 64 || tile_h == 128);
     if (!fine && !coarse) return cudaErrorInvalidValue;
     const dim3 blk = tile_w == 16 ? dim3(16, 8) : dim3(32, 4);
     dim3 grid((tile_w / blk.x) * (tile_h / blk.y), ntiles, C);
-    k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, (const u128*)scratch, out, status);
+    k_hex6_stencil<<<grid, blk, 0, st>>>(scales, C, H, W, h, tiles, (const u128*)scratch, wflag, out, status);
     return cudaGetLastError();
 }

@@ -263,21 +263,29 @@ def emit(path):
         for _, _, p in slots:
             for v in p.values():
                 den = den * v.denominator // gcd(den, v.denominator)
-    lines.append("")
-    lines.append("// the weight polynomials times HEX6_DEN are integer polynomials; their")
-    lines.append("// coefficients, per piece and slot, monomials padded to 16 (the 16th is 0)")
-    lines.append(f"#define HEX6_DEN {den}")
-    lines.append("static __device__ const short HEX6_ICOEF[HEX6_NREGION][HEX6_NSLOT][16] = {")
+    rows = []
     for slots in tables:
-        lines.append("  {")
+        rows.append([])
         for k in range(nslot):
             p = slots[k][2] if k < len(slots) else {}
             vals = []
             for m in MONOS:
                 v = p.get(m, Fr(0)) * den
                 assert v.denominator == 1 and abs(v.numerator) < (1 << 15)
-                vals.append(str(v.numerator))
-            lines.append("    {" + ", ".join(vals) + ", 0},")
+                vals.append(v.numerator)
+            rows[-1].append(vals)
+    cmin = min(min(v) for r in rows for v in r)
+    lines.append("")
+    lines.append("// the weight polynomials times HEX6_DEN are integer polynomials; their")
+    lines.append("// coefficients, per piece and slot, monomials padded to 16 (the 16th is 0);")
+    lines.append("// HEX6_CMIN is the smallest of them")
+    lines.append(f"#define HEX6_DEN {den}")
+    lines.append(f"#define HEX6_CMIN ({cmin})")
+    lines.append("static __device__ const short HEX6_ICOEF[HEX6_NREGION][HEX6_NSLOT][16] = {")
+    for r in rows:
+        lines.append("  {")
+        for vals in r:
+            lines.append("    {" + ", ".join(str(v) for v in vals) + ", 0},")
         lines.append("  },")
     lines.append("};")
     text = "\n".join(lines) + "\n"

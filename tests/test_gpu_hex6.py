@@ -217,6 +217,33 @@ def test_grouped_tiles_with_widths_at_the_bound():
         assert abs(got[y, x] - ref) < TOL * abs(ref), (y, x)
 
 
+def test_image_values_beyond_the_exact_range():
+    """A NaN pixel flags the windows that hold it (NaN output there and
+    BSF_ERANGE), pixels whose windows do not hold it are unaffected; an image
+    of values near 1e30 (beyond the 2^95 range of the window sums) is flagged
+    everywhere; the largest u8 footprints stay within the range."""
+    H, W = 128, 96
+    f = np.stack([synth.image(H, W, seed=21, dtype="f32"), synth.image(H, W, seed=22, dtype="f32") * 1e30])
+    f[0, 5, 5] = np.nan
+    a6 = np.full((2, 6, H, W), 2.0, np.float32)
+    got, st = _run(f[:, None], a6, "scales")
+    assert st & (1 << L.BSF_ERANGE)
+    assert np.isnan(got[0, 0, 5, 5]) and np.isnan(got[1]).all()
+    y, x = 100, 80
+    ref = _ref_on_crop(f[0], a6[0, :, y, x].astype(np.float64), y, x)
+    assert abs(got[0, 0, y, x] - ref) < TOL * abs(ref)
+    # u8 at 255 everywhere with sigma 40-48: no flag
+    H, W = 448, 448
+    g = np.full((H, W), 255, np.uint8)
+    p = synth.srt_field(H, W, seed=23, sigma=(40.0, 48.0), rho=(1.0, 6.0))
+    got, st = _run(g, p, "srt")
+    assert st == 0
+    y, x = 224, 224
+    a, _ = n6.map6(p[:, y, x].reshape(3, 1).astype(np.float64), 2)
+    ref = _ref_on_crop(g.astype(np.float64), a[:, 0], y, x)
+    assert abs(got[y, x] - ref) < TOL * abs(ref)
+
+
 def test_host_pipeline_and_unsupported_entry_points():
     dev = _cuda()
     H, W = 80, 72
