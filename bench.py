@@ -48,9 +48,9 @@ STENCIL_INT_OPS_PER_PX = 16 * 124
 # product (88), two words per product sum and accumulator (28), 32 for
 # position, truncation, bounds and addresses: 260 per tap
 STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
-# six directions: 64 taps x 24 lattice points x 15 coefficients x 6 sixteen-bit limbs,
+# six directions: 64 taps x 24 lattice points x 15 coefficients x 5 twenty-bit limbs,
 # one int32 multiply-add each
-HEX6_IMAD_PER_PX = 64 * 24 * 15 * 6
+HEX6_IMAD_PER_PX = 64 * 24 * 15 * 5
 # Benchmarked workloads: (params kind, largest sigma or scale, forward+backward).
 BENCH_WORKLOADS = {
     "u2048_u8_n4": ("srt", 32.0, False),
@@ -431,9 +431,9 @@ def run_ours(args):
         launches += 13 * chunks * args.steps
     if N == 6:
         # six directions: the stencil's exact integer part is 64 taps x 24 lattice points x 15
-        # coefficients, each the product of a 10-bit coefficient and a 96-bit window value in
-        # six 16-bit limbs (6 int32 multiply-adds into 32-bit sums), against the int32
-        # multiply-add rate (152 SMs x 64 per clock x 2070 MHz)
+        # coefficients, each the product of a small integer coefficient and a 96-bit window
+        # value in five 20-bit limbs (5 int32 multiply-adds into 32-bit sums), against the
+        # int32 multiply-add rate (152 SMs x 64 per clock x 2070 MHz)
         ops_px6 = HEX6_IMAD_PER_PX
         achieved6 = ops_px6 * px_per_launch / (st_ms / 1e3) / 1e12
         peak6 = 152 * 64 * 2.070e9 / 1e12
@@ -442,7 +442,7 @@ def run_ours(args):
                     "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
                     "peak_note": "int32 multiply-add rate, 152 SMs x 64 per clock x 2070 MHz (derived; a "
                                  "multiply-add chain probe reached 19.1 Tops/s); int32 multiply-adds of the exact "
-                                 "coefficient sums, 64 taps x 24 points x 15 coefficients x 6 sixteen-bit limbs",
+                                 "coefficient sums, 64 taps x 24 points x 15 coefficients x 5 twenty-bit limbs",
                     "int_madds_per_px": ops_px6,
                     "launches_per_step": n_st / args.steps,
                     "preintegrate_note": "scale map + window transfer and six exact running sums, per chunk"}

@@ -676,6 +676,10 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
 
 constexpr int ST_THREADS = 128;  // 32 x 4 pixels for 64-pixel tiles, 16 x 8 for 16-pixel tiles
 
+// the canonical piece's coefficients: every lane reads the same entry (the slot
+// loop is uniform), so they reach the multiply-adds as uniform operands
+__constant__ int HEX6_CC_CONST[HEX6_NSLOT][HEX6_NMONO] = HEX6_CCOEF_INIT;
+
 // ---- double-float (a pair of FP32 numbers, about 48 bits) ----
 struct dflt {
     float hi, lo;
@@ -728,10 +732,14 @@ __device__ __forceinline__ dflt df_of_frac48(long long x) {
 //     (each direction's step a_k u_k rounded once, so the 64 taps form an
 //     exact affine mesh for scales perturbed by 2^-48 lattice units); the taps
 //     are visited in Gray-code order, one step added or removed per tap;
-//   - the quartic of a tap's piece, F = sum_ab A_ab sigma^a tau^b / 432, has
-//     integer coefficients A_ab = sum_k c_abk g[m_k] (c from hex6_tables.h),
-//     computed exactly from the exact window sums in 16-bit limbs with 32-bit
-//     multiply-adds, all 15 in one pass over the 24 points;
+//   - the twelve pieces of a cell are images of one canonical piece under
+//     lattice symmetries that leave the element invariant: a tap of piece r is
+//     evaluated at its image x in the canonical piece (exact, 48-bit), reading
+//     the window at the piece's slot offsets;
+//   - the canonical quartic, F = sum_ab A_ab x_1^a x_2^b / 432, has integer
+//     coefficients A_ab = sum_k c_abk g[m_k] (c from hex6_tables.h, the same for
+//     every lane), computed exactly from the exact window sums in 20-bit limbs
+//     with 32-bit multiply-adds, all 15 in one pass over the 24 points;
 //   - the constant terms A_00, which carry the size of the sums, are added over
 //     the 64 taps exactly, in 128-bit integers;
 // and only the remaining terms (derivatives of the sums, smaller by the
@@ -742,18 +750,13 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
                                                               const u128* __restrict__ scratch,
                                                               const unsigned* __restrict__ wflag,
                                                               float* __restrict__ out, unsigned* __restrict__ status) {
-    // coefficients minus HEX6_CMIN (all non-negative): 16 per (piece, slot);
-    // pieces 24 * 64 + 16 bytes apart (bank spread)
-    __shared__ __align__(16) unsigned coef[HEX6_NREGION][HEX6_NSLOT * 16 + 4];
     __shared__ int soff[HEX6_NREGION][HEX6_NSLOT];
+    __shared__ __align__(16) int sym[HEX6_NREGION][8];  // L_r^-1 and v_r of each piece
     __shared__ int lut[16];
     __shared__ long long stp[2][6][ST_THREADS];  // per thread: the six steps of the tap mesh
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
-    for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT * 16; k += ST_THREADS) {
-        const int r = k / (HEX6_NSLOT * 16), rest = k % (HEX6_NSLOT * 16);
-        coef[r][rest] = (unsigned)((int)(&HEX6_ICOEF[0][0][0])[k] - HEX6_CMIN);
-    }
+    if (tid < HEX6_NREGION * 8) sym[tid / 8][tid % 8] = (tid % 8) < 6 ? HEX6_SYM[tid / 8][tid % 8] : 0;
     __syncthreads();
     const hex6_tile tl = tiles[blockIdx.y];
     const int ncol = tl.ncol;
@@ -847,57 +850,52 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
             return;
         }
         const bool neg = __popc(gq) & 1;
+        // the tap in the canonical piece: x = L_r^-1 ((sigma, tau) - v_r), exact (48-bit fractions)
+        const int4 sl = *reinterpret_cast<const int4*>(&sym[reg][0]);
+        const int2 sv = *reinterpret_cast<const int2*>(&sym[reg][4]);
+        const long long xs = sf - (long long)sv.x * ONE, xt = tf - (long long)sv.y * ONE;
+        const long long x1 = sl.x * xs + sl.y * xt, x2 = sl.z * xs + sl.w * xt;
         const u128* base = G + (long long)rr * ncol + cc;
-        // With u = g + 2^95 in six unsigned 16-bit limbs u_m (|g| < 2^95, checked
-        // by the pre-integration) and c' = c - HEX6_CMIN in [0, 624]:
-        //   A = sum_k c_k g[m_k] = sum_m 2^(16 m) (P_m - (-HEX6_CMIN) Q_m) - 2^95 sum_k c_k,
-        // P_m = sum_k c'_k u_km < 24 * 624 * 2^16 < 2^30 and Q_m = sum_k u_km in 32
-        // bits, and sum_k c_k = HEX6_DEN for the constant term, 0 for the others.
-        unsigned Q[6] = {0, 0, 0, 0, 0, 0};
-        unsigned P[6][HEX6_NMONO];
+        // A_m = sum_k C[k][m] g_k over the canonical piece's 24 points, exactly.  With
+        // u = g + 2^95 (|g| < 2^95, checked by the pre-integration) in five limbs of 20
+        // bits (the last 16), P[l][m] = sum_k C[k][m] u_kl is at most
+        // max_m sum_k |C[k][m]| (696) * 2^20 < 2^31 in magnitude: plain 32-bit
+        // multiply-adds, and A_m = sum_l 2^(20 l) P[l][m] - 2^95 sum_k C[k][m], the last
+        // sum HEX6_DEN for the constant term and 0 for the others.
+        int P[5][HEX6_NMONO];
 #pragma unroll
-        for (int l = 0; l < HEX6_NMONO; ++l)
+        for (int m = 0; m < HEX6_NMONO; ++m)
 #pragma unroll
-            for (int m = 0; m < 6; ++m) P[m][l] = 0;
+            for (int l = 0; l < 5; ++l) P[l][m] = 0;
 #pragma unroll 2
         for (int k = 0; k < HEX6_NSLOT; ++k) {
             const ulonglong2 gv = __ldg(reinterpret_cast<const ulonglong2*>(base + soff[reg][k]));
-            const unsigned lo = (unsigned)gv.x, mi = (unsigned)(gv.x >> 32);
+            const unsigned long long lo = gv.x;
             const unsigned hi = (unsigned)gv.y ^ 0x80000000u;  // bits 64-95 of g + 2^95
-            const unsigned w[6] = {lo & 0xFFFFu, lo >> 16, mi & 0xFFFFu, mi >> 16, hi & 0xFFFFu, hi >> 16};
+            const int w[5] = {(int)(lo & 0xFFFFFu), (int)((lo >> 20) & 0xFFFFFu), (int)((lo >> 40) & 0xFFFFFu),
+                              (int)(((lo >> 60) | ((unsigned long long)hi << 4)) & 0xFFFFFu), (int)(hi >> 16)};
 #pragma unroll
-            for (int m = 0; m < 6; ++m) Q[m] += w[m];
+            for (int m = 0; m < HEX6_NMONO; ++m) {
+                const int cm = HEX6_CC_CONST[k][m];
 #pragma unroll
-            for (int h4 = 0; h4 < 4; ++h4) {
-                const uint4 cq = *reinterpret_cast<const uint4*>(&coef[reg][k * 16 + h4 * 4]);
-                const unsigned cw[4] = {cq.x, cq.y, cq.z, cq.w};
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    if (h4 * 4 + l >= HEX6_NMONO) continue;
-#pragma unroll
-                    for (int m = 0; m < 6; ++m) P[m][h4 * 4 + l] += cw[l] * w[m];
-                }
+                for (int l = 0; l < 5; ++l) P[l][m] += cm * w[l];
             }
         }
         dflt ad[HEX6_NMONO];
 #pragma unroll
-        for (int mono = 0; mono < HEX6_NMONO; ++mono) {
-            int D[6];  // sum_k c_k u_km, at most 24 * 360 * 2^16 < 2^30 in magnitude
-#pragma unroll
-            for (int m = 0; m < 6; ++m) D[m] = (int)(P[m][mono] - Q[m] * (unsigned)(-HEX6_CMIN));
-            const long long E0 = (long long)D[0] + ((long long)D[1] << 16);
-            const long long E1 = (long long)D[2] + ((long long)D[3] << 16);
-            const long long E2 = (long long)D[4] + ((long long)D[5] << 16);
-            i128 A = ((i128)E2 << 64) + ((i128)E1 << 32) + (i128)E0;
-            if (mono == 0) {
+        for (int m = 0; m < HEX6_NMONO; ++m) {
+            const long long E0 = (long long)P[0][m] + ((long long)P[1][m] << 20);
+            const long long E1 = (long long)P[2][m] + ((long long)P[3][m] << 20);
+            i128 A = (i128)E0 + ((i128)E1 << 40) + ((i128)P[4][m] << 80);
+            if (m == 0) {
                 A -= (i128)HEX6_DEN << 95;
                 e00 += neg ? -A : A;
             } else {
-                ad[mono] = df_of_i128(neg ? -A : A);
+                ad[m] = df_of_i128(neg ? -A : A);
             }
         }
-        // the monomials sigma^a tau^b (a + b = 1..4) and the terms, summed as a tree
-        const dflt sg = df_of_frac48(sf), tg = df_of_frac48(tf);
+        // the monomials x_1^a x_2^b (a + b = 1..4) and the terms, summed as a tree
+        const dflt sg = df_of_frac48(x1), tg = df_of_frac48(x2);
         const dflt s2 = df_mul(sg, sg), st = df_mul(sg, tg), t2 = df_mul(tg, tg);
         const dflt a1 = df_add(df_mul(ad[1], sg), df_mul(ad[2], tg));
         const dflt a2 = df_add(df_mul(ad[3], s2), df_mul(ad[4], st));

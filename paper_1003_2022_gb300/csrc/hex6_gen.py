@@ -217,6 +217,81 @@ def check(samples, tables):
                     assert vals[r] == vals[owners[0]], (s, t, a, b, r)
 
 
+# ---- the symmetries of the element: one canonical piece ----
+
+R60 = ((0, -1), (1, 1))   # rotation by 60 degrees, in lattice coordinates (columns: images of e1, e2)
+SREF = ((1, 1), (0, -1))  # reflection across the s axis
+
+
+def mmul(A, B):
+    return tuple(tuple(sum(A[i][k] * B[k][j] for k in range(2)) for j in range(2)) for i in range(2))
+
+
+def mapply(A, p):
+    return (A[0][0] * p[0] + A[0][1] * p[1], A[1][0] * p[0] + A[1][1] * p[1])
+
+
+def lattice_symmetries():
+    """The twelve linear symmetries of the hexagonal lattice (rotations by
+    multiples of 60 degrees, with and without a reflection) as integer matrices
+    in lattice coordinates.  Each maps the six directions to themselves up to
+    sign, so M (the box spline of those directions) is invariant under it."""
+    out, A = [], ((1, 0), (0, 1))
+    for _ in range(6):
+        out += [A, mmul(A, SREF)]
+        A = mmul(R60, A)
+    dirs = set(XI) | {(-a, -b) for a, b in XI}
+    for L in out:
+        assert all(mapply(L, x) in dirs for x in XI)
+        assert abs(L[0][0] * L[1][1] - L[0][1] * L[1][0]) == 1
+    assert len(set(out)) == 12
+    return out
+
+
+def compose(p, L, v):
+    """p(L x + v) as a polynomial in x = (sigma, tau)."""
+    ps = {(1, 0): Fr(L[0][0]), (0, 1): Fr(L[0][1]), (0, 0): Fr(v[0])}
+    pt = {(1, 0): Fr(L[1][0]), (0, 1): Fr(L[1][1]), (0, 0): Fr(v[1])}
+    out = {}
+    for (a, b), c in p.items():
+        out = padd(out, {k: c * w for k, w in pmul(ppow(ps, a), ppow(pt, b)).items()})
+    return out
+
+
+def canonical_maps(samples, tables, canon):
+    """For every piece r an affine lattice map phi_r(x) = L x + v that takes the
+    canonical piece onto piece r (both in the unit cell).  The weight of the
+    lattice point phi_r(m) at phi_r(x) is the weight of m at x, so a point of
+    piece r is evaluated with the canonical piece's polynomials at
+    x = phi_r^-1(sigma, tau), the slots read at phi_r of the canonical slots.
+    Checked exactly: every polynomial of piece r composed with phi_r is the
+    canonical one of its slot."""
+    maps = []
+    for r in range(12):
+        found = None
+        for L in lattice_symmetries():
+            for v in itertools.product(range(-2, 3), repeat=2):
+                x = mapply(L, samples[canon])
+                x = (x[0] + v[0], x[1] + v[1])
+                if 0 < x[0] < 1 and 0 < x[1] < 1 and region_code(*x) == region_code(*samples[r]):
+                    found = (L, v)
+                    break
+            if found:
+                break
+        assert found, r
+        L, v = found
+        byoff = {(di, dj): p for di, dj, p in tables[r]}
+        order = []
+        for di, dj, p0 in tables[canon]:
+            m = mapply(L, (-di, -dj))
+            key = (-(m[0] + v[0]), -(m[1] + v[1]))
+            assert compose(byoff[key], L, v) == p0, (r, di, dj)
+            order.append(key)
+        assert sorted(order) == sorted(byoff)
+        maps.append((L, v, order))
+    return maps
+
+
 def on_closure(sample, s, t):
     """True if (s, t) is in the closed piece that contains `sample`."""
     lines = [lambda x, y: x + y - 1, lambda x, y: x - y, lambda x, y: 2 * x + y - 1, lambda x, y: 2 * x + y - 2,
@@ -232,62 +307,62 @@ def on_closure(sample, s, t):
 def emit(path):
     samples, tables, lut = build()
     nslot = max(len(s) for s in tables)
-    lines = ["// Generated by hex6_gen.py -- do not edit.",
-             "// Pieces of the six-directional interpolation element on the hexagonal",
-             "// lattice: weight of lattice point (floor(s) - di, floor(t) - dj) at the",
-             "// fractional position (sigma, tau) of a point in piece r is",
-             "// sum_k HEX6_ICOEF[r][slot][k] * sigma^a_k tau^b_k / HEX6_DEN (monomial order below).",
-             "#pragma once", "",
-             f"#define HEX6_NREGION 12", f"#define HEX6_NSLOT {nslot}", f"#define HEX6_NMONO {len(MONOS)}", "",
-             "// monomial exponents (a, b) of sigma^a tau^b",
-             "static __device__ const int HEX6_MONO_A[HEX6_NMONO] = {" + ", ".join(str(a) for a, _ in MONOS) + "};",
-             "static __device__ const int HEX6_MONO_B[HEX6_NMONO] = {" + ", ".join(str(b) for _, b in MONOS) + "};",
-             "",
-             "// piece of a code: bit 3 = upper triangle (sigma + tau >= 1), bit 0 = sigma > tau,",
-             "// bit 1 = 2 sigma + tau > 1 (lower) or > 2 (upper), bit 2 = sigma + 2 tau > 1 or > 2",
-             "static __device__ const int HEX6_REGION_LUT[16] = {" + ", ".join(str(v) for v in lut) + "};", "",
-             "// number of lattice points with a non-zero weight, per piece",
-             "static __device__ const int HEX6_COUNT[HEX6_NREGION] = {" + ", ".join(str(len(s)) for s in tables) + "};",
-             "// offsets (di, dj) per piece and slot (unused slots: 0, 0 with zero weight)",
-             "static __device__ const signed char HEX6_DI[HEX6_NREGION][HEX6_NSLOT] = {"]
-    for slots in tables:
-        lines.append("    {" + ", ".join(str(s[0]) for s in slots) + ", 0" * (nslot - len(slots)) + "},")
-    lines.append("};")
-    lines.append("static __device__ const signed char HEX6_DJ[HEX6_NREGION][HEX6_NSLOT] = {")
-    for slots in tables:
-        lines.append("    {" + ", ".join(str(s[1]) for s in slots) + ", 0" * (nslot - len(slots)) + "},")
-    lines.append("};")
-    # integer coefficients: every coefficient times the common denominator
+    assert all(len(s) == nslot for s in tables)
+    # the canonical piece: the one with the fewest non-zero coefficients
+    nnz = [sum(len(p) for _, _, p in slots) for slots in tables]
+    canon = min(range(12), key=lambda r: (nnz[r], r))
+    maps = canonical_maps(samples, tables, canon)
+    # integer coefficients of the canonical piece: every coefficient times the common denominator
     den = 1
     for slots in tables:
         for _, _, p in slots:
             for v in p.values():
                 den = den * v.denominator // gcd(den, v.denominator)
     rows = []
-    for slots in tables:
-        rows.append([])
-        for k in range(nslot):
-            p = slots[k][2] if k < len(slots) else {}
-            vals = []
-            for m in MONOS:
-                v = p.get(m, Fr(0)) * den
-                assert v.denominator == 1 and abs(v.numerator) < (1 << 15)
-                vals.append(v.numerator)
-            rows[-1].append(vals)
-    cmin = min(min(v) for r in rows for v in r)
-    lines.append("")
-    lines.append("// the weight polynomials times HEX6_DEN are integer polynomials; their")
-    lines.append("// coefficients, per piece and slot, monomials padded to 16 (the 16th is 0);")
-    lines.append("// HEX6_CMIN is the smallest of them")
-    lines.append(f"#define HEX6_DEN {den}")
-    lines.append(f"#define HEX6_CMIN ({cmin})")
-    lines.append("static __device__ const short HEX6_ICOEF[HEX6_NREGION][HEX6_NSLOT][16] = {")
-    for r in rows:
-        lines.append("  {")
-        for vals in r:
-            lines.append("    {" + ", ".join(str(v) for v in vals) + ", 0},")
-        lines.append("  },")
+    for _, _, p in tables[canon]:
+        vals = []
+        for m in MONOS:
+            v = p.get(m, Fr(0)) * den
+            assert v.denominator == 1
+            vals.append(v.numerator)
+        rows.append(vals)
+    lines = ["// Generated by hex6_gen.py -- do not edit.",
+             "// Pieces of the six-directional interpolation element on the hexagonal",
+             "// lattice.  The twelve pieces of a lattice cell are images of one canonical",
+             "// piece under lattice symmetries phi_r(x) = L_r x + v_r, which leave the element",
+             "// invariant.  A point of the cell at fractional position (sigma, tau) in piece r",
+             "// has, at x = L_r^-1 ((sigma, tau) - v_r), the canonical weights: lattice point",
+             "// (floor(s) - HEX6_DI[r][k], floor(t) - HEX6_DJ[r][k]) weighs",
+             "// sum_m C[k][m] x_1^a_m x_2^b_m / HEX6_DEN, C = HEX6_CCOEF_INIT (monomial order below).",
+             "#pragma once", "",
+             f"#define HEX6_NREGION 12", f"#define HEX6_NSLOT {nslot}", f"#define HEX6_NMONO {len(MONOS)}",
+             f"#define HEX6_DEN {den}", f"#define HEX6_CANON {canon}", "",
+             "// monomial exponents (a, b) of x_1^a x_2^b",
+             "static __device__ const int HEX6_MONO_A[HEX6_NMONO] = {" + ", ".join(str(a) for a, _ in MONOS) + "};",
+             "static __device__ const int HEX6_MONO_B[HEX6_NMONO] = {" + ", ".join(str(b) for _, b in MONOS) + "};",
+             "",
+             "// piece of a code: bit 3 = upper triangle (sigma + tau >= 1), bit 0 = sigma > tau,",
+             "// bit 1 = 2 sigma + tau > 1 (lower) or > 2 (upper), bit 2 = sigma + 2 tau > 1 or > 2",
+             "static __device__ const int HEX6_REGION_LUT[16] = {" + ", ".join(str(v) for v in lut) + "};", "",
+             "// per piece: L_r^-1 (row-major, 4 entries), then v_r",
+             "static __device__ const int HEX6_SYM[HEX6_NREGION][6] = {"]
+    for L, v, _ in maps:
+        dt = L[0][0] * L[1][1] - L[0][1] * L[1][0]
+        inv = (L[1][1] * dt, -L[0][1] * dt, -L[1][0] * dt, L[0][0] * dt)
+        lines.append("    {" + ", ".join(str(x) for x in inv + tuple(v)) + "},")
     lines.append("};")
+    lines.append("// offsets (di, dj) per piece and canonical slot")
+    for nm, c in (("HEX6_DI", 0), ("HEX6_DJ", 1)):
+        lines.append(f"static __device__ const signed char {nm}[HEX6_NREGION][HEX6_NSLOT] = {{")
+        for _, _, order in maps:
+            lines.append("    {" + ", ".join(str(o[c]) for o in order) + "},")
+        lines.append("};")
+    lines.append("// the canonical piece's coefficients (times HEX6_DEN), per slot and monomial, as")
+    lines.append("// an initializer")
+    lines.append("#define HEX6_CCOEF_INIT \\")
+    for k in range(nslot):
+        lines.append("    " + ("{" if k == 0 else " ") + "{" + ", ".join(str(v) for v in rows[k]) + "}" +
+                     ("}" if k == nslot - 1 else ", \\"))
     text = "\n".join(lines) + "\n"
     if path is None:
         return text
