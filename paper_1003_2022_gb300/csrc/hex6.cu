@@ -52,55 +52,270 @@ __constant__ double MAP6_Z[6][3] = {{1.0, 0.0, 1.0},
                                     {-0.5, 0.86602540378443864676, 1.0},
                                     {-0.5, -0.86602540378443864676, -1.0}};
 
+__constant__ float MAP6_C2F[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
+__constant__ float MAP6_S2F[6] = {0.0f, 0.86602540378443864676f, 0.86602540378443864676f, 0.0f,
+                                  -0.86602540378443864676f, -0.86602540378443864676f};
+__constant__ float MAP6_ZF[6][3] = {{1.0f, 0.0f, 1.0f},
+                                    {-0.5f, 0.86602540378443864676f, -1.0f},
+                                    {-0.5f, -0.86602540378443864676f, 1.0f},
+                                    {1.0f, 0.0f, -1.0f},
+                                    {-0.5f, 0.86602540378443864676f, 1.0f},
+                                    {-0.5f, -0.86602540378443864676f, -1.0f}};
+// the constants above in the precision R of the solver
+template <class R>
+struct m6c;
+template <>
+struct m6c<double> {
+    static __device__ __forceinline__ double c2(int k) { return MAP6_C2[k]; }
+    static __device__ __forceinline__ double s2(int k) { return MAP6_S2[k]; }
+    static __device__ __forceinline__ double z(int k, int l) { return MAP6_Z[k][l]; }
+};
+template <>
+struct m6c<float> {
+    static __device__ __forceinline__ float c2(int k) { return MAP6_C2F[k]; }
+    static __device__ __forceinline__ float s2(int k) { return MAP6_S2F[k]; }
+    static __device__ __forceinline__ float z(int k, int l) { return MAP6_ZF[k][l]; }
+};
+
 // ||K||^2 for six directions: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m)
 // = (S0^2 + |S1|^2) / 2, S0 = sum q_k, S1 = sum q_k exp(2 i theta_k), q = p^2
-__device__ __forceinline__ double kurt6(const double p[6]) {
-    double s0 = 0.0, sr = 0.0, si = 0.0;
+template <class R>
+__device__ __forceinline__ R kurt6(const R p[6]) {
+    R s0 = 0, sr = 0, si = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double q = p[k] * p[k];
+        const R q = p[k] * p[k];
         s0 += q;
-        sr += q * MAP6_C2[k];
-        si += q * MAP6_S2[k];
+        sr += q * m6c<R>::c2(k);
+        si += q * m6c<R>::s2(k);
     }
-    return 0.5 * (s0 * s0 + sr * sr + si * si);
+    return R(0.5) * (s0 * s0 + sr * sr + si * si);
 }
 
-__device__ __forceinline__ void p_of_t(const double pbar[6], const double t[3], double p[6]) {
+template <class R>
+__device__ __forceinline__ void p_of_t(const R pbar[6], const R t[3], R p[6]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) p[k] = pbar[k] + MAP6_Z[k][0] * t[0] + MAP6_Z[k][1] * t[1] + MAP6_Z[k][2] * t[2];
+    for (int k = 0; k < 6; ++k)
+        p[k] = pbar[k] + m6c<R>::z(k, 0) * t[0] + m6c<R>::z(k, 1) * t[1] + m6c<R>::z(k, 2) * t[2];
 }
 
 // A x = b for a symmetric positive definite d x d matrix, d = 1, 2, 3 (unrolled Cholesky)
-__device__ __forceinline__ bool spd_solve(int d, const double A[3][3], const double b[3], double x[3]) {
+template <class R>
+__device__ __forceinline__ bool spd_solve(int d, const R A[3][3], const R b[3], R x[3]) {
     if (d == 1) {
-        if (!(A[0][0] > 0.0)) return false;
+        if (!(A[0][0] > R(0))) return false;
         x[0] = b[0] / A[0][0];
         return true;
     }
     if (d == 2) {
-        const double det = A[0][0] * A[1][1] - A[0][1] * A[0][1];
-        if (!(A[0][0] > 0.0) || !(det > 0.0)) return false;
-        const double id = 1.0 / det;
+        const R det = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+        if (!(A[0][0] > R(0)) || !(det > R(0))) return false;
+        const R id = R(1) / det;
         x[0] = (A[1][1] * b[0] - A[0][1] * b[1]) * id;
         x[1] = (A[0][0] * b[1] - A[0][1] * b[0]) * id;
         return true;
     }
-    if (!(A[0][0] > 0.0)) return false;
-    const double l00 = sqrt(A[0][0]);
-    const double l10 = A[1][0] / l00, l20 = A[2][0] / l00;
-    const double d11 = A[1][1] - l10 * l10;
-    if (!(d11 > 0.0)) return false;
-    const double l11 = sqrt(d11);
-    const double l21 = (A[2][1] - l20 * l10) / l11;
-    const double d22 = A[2][2] - l20 * l20 - l21 * l21;
-    if (!(d22 > 0.0)) return false;
-    const double l22 = sqrt(d22);
-    const double y0 = b[0] / l00, y1 = (b[1] - l10 * y0) / l11, y2 = (b[2] - l20 * y0 - l21 * y1) / l22;
+    if (!(A[0][0] > R(0))) return false;
+    const R l00 = sqrt(A[0][0]);
+    const R l10 = A[1][0] / l00, l20 = A[2][0] / l00;
+    const R d11 = A[1][1] - l10 * l10;
+    if (!(d11 > R(0))) return false;
+    const R l11 = sqrt(d11);
+    const R l21 = (A[2][1] - l20 * l10) / l11;
+    const R d22 = A[2][2] - l20 * l20 - l21 * l21;
+    if (!(d22 > R(0))) return false;
+    const R l22 = sqrt(d22);
+    const R y0 = b[0] / l00, y1 = (b[1] - l10 * y0) / l11, y2 = (b[2] - l20 * y0 - l21 * y1) / l22;
     x[2] = y2 / l22;
     x[1] = (y1 - l21 * x[2]) / l11;
     x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
     return true;
+}
+
+// The active-set Newton iteration on the null-space coordinates t (p = pbar + Z t)
+// from a feasible t with the working set wmask (nw bounds): a Newton step on the
+// face of the working set, the ratio test against the other bounds, Armijo
+// backtracking far from the optimum; on convergence (a step below step_tol * T)
+// the bound multipliers, and the most negative one (below -mult_tol * |g|)
+// leaves the working set.  R = float for the first pass, double for the last.
+template <class R>
+__device__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int& nw, int max_it, R step_tol,
+                            R mult_tol, R armijo_rel) {
+    for (int it = 0; it < max_it; ++it) {
+        R p[6];
+        p_of_t(pbar, t, p);
+        R s0 = 0, sr = 0, si = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const R q = p[k] * p[k];
+            s0 += q;
+            sr += q * m6c<R>::c2(k);
+            si += q * m6c<R>::s2(k);
+        }
+        const R h0 = R(0.5) * (s0 * s0 + sr * sr + si * si);
+        // gradient and Hessian in t: H = 4 (sg sg^T + mr mr^T + mi mi^T) + 4 Z^T diag(Dq) Z
+        R g[3] = {0, 0, 0}, Hm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        R sg[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const R dq = R(0.5) * (s0 + m6c<R>::c2(k) * sr + m6c<R>::s2(k) * si);
+            const R gp = R(4) * p[k] * dq;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const R z = m6c<R>::z(k, l);
+                g[l] += z * gp;
+                sg[l] += p[k] * z;
+                mr[l] += m6c<R>::c2(k) * p[k] * z;
+                mi[l] += m6c<R>::s2(k) * p[k] * z;
+#pragma unroll
+                for (int m = 0; m <= l; ++m) Hm[l][m] += R(4) * dq * z * m6c<R>::z(k, m);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int m = 0; m <= l; ++m) {
+                Hm[l][m] += R(4) * (sg[l] * sg[m] + mr[l] * mr[m] + mi[l] * mi[m]);
+                Hm[m][l] = Hm[l][m];
+            }
+        // the first two bounds of the working set, and an orthonormal basis N of
+        // the directions that keep them
+        R za[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
+        int seen = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if ((wmask >> k) & 1) {
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    if (seen == 0) za[l] = m6c<R>::z(k, l);
+                    if (seen == 1) zb[l] = m6c<R>::z(k, l);
+                }
+                ++seen;
+            }
+        const int d = 3 - nw;
+        R N[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        if (nw == 1) {
+            const R zn = sqrt(za[0] * za[0] + za[1] * za[1] + za[2] * za[2]);
+            const R n1[3] = {za[0] / zn, za[1] / zn, za[2] / zn};
+            // u: the unit vector of the smallest component of n1, made orthogonal to n1
+            R u[3] = {0, 0, 0};
+            const int e = (fabs(n1[1]) < fabs(n1[0])) ? ((fabs(n1[2]) < fabs(n1[1])) ? 2 : 1)
+                                                         : ((fabs(n1[2]) < fabs(n1[0])) ? 2 : 0);
+            const R dd = e == 0 ? n1[0] : (e == 1 ? n1[1] : n1[2]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) u[l] = (l == e ? R(1) : R(0)) - dd * n1[l];
+            const R un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) u[l] /= un;
+            const R v[3] = {n1[1] * u[2] - n1[2] * u[1], n1[2] * u[0] - n1[0] * u[2], n1[0] * u[1] - n1[1] * u[0]};
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                N[l][0] = u[l];
+                N[l][1] = v[l];
+            }
+        } else if (nw == 2) {
+            const R n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2],
+                                 za[0] * zb[1] - za[1] * zb[0]};
+            const R nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) N[l][0] = n[l] / nn;
+        }
+        R step[3] = {0, 0, 0}, dec = 0;
+        if (d > 0) {
+            R Hr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gr[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= d) continue;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) gr[a] -= N[l][a] * g[l];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (b >= d) continue;
+                    R sab = 0;
+#pragma unroll
+                    for (int l = 0; l < 3; ++l)
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) sab += N[l][a] * Hm[l][m] * N[m][b];
+                    Hr[a][b] = sab;
+                }
+            }
+            if (!spd_solve(d, Hr, gr, u)) break;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) step[l] = N[l][0] * u[0] + (d > 1 ? N[l][1] * u[1] : R(0)) +
+                                                  (d > 2 ? N[l][2] * u[2] : R(0));
+            dec = -(g[0] * step[0] + g[1] * step[1] + g[2] * step[2]);
+        }
+        // converged on the face when the Newton step is at the rounding level of t
+        // (the decrement alone cannot tell: near the optimum it is rounding noise)
+        const R smax = fmax(fabs(step[0]), fmax(fabs(step[1]), fabs(step[2])));
+        if (d == 0 || dec <= R(0) || smax <= step_tol * T) {
+            // converged on the face: bound multipliers from g = sum_{k in W} lambda_k z_k
+            if (nw == 0) return;
+            R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[3] = {0, 0, 0}, lam[3] = {0, 0, 0};
+            int idx[3] = {0, 0, 0}, a = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if ((wmask >> k) & 1) {
+                    if (a < 3) idx[a] = k;
+                    ++a;
+                }
+            for (int i = 0; i < nw; ++i) {
+                const int ki = idx[i];
+                rhs[i] = m6c<R>::z(ki, 0) * g[0] + m6c<R>::z(ki, 1) * g[1] + m6c<R>::z(ki, 2) * g[2];
+                for (int j2 = 0; j2 < nw; ++j2) {
+                    const int kj = idx[j2];
+                    G[i][j2] = m6c<R>::z(ki, 0) * m6c<R>::z(kj, 0) + m6c<R>::z(ki, 1) * m6c<R>::z(kj, 1) +
+                               m6c<R>::z(ki, 2) * m6c<R>::z(kj, 2);
+                }
+            }
+            if (!spd_solve(nw, G, rhs, lam)) return;
+            int worst = -1;
+            const R gs = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+            R lw = -mult_tol * (gs + R(1e-30));
+            for (int i = 0; i < nw; ++i)
+                if (lam[i] < lw) {
+                    lw = lam[i];
+                    worst = idx[i];
+                }
+            if (worst < 0) return;
+            wmask &= ~(1 << worst);
+            --nw;
+            continue;
+        }
+        // longest step along the Newton direction that keeps p >= lb
+        R amax = 1;
+        int blk = -1;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if ((wmask >> k) & 1) continue;
+            const R dp = m6c<R>::z(k, 0) * step[0] + m6c<R>::z(k, 1) * step[1] + m6c<R>::z(k, 2) * step[2];
+            if (dp < R(0)) {
+                const R ak = fmax(p[k] - lb, R(0)) / (-dp);
+                if (ak < amax) {
+                    amax = ak;
+                    blk = k;
+                }
+            }
+        }
+        // backtracking (Armijo) while far from the optimum; near it the full Newton
+        // step converges quadratically and the test would only see rounding noise
+        R alpha = amax;
+        if (dec > armijo_rel * h0) {
+            for (int bt = 0; bt < 40; ++bt) {
+                const R tn[3] = {t[0] + alpha * step[0], t[1] + alpha * step[1], t[2] + alpha * step[2]};
+                R pn[6];
+                p_of_t(pbar, tn, pn);
+                if (kurt6(pn) <= h0 - R(0.25) * alpha * dec) break;
+                alpha *= R(0.5);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l) t[l] += alpha * step[l];
+        if (blk >= 0 && alpha == amax && nw < 3) {
+            wmask |= 1 << blk;
+            ++nw;
+        }
+    }
 }
 
 struct map6_p {
@@ -165,185 +380,40 @@ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
         for (int k = 0; k < 6; ++k) p[k] = fmax(p[k], lb);
         return res;
     }
-    for (int it = 0; it < 60; ++it) {
-        p_of_t(pbar, t, p);
-        double s0 = 0.0, sr = 0.0, si = 0.0;
+    // single precision first, to about the rounding level of FP32; then the
+    // same iteration in FP64 from there (typically one or two steps and the
+    // multiplier check), so the result is the FP64 optimum
+    float pbf[6], tf[3];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const double q = p[k] * p[k];
-            s0 += q;
-            sr += q * MAP6_C2[k];
-            si += q * MAP6_S2[k];
-        }
-        const double h0 = 0.5 * (s0 * s0 + sr * sr + si * si);
-        // gradient and Hessian in t: H = 4 (sg sg^T + mr mr^T + mi mi^T) + 4 Z^T diag(Dq) Z
-        double g[3] = {0, 0, 0}, Hm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        double sg[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+    for (int k = 0; k < 6; ++k) pbf[k] = (float)pbar[k];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const double dq = 0.5 * (s0 + MAP6_C2[k] * sr + MAP6_S2[k] * si);
-            const double gp = 4.0 * p[k] * dq;
+    for (int l = 0; l < 3; ++l) tf[l] = (float)t[l];
+    map6_newton<float>(pbf, (float)lb, (float)T, tf, wmask, nw, 30, 1e-5f, 1e-4f, 1e-5f);
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                const double z = MAP6_Z[k][l];
-                g[l] += z * gp;
-                sg[l] += p[k] * z;
-                mr[l] += MAP6_C2[k] * p[k] * z;
-                mi[l] += MAP6_S2[k] * p[k] * z;
-#pragma unroll
-                for (int m = 0; m <= l; ++m) Hm[l][m] += 4.0 * dq * z * MAP6_Z[k][m];
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int m = 0; m <= l; ++m) {
-                Hm[l][m] += 4.0 * (sg[l] * sg[m] + mr[l] * mr[m] + mi[l] * mi[m]);
-                Hm[m][l] = Hm[l][m];
-            }
-        // the first two bounds of the working set, and an orthonormal basis N of
-        // the directions that keep them
-        double za[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
-        int seen = 0;
+    for (int l = 0; l < 3; ++l) t[l] = (double)tf[l];
+    if (nw > 0) {  // onto the face of the working set exactly: p_k = lb for its bounds (least-norm change of t)
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[3] = {0, 0, 0}, mu[3] = {0, 0, 0};
+        int idx[3] = {0, 0, 0}, a = 0;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             if ((wmask >> k) & 1) {
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    if (seen == 0) za[l] = MAP6_Z[k][l];
-                    if (seen == 1) zb[l] = MAP6_Z[k][l];
-                }
-                ++seen;
+                if (a < 3) idx[a] = k;
+                ++a;
             }
-        const int d = 3 - nw;
-        double N[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-        if (nw == 1) {
-            const double zn = sqrt(za[0] * za[0] + za[1] * za[1] + za[2] * za[2]);
-            const double n1[3] = {za[0] / zn, za[1] / zn, za[2] / zn};
-            // u: the unit vector of the smallest component of n1, made orthogonal to n1
-            double u[3] = {0, 0, 0};
-            const int e = (fabs(n1[1]) < fabs(n1[0])) ? ((fabs(n1[2]) < fabs(n1[1])) ? 2 : 1)
-                                                         : ((fabs(n1[2]) < fabs(n1[0])) ? 2 : 0);
-            const double dd = e == 0 ? n1[0] : (e == 1 ? n1[1] : n1[2]);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) u[l] = (l == e ? 1.0 : 0.0) - dd * n1[l];
-            const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) u[l] /= un;
-            const double v[3] = {n1[1] * u[2] - n1[2] * u[1], n1[2] * u[0] - n1[0] * u[2], n1[0] * u[1] - n1[1] * u[0]};
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                N[l][0] = u[l];
-                N[l][1] = v[l];
-            }
-        } else if (nw == 2) {
-            const double n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2],
-                                 za[0] * zb[1] - za[1] * zb[0]};
-            const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) N[l][0] = n[l] / nn;
+        double pc[6];
+        p_of_t(pbar, t, pc);
+        for (int i = 0; i < nw; ++i) {
+            rhs[i] = lb - pc[idx[i]];
+            for (int j = 0; j < nw; ++j)
+                G[i][j] = MAP6_Z[idx[i]][0] * MAP6_Z[idx[j]][0] + MAP6_Z[idx[i]][1] * MAP6_Z[idx[j]][1] +
+                          MAP6_Z[idx[i]][2] * MAP6_Z[idx[j]][2];
         }
-        double step[3] = {0, 0, 0}, dec = 0.0;
-        if (d > 0) {
-            double Hr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gr[3] = {0, 0, 0}, u[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a >= d) continue;
-#pragma unroll
-                for (int l = 0; l < 3; ++l) gr[a] -= N[l][a] * g[l];
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    if (b >= d) continue;
-                    double sab = 0.0;
-#pragma unroll
-                    for (int l = 0; l < 3; ++l)
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) sab += N[l][a] * Hm[l][m] * N[m][b];
-                    Hr[a][b] = sab;
-                }
-            }
-            if (!spd_solve(d, Hr, gr, u)) break;
-#pragma unroll
-            for (int l = 0; l < 3; ++l) step[l] = N[l][0] * u[0] + (d > 1 ? N[l][1] * u[1] : 0.0) +
-                                                  (d > 2 ? N[l][2] * u[2] : 0.0);
-            dec = -(g[0] * step[0] + g[1] * step[1] + g[2] * step[2]);
-        }
-        // converged on the face when the Newton step is at the rounding level of t
-        // (the decrement alone cannot tell: near the optimum it is rounding noise)
-        const double smax = fmax(fabs(step[0]), fmax(fabs(step[1]), fabs(step[2])));
-        if (d == 0 || dec <= 0.0 || smax <= 1e-12 * T) {
-            // converged on the face: bound multipliers from g = sum_{k in W} lambda_k z_k
-            if (nw == 0) return res;
-            double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[3] = {0, 0, 0}, lam[3] = {0, 0, 0};
-            int idx[3] = {0, 0, 0}, a = 0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
-                if ((wmask >> k) & 1) {
-                    if (a < 3) idx[a] = k;
-                    ++a;
-                }
-            for (int i = 0; i < nw; ++i) {
-                const int ki = idx[i];
-                rhs[i] = MAP6_Z[ki][0] * g[0] + MAP6_Z[ki][1] * g[1] + MAP6_Z[ki][2] * g[2];
-                for (int j2 = 0; j2 < nw; ++j2) {
-                    const int kj = idx[j2];
-                    G[i][j2] = MAP6_Z[ki][0] * MAP6_Z[kj][0] + MAP6_Z[ki][1] * MAP6_Z[kj][1] +
-                               MAP6_Z[ki][2] * MAP6_Z[kj][2];
-                }
-            }
-            if (!spd_solve(nw, G, rhs, lam)) return res;
-            int worst = -1;
-            const double gs = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
-            double lw = -1e-10 * (gs + 1e-300);
+        if (spd_solve(nw, G, rhs, mu))
             for (int i = 0; i < nw; ++i)
-                if (lam[i] < lw) {
-                    lw = lam[i];
-                    worst = idx[i];
-                }
-            if (worst < 0) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k)
-                    if ((wmask >> k) & 1) p[k] = lb;
-                return res;
-            }
-            wmask &= ~(1 << worst);
-            --nw;
-            continue;
-        }
-        // longest step along the Newton direction that keeps p >= lb
-        double amax = 1.0;
-        int blk = -1;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            if ((wmask >> k) & 1) continue;
-            const double dp = MAP6_Z[k][0] * step[0] + MAP6_Z[k][1] * step[1] + MAP6_Z[k][2] * step[2];
-            if (dp < 0.0) {
-                const double ak = fmax(p[k] - lb, 0.0) / (-dp);
-                if (ak < amax) {
-                    amax = ak;
-                    blk = k;
-                }
-            }
-        }
-        // backtracking (Armijo) while far from the optimum; near it the full Newton
-        // step converges quadratically and the test would only see rounding noise
-        double alpha = amax;
-        if (dec > 1e-10 * h0) {
-            for (int bt = 0; bt < 40; ++bt) {
-                const double tn[3] = {t[0] + alpha * step[0], t[1] + alpha * step[1], t[2] + alpha * step[2]};
-                double pn[6];
-                p_of_t(pbar, tn, pn);
-                if (kurt6(pn) <= h0 - 0.25 * alpha * dec) break;
-                alpha *= 0.5;
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < 3; ++l) t[l] += alpha * step[l];
-        if (blk >= 0 && alpha == amax && nw < 3) {
-            wmask |= 1 << blk;
-            ++nw;
-        }
+                for (int l = 0; l < 3; ++l) t[l] += mu[i] * MAP6_Z[idx[i]][l];
     }
+    map6_newton<double>(pbar, lb, T, t, wmask, nw, 60, 1e-12, 1e-10, 1e-10);
     p_of_t(pbar, t, p);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
