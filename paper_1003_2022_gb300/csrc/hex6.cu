@@ -15,17 +15,18 @@
 //   step 3: Eq. keyeqn, 64 taps of Eq. FD_mesh, F(y) = sum_m g[m] beta^6_b(y - m)
 //           with the element's exact polynomial pieces (hex6_tables.h, 24
 //           lattice points per tap).
-// Sixth-order running sums of a whole image outgrow FP64 (they grow like L^6
-// and the 64-tap difference cancels them), so each tile of 64 x 64 output
-// pixels gets its own window of the lattice, sized from the tile's largest
-// footprint.  The window is a parallelogram with sides along 0 and 150
+// Sixth-order running sums of a whole image outgrow any fixed word (they grow
+// like L^6 and the 64-tap difference cancels them), so each tile of output
+// pixels (64 x 64, 16 x 16 for small footprints, groups of up to 4 x 2 64-tiles
+// for large ones) gets its own window of the lattice, sized from the tile's
+// largest footprint, holding the running sums exactly as 128-bit integers.  The window is a parallelogram with sides along 0 and 150
 // degrees, stored row by row (row r = j - j0, column c = i - i_left + 2r): in
 // those coordinates every lattice direction has non-negative components, so
 // each running sum enters the window through its bottom or left side, where
 // the sums over the whole plane are zero, and the window's sums equal the
 // whole-plane ones.  The scale map for six directions (Sec. 3.2.2 with the
-// kurtosis norm written for N directions) is solved per pixel in FP64 by a
-// primal active-set Newton method.
+// kurtosis norm written for N directions) is solved per pixel by a primal
+// active-set Newton method, in FP32 first and to its end in FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -429,8 +430,8 @@ struct map6_result {
 };
 
 // the bound p_k >= 1e-3 T keeps the smallest width at least 0.077 times the
-// typical one: the 64-tap FP64 difference loses accuracy like the square of
-// that ratio for each width at the bound
+// typical one: the stencil's rounded (double-float) part loses accuracy like
+// the square of that ratio for each width at the bound
 constexpr double MAP6_REL_BOUND = 1e-3;
 
 // covariance (kind COV) or (sigma, rho, theta) (kind SRT) -> six scales; the
