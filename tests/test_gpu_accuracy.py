@@ -204,6 +204,6 @@ def test_batched_rgb_4096_workload_six_directions(accuracy_record):
                     mg.append(refs[-1])
                     mr.append(_direct6_on_crop(imgs[b, c], a[:, 0], y, x, definition=True))
     fig = _figures(np.array(gots), np.array(refs))
-    accuracy_record["b4c3_4096_f32_n6/fp64_hex"] = fig
+    accuracy_record["b4c3_4096_f32_n6/exact_hex"] = fig
     accuracy_record["b4c3_4096_f32_n6/method_error_vs_pixel_comb"] = _figures(np.array(mg), np.array(mr))
     assert fig["max_norm"] < TOL
