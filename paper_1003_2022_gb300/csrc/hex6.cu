@@ -602,7 +602,8 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
     u128* s120 = s90b + np;
     u128* wt = s120 + np;  // warp totals
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < 4 * np; k += PRE_THREADS) smq[k] = 0;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;  // a multiple of 32, at most PRE_THREADS
+    for (int k = tid; k < 4 * np; k += nthr) smq[k] = 0;
     const InT* f = img + ((size_t)tl.b * C + c) * (size_t)H * W;
     u128* G = scratch + tl.off + (long long)c * ncol * nrow;
     // The transfer weights need only single precision: an error in a mass is a
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
         if (lane == 31) wt[warp] = v;
         __syncthreads();
         // every warp scans the warp totals itself (no second barrier)
-        u128 wsum = lane < PRE_THREADS / 32 ? wt[lane] : (u128)0;
+        u128 wsum = lane < nwarp ? wt[lane] : (u128)0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const u128 u = shfl_up_T(wsum, o);
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
     __syncthreads();
     if (tid == 0) {
         unsigned bad = 0, qb = 0;
-        for (int k = 0; k < PRE_THREADS / 32; ++k) {
+        for (int k = 0; k < nwarp; ++k) {
             bad |= red[k];
             qb = max(qb, red[32 + k]);
         }
@@ -1046,14 +1047,18 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
                                int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st) {
     const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
+    // as many threads as the widest window of the chunk needs (PRE_CPT columns each, whole
+    // warps): narrow windows take small blocks, several of them per SM
+    if (ncol_max < 1 || ncol_max > PRE_THREADS * PRE_CPT) return cudaErrorInvalidValue;
+    const int nthr = ((ncol_max + PRE_CPT - 1) / PRE_CPT + 31) / 32 * 32;
     dim3 grid(ntiles, C);
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<uint8_t><<<grid, PRE_THREADS, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch,
+        k_hex6_preint<uint8_t><<<grid, nthr, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch,
                                                                  wflag);
     } else {
         cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hex6_preint<float><<<grid, PRE_THREADS, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch,
+        k_hex6_preint<float><<<grid, nthr, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch,
                                                                wflag);
     }
     return cudaGetLastError();
