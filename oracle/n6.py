@@ -487,7 +487,7 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
     four-directional map, except the lower bound: p_k >= max(eps, 1e-3 T),
     T = sum_k p_k = 12 tr C (reading: the bound of Eq. opt1 is any small
     positive number; taken relative to the size, it keeps the smallest width
-    at least 0.077 times the typical one, which the FP64 six-directional path
+    at least 0.077 times the typical one, which the six-directional GPU path
     needs for its accuracy).  Elongations beyond the bound U of that
     constraint (U_boundN with the hexagon scaled by 1 - 6e-3) are lowered to
     (1 - eta) U keeping lmax + lmin and the orientation (flag 1); when no
