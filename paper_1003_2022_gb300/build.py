@@ -19,7 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbsf.so")
-SOURCES = ["bsf_api.cu", "scan4.cu", "stencil4.cu", "noalloc.cu", "adjoint4.cu", "adaptive.cu", "hex6.cu"]
+SOURCES = ["bsf_api.cu", "scan4.cu", "stencil4.cu", "noalloc.cu", "adjoint4.cu", "adaptive.cu", "hex6.cu",
+           "hex6_plan.cpp"]
 HEADERS = ["bsf_common.cuh", "bsf_internal.h", "map4.cuh", "hex6_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

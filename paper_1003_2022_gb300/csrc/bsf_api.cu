@@ -403,9 +403,7 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
 static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
                           const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
                           float ascale = 1.f) {
-    const int fine = 16, coarse = 64, ratio = coarse / fine;
-    const float split_below = 16.f;  // px: largest half-extent for which a 64-tile is cut into 16-tiles
-    const float group_from = 32.f;   // px: smallest half-extent of a 64-tile that joins a group
+    const int fine = 16;
     const double h = (double)o.hex_spacing;
     const int64_t HW = H * W;
     const int fx = (int)((W + fine - 1) / fine), fy = (int)((H + fine - 1) / fine);
@@ -420,108 +418,12 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     std::vector<unsigned> ext((size_t)B * nfine * 2);
     BSF_TRY(cudaMemcpyAsync(ext.data(), c->h6_ext, ext_bytes, cudaMemcpyDeviceToHost, st));
     BSF_TRY(cudaStreamSynchronize(st));
-    auto ext_of = [&](int64_t b, int bx, int by, float* ex, float* ey) {
-        const size_t t = (size_t)(b * nfine + (int64_t)by * fx + bx) * 2;
-        memcpy(ex, &ext[t], sizeof(float));
-        memcpy(ey, &ext[t + 1], sizeof(float));
-    };
-    // Tile records, one launch shape per class.  A window spans its tile plus
-    // the footprint, sheared into a parallelogram (a row of the window is as
-    // wide as the tile, twice the footprint, and sqrt(3) times the window's
-    // height), so neighbouring 64-tiles with large footprints share one window:
-    // groups of 4 x 2, 4 x 1 and 2 x 1 aligned 64-tiles (256 x 128, 256 x 64,
-    // 128 x 64 pixels) are taken, largest first, where every tile of the group
-    // has a footprint half-extent of at least group_from and at least half the
-    // group's largest (a group's window is no larger, for the kernels of any
-    // of its tiles, than a few times the tile's own: the conditioning of the
-    // stencil grows with the window) and the window fits the
-    // pre-integration's width; then single 64-tiles; tiles with small
-    // footprints are cut into 16-tiles.
-    static const int group[4][2] = {{4, 2}, {4, 1}, {2, 1}, {1, 1}};
-    std::vector<hex6_tile> cls[5];
-    const int cx = (int)((W + coarse - 1) / coarse), cy = (int)((H + coarse - 1) / coarse);
-    std::vector<float> e64((size_t)cx * cy * 2);
-    std::vector<unsigned char> taken((size_t)cx * cy);
-    for (int64_t b = 0; b < B; ++b) {
-        for (int ty = 0; ty < cy; ++ty)
-            for (int tx = 0; tx < cx; ++tx) {
-                float ex = 0.f, ey = 0.f;
-                for (int by = ty * ratio; by < std::min(fy, (ty + 1) * ratio); ++by)
-                    for (int bx = tx * ratio; bx < std::min(fx, (tx + 1) * ratio); ++bx) {
-                        float a, e;
-                        ext_of(b, bx, by, &a, &e);
-                        ex = std::max(ex, a);
-                        ey = std::max(ey, e);
-                    }
-                if (!(ex >= 0.f && ey >= 0.f && ex < 1e5f && ey < 1e5f)) return BSF_EINVAL;
-                e64[((size_t)ty * cx + tx) * 2] = ex;
-                e64[((size_t)ty * cx + tx) * 2 + 1] = ey;
-            }
-        std::fill(taken.begin(), taken.end(), 0);
-        for (int g = 0; g < 4; ++g) {
-            const int gw = group[g][0], gh = group[g][1];
-            for (int ty = 0; ty + gh <= cy; ty += gh)
-                for (int tx = 0; tx + gw <= cx; tx += gw) {
-                    float ex = 0.f, ey = 0.f, lo = 1e30f, hi = 0.f;
-                    bool free = true;
-                    for (int yy = ty; yy < ty + gh; ++yy)
-                        for (int xx = tx; xx < tx + gw; ++xx) {
-                            const size_t k = (size_t)yy * cx + xx;
-                            free = free && !taken[k];
-                            ex = std::max(ex, e64[2 * k]);
-                            ey = std::max(ey, e64[2 * k + 1]);
-                            lo = std::min(lo, std::max(e64[2 * k], e64[2 * k + 1]));
-                            hi = std::max(hi, std::max(e64[2 * k], e64[2 * k + 1]));
-                        }
-                    if (!free || lo < (g < 3 ? group_from : split_below) || (g < 3 && lo < 0.5f * hi)) continue;
-                    hex6_tile t;
-                    hex6_window(tx * coarse, ty * coarse, gw * coarse, gh * coarse, (int)H, (int)W, ex, ey, h, &t);
-                    if (g < 3 && t.ncol > hex6_max_cols()) continue;  // too wide: smaller groups
-                    t.b = (int)b;
-                    cls[g].push_back(t);
-                    for (int yy = ty; yy < ty + gh; ++yy)
-                        for (int xx = tx; xx < tx + gw; ++xx) taken[(size_t)yy * cx + xx] = 1;
-                }
-        }
-        for (int ty = 0; ty < cy; ++ty)
-            for (int tx = 0; tx < cx; ++tx) {
-                if (taken[(size_t)ty * cx + tx]) continue;
-                for (int by = ty * ratio; by < std::min(fy, (ty + 1) * ratio); ++by)
-                    for (int bx = tx * ratio; bx < std::min(fx, (tx + 1) * ratio); ++bx) {
-                        float a, e;
-                        ext_of(b, bx, by, &a, &e);
-                        hex6_tile t;
-                        hex6_window(bx * fine, by * fine, fine, fine, (int)H, (int)W, a, e, h, &t);
-                        t.b = (int)b;
-                        cls[4].push_back(t);
-                    }
-            }
-    }
     std::vector<hex6_tile> tl;
-    for (auto& v : cls) tl.insert(tl.end(), v.begin(), v.end());
-    // chunks of one tile shape, at most 8 GiB of windows (enough windows of
-    // the largest footprints for several blocks on every SM) and 65535 tiles
-    // (a grid dimension)
-    const size_t budget = (size_t)8 << 30;
-    struct chunk {
-        size_t first, last;
-        int cols;
-        size_t bytes;
-    };
-    std::vector<chunk> chunks;
-    for (size_t t = 0; t < tl.size(); ++t) {
-        if (tl[t].ncol > hex6_max_cols()) return BSF_EINVAL;  // footprint too wide for one window
-        const size_t bytes = (size_t)C * tl[t].ncol * tl[t].nrow * 16;
-        if (bytes > budget) return BSF_EINVAL;
-        if (chunks.empty() || tl[t].w != tl[chunks.back().first].w || tl[t].hh != tl[chunks.back().first].hh ||
-            chunks.back().bytes + bytes > budget || t - chunks.back().first >= 65535)
-            chunks.push_back({t, t, 0, 0});
-        chunk& ch = chunks.back();
-        tl[t].off = (long long)(ch.bytes / 16);
-        ch.bytes += bytes;
-        ch.last = t + 1;
-        ch.cols = std::max(ch.cols, tl[t].ncol);
-    }
+    std::vector<hex6_chunk> chunks;
+    // chunks of at most 8 GiB of windows: enough windows of the largest
+    // footprints for several blocks of the pre-integration on every SM
+    const bsf_status ps = hex6_plan(B, C, H, W, h, ext.data(), (size_t)8 << 30, tl, chunks);
+    if (ps != BSF_OK) return ps;
     size_t win = 0;
     for (auto& ch : chunks) win = std::max(win, ch.bytes);
     if (tl.empty()) return BSF_OK;
@@ -533,7 +435,7 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     BSF_TRY(cudaMemcpyAsync(c->h6_tiles, tl.data(), tl.size() * sizeof(hex6_tile), cudaMemcpyHostToDevice, st));
     const hex6_tile* dt = (const hex6_tile*)c->h6_tiles;
     for (size_t i = 0; i < chunks.size(); ++i) {
-        const chunk& ch = chunks[i];
+        const hex6_chunk& ch = chunks[i];
         const int n = (int)(ch.last - ch.first);
         BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
                                    c->h6_win, (unsigned*)c->h6_flag, st));

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct scan_plan {
     int band_h;         // rows per band
     int nb;             // bands per image
@@ -66,11 +68,13 @@ cudaError_t launch_fill(float* p, size_t n, float v, cudaStream_t st);
 cudaError_t launch_adaptive_cov(const float* J, long long HW, int B, float s0sq, float tau, float* cov,
                                 cudaStream_t st);
 
-// Six-directional filter on the hexagonal lattice (hex6.cu).
+// Six-directional filter on the hexagonal lattice (hex6.cu; planning in hex6_plan.cpp).
 // One lattice window per (batch entry, output tile of 64 x 64 pixels; 16 x 16
-// where the footprints are small, 256 x 64 where four neighbouring 64-tiles all
-// have large footprints); channel c of the tile's image has its
-// window at off + c * ncol * nrow elements (exact 128-bit running sums).
+// where the footprints are small; groups of 2 x 1, 4 x 1 or 4 x 2 64-tiles where
+// they are large); channel c of the tile's image has its window at
+// off + c * ncol * nrow elements (exact 128-bit running sums).
+constexpr int HEX6_PRE_THREADS = 512;  // largest block of the pre-integration
+constexpr int HEX6_PRE_CPT = 8;        // window columns per pre-integration thread
 struct hex6_tile {
     long long off;   // 16-byte elements from the chunk's window base
     int i_left;      // lattice column i of storage column 0 in row 0
@@ -78,10 +82,22 @@ struct hex6_tile {
     int ncol, nrow;  // storage size; column c of row r is lattice point (c + i_left - 2 r, j0w + r)
     int b;           // batch entry
     int x0, y0;      // first output pixel of the tile
-    int w, hh;       // tile shape in pixels: 16 x 16, 64 x 64 or 256 x 64
+    int w, hh;       // tile shape in pixels: 16 x 16, or 64, 128, 256 x 64, 128
+};
+// a run of tiles of one shape whose windows share one buffer
+struct hex6_chunk {
+    size_t first, last;  // tiles [first, last) of the plan
+    int cols;            // widest window
+    size_t bytes;        // windows of all channels
 };
 void hex6_window(int x0, int y0, int w, int hh, int H, int W, double ex, double ey, double h, hex6_tile* t);
 int hex6_max_cols();
+// tile records and chunks (at most `budget` bytes of windows and 65535 tiles,
+// one tile shape each) from the largest footprint half-extents of every 16 x 16
+// block: ext holds B * ceil(H/16) * ceil(W/16) pairs (ex, ey) as FP32 bits.
+// BSF_EINVAL: an extent not finite or above 1e5 px, or a window too wide.
+int hex6_plan(int64_t B, int64_t C, int64_t H, int64_t W, double h, const unsigned* ext, size_t budget,
+              std::vector<hex6_tile>& tiles, std::vector<hex6_chunk>& chunks);
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st);
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, float* scales,

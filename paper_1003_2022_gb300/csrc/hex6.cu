@@ -562,8 +562,8 @@ __global__ void k_map6_out(const float* __restrict__ params, int kind, long long
     if (flags) flags[p] = (uint8_t)R.flag;
 }
 
-constexpr int PRE_THREADS = 512;
-constexpr int PRE_CPT = 8;  // window columns per thread
+constexpr int PRE_THREADS = HEX6_PRE_THREADS;
+constexpr int PRE_CPT = HEX6_PRE_CPT;  // window columns per thread
 constexpr int MU_FRAC_BITS = 24;  // fixed point of the transferred masses
 
 // step 2 on one window: transfer of the image and the six running sums, row by
@@ -990,43 +990,6 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
 
 }  // namespace
 
-// geometry of the window of one tile: every lattice point that the taps of
-// its pixels read (host side; ex, ey = the tile's largest footprint half-extents)
-void hex6_window(int tx0, int ty0, int tw, int th_, int H, int W, double ex, double ey, double h, hex6_tile* t) {
-    const double SQ3 = 1.7320508075688772935;
-    const int x0 = tx0, x1 = std::min(W, tx0 + tw) - 1;
-    const int y0 = ty0, y1 = std::min(H, ty0 + th_) - 1;
-    // taps: n + tau - x_q, in n + [-ex, ex] x [-ey, ey] - (h/2, 3 sqrt3 h / 2)
-    const double xl = x0 - ex - 0.5 * h, xh = x1 + ex - 0.5 * h;
-    const double yl = y0 - ey - 1.5 * SQ3 * h, yh = y1 + ey - 1.5 * SQ3 * h;
-    const double tl = 2.0 * yl / (h * SQ3), th = 2.0 * yh / (h * SQ3);
-    const int j0 = (int)floor(tl) - 4, j1 = (int)floor(th) + 5;
-    t->j0w = j0;
-    t->nrow = j1 - j0 + 1;
-    // row j is read by taps with t in [j - 3, j + 3); their cells' columns i0 run
-    // over floor(x/h - t/2) and the slots reach i0 - 2 .. i0 + 3
-    long long ileft = (1LL << 40), ncol = 0;
-    for (int r = 0; r < t->nrow; ++r) {
-        const int j = j0 + r;
-        const long long imin = (long long)floor(xl / h - 0.5 * (j + 3)) - 4;
-        ileft = std::min(ileft, imin + 2LL * r);
-    }
-    for (int r = 0; r < t->nrow; ++r) {
-        const int j = j0 + r;
-        const long long imax = (long long)floor(xh / h - 0.5 * (j - 3)) + 5;
-        ncol = std::max(ncol, imax - (ileft - 2LL * r) + 1);
-    }
-    t->i_left = (int)ileft;
-    t->ncol = (int)ncol;
-    t->x0 = tx0;
-    t->y0 = ty0;
-    t->w = tw;
-    t->hh = th_;
-}
-
-// widest window: PRE_CPT columns per thread, and four 128-bit state rows plus the
-// warp totals in 227 KB of shared memory
-int hex6_max_cols() { return std::min(PRE_THREADS * PRE_CPT, (232448 - 32 * 16) / (4 * 16) * PRE_CPT / (PRE_CPT + 1) - 8); }
 
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st) {
