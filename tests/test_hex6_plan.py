@@ -164,3 +164,39 @@ def test_plan_rejects_bad_extents(lib):
     # a window wider than the pre-integration holds
     e = np.full((1, 7, 7, 2), 900.0, np.float32)
     assert _plan(lib, 1, 1, H, W, 0.5, e, 1 << 30)[0] == 1
+
+
+def _six_sums(mu):
+    """The pre-integration's six running sums in a window's storage coordinates
+    (row r, column c; the directions' backward steps in (rows, columns) are
+    0: (0, 1), 30: (1, 3), 60: (1, 2), 90: (2, 3), 120: (1, 1), 150: (1, 0)),
+    nested in that order as the kernel nests them, in exact integers."""
+    S = np.array(mu, dtype=object)
+    for dr, dc in ((0, 1), (1, 3), (1, 2), (2, 3), (1, 1), (1, 0)):
+        T = S.copy()
+        nrow, ncol = S.shape
+        for r in range(nrow):
+            for c in range(ncol):
+                if r >= dr and c >= dc and (dr or dc):
+                    T[r, c] = S[r, c] + T[r - dr, c - dc]
+        S = T
+    return S
+
+
+def test_range_bound_of_the_window_sums():
+    """The bound the pre-integration tests against 2^126 (no running sum can have
+    wrapped 128 bits): |partial sums| <= max |mass| * ncol * n30 * n60 * n90 *
+    n120 * nrow, with n_k the longest line of direction k in the window.  Exact
+    sums of constant and sign-alternating masses stay within it, and the
+    constant case comes within a modest factor of it."""
+    for nrow, ncol in ((7, 11), (12, 30), (20, 9)):
+        n30 = min(nrow - 1, (ncol - 1) // 3) + 1
+        n60 = min(nrow - 1, (ncol - 1) // 2) + 1
+        n90 = min((nrow - 1) // 2, (ncol - 1) // 3) + 1
+        n120 = min(nrow - 1, ncol - 1) + 1
+        bound = ncol * n30 * n60 * n90 * n120 * nrow
+        ones = _six_sums(np.ones((nrow, ncol), dtype=object))
+        alt = _six_sums(np.fromfunction(lambda r, c: (-1) ** (r + c), (nrow, ncol), dtype=int).astype(object))
+        top = max(abs(v) for v in ones.ravel())
+        assert top <= bound and max(abs(v) for v in alt.ravel()) <= bound
+        assert top * 1000 >= bound
