@@ -237,7 +237,7 @@ bsf_status bsf_profile_end(bsf_ctx* c, double* ms_pre, double* ms_st, int* nlaun
 }
 
 bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, int precision, size_t* bytes) {
-    if (!bytes || H <= 0 || W <= 0 || halo < 2) return BSF_EINVAL;
+    if (!bytes || H <= 0 || W <= 0 || halo < 2 || halo > kMaxHalo) return BSF_EINVAL;
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (precision != BSF_PREC_EXACT && precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (N != 4) return BSF_EUNSUPPORTED;
@@ -278,6 +278,7 @@ bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_
 static bsf_status resolve_halo(bsf_ctx* c, const float* params, int kind, int64_t nfield, int64_t HW, const bsf_opts& o,
                                cudaStream_t st, int* P) {
     if (o.halo > 0) {
+        if (o.halo > kMaxHalo) return BSF_EINVAL;
         *P = o.halo;
         return BSF_OK;
     }
@@ -723,7 +724,7 @@ bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t
 
 bsf_status bsf_preintegrate(bsf_ctx* c, const void* image, int dtype, int64_t H, int64_t W, int N, int halo,
                             int precision, void* buffer, void* stream) {
-    if (!c || !image || !buffer || !dims_ok(H, W) || halo < 2) return BSF_EINVAL;
+    if (!c || !image || !buffer || !dims_ok(H, W) || halo < 2 || halo > kMaxHalo) return BSF_EINVAL;
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (precision != BSF_PREC_EXACT && precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (N != 4) return BSF_EUNSUPPORTED;
@@ -741,7 +742,7 @@ bsf_status bsf_preintegrate(bsf_ctx* c, const void* image, int dtype, int64_t H,
 
 bsf_status bsf_apply(bsf_ctx* c, const void* buffer, int dtype, int64_t H, int64_t W, int N, int halo,
                      const float* params, int kind, const bsf_opts* opts, float* out, void* stream) {
-    if (!c || !buffer || !params || !out || !dims_ok(H, W) || halo < 2) return BSF_EINVAL;
+    if (!c || !buffer || !params || !out || !dims_ok(H, W) || halo < 2 || halo > kMaxHalo) return BSF_EINVAL;
     if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
     if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
     if (N != 4) return BSF_EUNSUPPORTED;

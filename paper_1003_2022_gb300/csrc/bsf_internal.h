@@ -17,6 +17,10 @@ struct scan_plan {
     bool ok;            // false: the row is too wide for one CTA
 };
 
+// largest halo (padding of the pre-integrated buffer, px) any entry point accepts: with
+// H, W <= 2^20 the padded sizes and byte counts then stay far inside int and size_t
+constexpr int kMaxHalo = 1 << 20;
+
 scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes);
 // widest buffer row one band CTA holds; narrow: the width at which the 128-bit
 // form keeps four columns per thread (chosen for batches of several waves)

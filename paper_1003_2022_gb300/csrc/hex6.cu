@@ -1015,12 +1015,17 @@ cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int 
     if (ncol_max < 1 || ncol_max > PRE_THREADS * PRE_CPT) return cudaErrorInvalidValue;
     const int nthr = ((ncol_max + PRE_CPT - 1) / PRE_CPT + 31) / 32 * 32;
     dim3 grid(ntiles, C);
+    // the attribute is the kernel's largest shared-memory size (set on every launch, the
+    // same value each time: launches from several host threads never lower it for another);
+    // each launch still asks only for its chunk's size
+    const int smem_cap = (int)((4 * (size_t)(hex6_max_cols() + hex6_max_cols() / PRE_CPT + 1) + 32) * sizeof(u128));
+    if ((int)smem > smem_cap) return cudaErrorInvalidValue;
     if (dtype_u8) {
-        cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
         k_hex6_preint<uint8_t><<<grid, nthr, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch,
                                                                  wflag);
     } else {
-        cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
         k_hex6_preint<float><<<grid, nthr, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch,
                                                                wflag);
     }

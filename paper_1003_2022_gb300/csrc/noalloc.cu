@@ -43,6 +43,7 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     if (N != 4) return BSF_EUNSUPPORTED;
     // the halo must come from the options (no device reduction, which would need a result word)
     int P = opts->halo;
+    if (P > kMaxHalo) return BSF_EINVAL;
     if (P <= 0) {
         if (!(opts->max_scale > 0.f) || opts->max_scale > 1e5f) return BSF_EINVAL;
         const float ext = (kind == BSF_PARAM_SCALES) ? 2.41422f * opts->max_scale : 8.3640f * opts->max_scale;
@@ -50,7 +51,9 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     }
     const int mode = opts->precision == BSF_PREC_FP64 ? MODE_F64 : (dtype == BSF_U8 ? MODE_U64 : MODE_U128);
     const size_t esz = mode == MODE_U128 ? 16 : 8;
-    const int64_t Hp = H + 2 * (int64_t)P, Wp = W + 2 * (int64_t)P;
+    const int64_t Hp = H + 2 * (int64_t)P, Wp = W + 2 * (int64_t)P;  // at most 3 * 2^20 each
+    // the buffer alone already beyond the scratch: reject before planning the scan
+    if ((uint64_t)Hp * (uint64_t)Wp * esz > (uint64_t)BSF_NOALLOC_SCRATCH_BYTES) return BSF_ENOSCRATCH;
     const scan_plan plan = make_scan_plan((int)Hp, (int)Wp, 1, esz);
     const size_t buf_bytes = round_up256((size_t)(Hp * Wp) * esz);
     if (buf_bytes + plan.work_bytes > (size_t)BSF_NOALLOC_SCRATCH_BYTES) return BSF_ENOSCRATCH;

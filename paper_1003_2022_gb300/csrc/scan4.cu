@@ -381,11 +381,9 @@ static void launch_band(const scan_plan& p, const InT* img, long long img_stride
                         int P, int Hp, int Wp, int pitch, const void* carry, void* local, void* G, long long G_stride,
                         cudaStream_t st) {
     typedef typename mode_traits<MODE>::T T;
-    static bool attr_set = false;  // per instantiation: allow up to 96 KiB of g2 state
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr_set = true;
-    }
+    // allow up to 96 KiB of g2 state; the attribute belongs to the current device, so it is
+    // set on every launch (a cheap host call) rather than once per process
+    cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     dim3 grid(p.nb, nimg);
     k_band<MODE, InT, CPT><<<grid, p.threads, p.smem, st>>>(img, img_stride, H, W, col0, P, Hp, Wp, pitch, p.band_h, p.nb,
                                                         (const T*)carry, (T*)local, (T*)G, G_stride);

@@ -64,3 +64,26 @@ def test_python_binding_refuses_to_run_without_library(tmp_path, lib):
             mod.load(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_halo_bounds_rejected_before_any_device_call(lib):
+    """A halo beyond the library's bound, or an image whose buffer exceeds the
+    fixed scratch of the allocation-free entry point, is an argument error
+    returned on the host: nothing is planned or launched (a huge halo once
+    overflowed the padded size and divided by zero in the scan planner)."""
+    o = lib.default_opts()
+    o.halo = 2 ** 31 - 1
+    dummy = 16  # non-null pointers that are never dereferenced
+    assert lib.bsf_filter_noalloc(dummy, lib.BSF_U8, 2, 2, 4, dummy, lib.BSF_PARAM_SCALES, o, dummy, 0) \
+        == lib.BSF_EINVAL
+    o.halo = 1 << 20
+    assert lib.bsf_filter_noalloc(dummy, lib.BSF_U8, 1 << 20, 1 << 20, 4, dummy, lib.BSF_PARAM_SCALES, o, dummy,
+                                  0) == lib.BSF_ENOSCRATCH
+    o.halo = 4
+    assert lib.bsf_filter_noalloc(dummy, lib.BSF_F32, 4096, 4096, 4, dummy, lib.BSF_PARAM_SCALES, o, dummy, 0) \
+        == lib.BSF_ENOSCRATCH
+    with pytest.raises(lib.BsfError) as e:
+        lib.bsf_buffer_bytes(lib.BSF_U8, 10, 20, 4, (1 << 20) + 1, lib.BSF_PREC_EXACT)
+    assert e.value.code == lib.BSF_EINVAL
+    assert lib.bsf_buffer_bytes(lib.BSF_U8, 1 << 20, 1 << 20, 4, 1 << 20, lib.BSF_PREC_EXACT) \
+        == (3 << 20) * (3 << 20) * 8
