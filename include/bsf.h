@@ -125,6 +125,13 @@ typedef struct {
     float hex_spacing;  /* N = 6 only: spacing h (px) of the hexagonal lattice the image is
                          transferred to: 1, 0.5 (default), 0.25 or 0.125.  The method error of
                          the transfer falls like h^2, the pre-integration work grows like 1/h^2. */
+    float rel_bound;  /* N = 6 only: the map's lower bound on each p_k = a_k^2 relative to the
+                         trace T = sum_k p_k: p_k >= max(eps, rel_bound * T), and elongations are
+                         bounded by the hexagon of the six directions scaled by 1 - 6 rel_bound.
+                         Default 1e-3 (no width below 0.077 times the typical one); must lie in
+                         [0, 1/6).  The 1e-5 accuracy of the six-directional path is stated for
+                         the default: 0 leaves only eps, whose tiny widths cost the stencil's
+                         rounded part accuracy (BSF_EINVAL outside the range). */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -63,7 +63,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -93,8 +93,15 @@ def _load():
                                 _dp, _u8p]
         lib.bo_U_bound.restype = ctypes.c_double
         lib.bo_U_bound.argtypes = [ctypes.c_double]
+        lib.bo_num_threads.restype = ctypes.c_int
+        lib.bo_num_threads.argtypes = []
         _lib = lib
     return _lib
+
+
+def num_threads() -> int:
+    """Host threads the oracle's parallel loops use (OpenMP; OMP_NUM_THREADS caps it)."""
+    return int(_load().bo_num_threads())
 
 
 def _d(x):

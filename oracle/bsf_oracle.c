@@ -26,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define SQRT2 1.41421356237309504880
 #define INV_SQRT2 0.70710678118654752440
@@ -153,6 +156,8 @@ void bo_direct4(const double* f, int H, int W, const double* a, const int64_t* i
                 double* out) {
     const int64_t HW = (int64_t)H * W;
     const int64_t count = npix < 0 ? HW : npix;
+    /* pixels are independent: shared among the host threads */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < count; ++t) {
         const int64_t p = npix < 0 ? t : idx[t];
         const int n2 = (int)(p / W), n1 = (int)(p % W);
@@ -187,6 +192,7 @@ void bo_adjoint4(const double* g, int H, int W, const double* a, double amax, co
                  double* out) {
     const int64_t HW = (int64_t)H * W;
     const int R = (int)ceil(0.5 * (amax + SQRT2 * amax)) + 2;
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < npts; ++t) {
         const int k2 = (int)(idx[t] / W), k1 = (int)(idx[t] % W);
         double s = 0;
@@ -225,21 +231,30 @@ void bo_preint4_i64(const int64_t* f, int H, int W, int P, int64_t* Gout) {
     uint64_t* g90 = (uint64_t*)calloc(n, 8);
     uint64_t* G = (uint64_t*)calloc(n, 8);
 #define AT(A, c, r) A[(int64_t)(r) * Wp + (c)]
+    /* RS1 runs along rows (rows independent); RS2-RS4 step from row r-1 to row r
+       (the columns of one row independent) */
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < Hp; ++r)
         for (int c = 0; c < Wp; ++c) {
             uint64_t fv = 0;
             if (r >= P && r < P + H && c >= P && c < P + W) fv = (uint64_t)f[(int64_t)(r - P) * W + (c - P)];
             AT(g0, c, r) = fv + (c > 0 ? AT(g0, c - 1, r) : 0);
         }
-    for (int r = 0; r < Hp; ++r)
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < Wp; ++c)
             AT(g45, c, r) = AT(g0, c, r) + (c > 0 && r > 0 ? AT(g45, c - 1, r - 1) : 0);
-    for (int r = 0; r < Hp; ++r)
+    }
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < Wp; ++c)
             AT(g90, c, r) = AT(g45, c, r) + (r > 0 ? AT(g90, c, r - 1) : 0);
-    for (int r = 0; r < Hp; ++r)
+    }
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = Wp - 1; c >= 0; --c)
             AT(G, c, r) = AT(g90, c, r) + (c + 1 < Wp && r > 0 ? AT(G, c + 1, r - 1) : 0);
+    }
     memcpy(Gout, G, n * 8);
     free(g0); free(g45); free(g90); free(G);
 }
@@ -251,21 +266,28 @@ void bo_preint4_f64(const double* f, int H, int W, int P, double* gbout) {
     double* g45 = (double*)calloc(n, 8);
     double* g90 = (double*)calloc(n, 8);
     double* gb = gbout;
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < Hp; ++r)
         for (int c = 0; c < Wp; ++c) {
             double fv = 0;
             if (r >= P && r < P + H && c >= P && c < P + W) fv = f[(int64_t)(r - P) * W + (c - P)];
             AT(g0, c, r) = fv + (c > 0 ? AT(g0, c - 1, r) : 0);
         }
-    for (int r = 0; r < Hp; ++r)
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < Wp; ++c)
             AT(g45, c, r) = SQRT2 * AT(g0, c, r) + (c > 0 && r > 0 ? AT(g45, c - 1, r - 1) : 0);
-    for (int r = 0; r < Hp; ++r)
+    }
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < Wp; ++c)
             AT(g90, c, r) = AT(g45, c, r) + (r > 0 ? AT(g90, c, r - 1) : 0);
-    for (int r = 0; r < Hp; ++r)
+    }
+    for (int r = 0; r < Hp; ++r) {
+#pragma omp parallel for schedule(static)
         for (int c = Wp - 1; c >= 0; --c)
             AT(gb, c, r) = SQRT2 * AT(g90, c, r) + (c + 1 < Wp && r > 0 ? AT(gb, c + 1, r - 1) : 0);
+    }
     free(g0); free(g45); free(g90);
 #undef AT
 }
@@ -291,6 +313,7 @@ int64_t bo_stencil4(const double* gb, int H, int W, int P, const double* a, cons
     const double bvec[4] = {1.0, SQRT2, 1.0, SQRT2};
     const int64_t count = npix < 0 ? HW : npix;
     int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
     for (int64_t t = 0; t < count; ++t) {
         const int64_t p = npix < 0 ? t : idx[t];
         const int n2 = (int)(p / W), n1 = (int)(p % W);
@@ -401,6 +424,7 @@ static int cubic_real_roots(double c0, double c1, double c2, double c3, double r
 int bo_map4(const double* params, int kind, int64_t npix, double eps, double eta, double* a_out,
             uint8_t* flags) {
     const double PI = 3.14159265358979323846;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t p = 0; p < npix; ++p) {
         double C11, C12, C22;
         uint8_t flag = 0;
@@ -484,4 +508,13 @@ int bo_map4(const double* params, int kind, int64_t npix, double eps, double eta
         if (flags) flags[p] = flag;
     }
     return 0;
+}
+
+/* Number of host threads the parallel loops above use (1 without OpenMP). */
+int bo_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -481,7 +481,7 @@ def _cov_from_params(v0, v1, v2, kind):
 REL_BOUND6 = 1e-3
 
 
-def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
+def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3, rel_bound: float = REL_BOUND6):
     """Per-pixel scales for N = 6 from covariance planes (kind 1) or (sigma,
     rho, theta) planes (kind 2), shape (3, ...).  The same conventions as the
     four-directional map, except the lower bound: p_k >= max(eps, 1e-3 T),
@@ -493,6 +493,8 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
     (1 - eta) U keeping lmax + lmin and the orientation (flag 1); when no
     p >= bound reproduces the covariance, the minimiser over p >= 0 is raised
     to the bound (flag 2); invalid input gives NaN scales (flag 4).
+    ``rel_bound`` replaces the share 1e-3 of the trace (0: the bound is eps
+    alone, the paper's form of the constraint; the hexagon is then unscaled).
     Returns (a of shape (6, ...), flags uint8)."""
     P = np.asarray(params, float)
     shp = P.shape[1:]
@@ -508,7 +510,7 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
             flags[p] = FLAG_INVALID
             continue
         fl = 0
-        U = U_boundN(th, 6, 1.0 - 6.0 * REL_BOUND6)
+        U = U_boundN(th, 6, 1.0 - 6.0 * rel_bound)
         if lmax / lmin > (1.0 - eta) * U:
             s = lmax + lmin
             lmin = s / (1.0 + (1.0 - eta) * U)
@@ -520,7 +522,7 @@ def map6(params, kind: int, eps: float = 1e-3, eta: float = 1e-3):
             m, d = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
             C = np.array([[m + d * math.cos(2 * th), d * math.sin(2 * th)],
                           [d * math.sin(2 * th), m - d * math.cos(2 * th)]])
-        bound = max(eps, REL_BOUND6 * 12.0 * (C[0, 0] + C[1, 1]))
+        bound = max(eps, rel_bound * 12.0 * (C[0, 0] + C[1, 1]))
         pk, ok = mapN_kkt(th6, C, bound)
         if not ok:
             pk, ok = mapN_kkt(th6, C, 0.0)

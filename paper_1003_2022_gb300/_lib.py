@@ -53,6 +53,7 @@ class bsf_opts(ctypes.Structure):
         ("max_scale", ctypes.c_float),
         ("iterations", ctypes.c_int),
         ("hex_spacing", ctypes.c_float),
+        ("rel_bound", ctypes.c_float),
     ]
 
 

@@ -120,6 +120,7 @@ void bsf_default_opts(bsf_opts* o) {
     o->max_scale = 0.f;
     o->iterations = 1;
     o->hex_spacing = 0.5f;
+    o->rel_bound = 1e-3f;
 }
 
 const char* bsf_status_string(bsf_status s) {
@@ -266,9 +267,11 @@ bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_
     bsf_opts o;
     bsf_default_opts(&o);
     if (opts) o = *opts;
+    if (N == 6 && !(o.rel_bound >= 0.f && o.rel_bound < 1.f / 6.f)) return BSF_EINVAL;
     BSF_TRY(cudaSetDevice(c->device));
     if (N == 6)
-        BSF_TRY(launch_map6_out(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
+        BSF_TRY(launch_map6_out(params, kind, (long long)npix, o.eps, o.eta, o.rel_bound, scales, flags,
+                                 (cudaStream_t)stream));
     else
         BSF_TRY(launch_map4(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
     return BSF_OK;
@@ -414,7 +417,7 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     BSF_TRY(grow(&c->h6_ext, &c->h6_ext_bytes, ext_bytes));
     BSF_TRY(cudaMemsetAsync(c->h6_ext, 0, ext_bytes, st));
     BSF_TRY(prof_mark(c, 0, st));
-    BSF_TRY(launch_map6(params, kind, (int)B, (int)H, (int)W, fine, o.eps, o.eta, ascale, (double*)c->h6_scales,
+    BSF_TRY(launch_map6(params, kind, (int)B, (int)H, (int)W, fine, o.eps, o.eta, o.rel_bound, ascale, (double*)c->h6_scales,
                         (unsigned*)c->h6_ext, c->d_status, st));
     std::vector<unsigned> ext((size_t)B * nfine * 2);
     BSF_TRY(cudaMemcpyAsync(ext.data(), c->h6_ext, ext_bytes, cudaMemcpyDeviceToHost, st));
@@ -463,6 +466,7 @@ static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t 
     if (opts) *o = *opts;
     if (o->precision != BSF_PREC_EXACT && o->precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (o->iterations < 1 || o->iterations > 64) return BSF_EINVAL;
+    if (N == 6 && !(o->rel_bound >= 0.f && o->rel_bound < 1.f / 6.f)) return BSF_EINVAL;
     if (N == 6 && !(o->hex_spacing == 1.f || o->hex_spacing == 0.5f || o->hex_spacing == 0.25f ||
                     o->hex_spacing == 0.125f))
         return BSF_EINVAL;

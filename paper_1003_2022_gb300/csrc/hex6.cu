@@ -429,14 +429,12 @@ struct map6_result {
     int flag;
 };
 
-// the bound p_k >= 1e-3 T keeps the smallest width at least 0.077 times the
-// typical one: the stencil's rounded (double-float) part loses accuracy like
-// the square of that ratio for each width at the bound
-constexpr double MAP6_REL_BOUND = 1e-3;
-
+// rel (default 1e-3): the bound p_k >= rel T keeps the smallest width at least
+// 0.077 times the typical one; the stencil's rounded (double-float) part loses
+// accuracy like the square of that ratio for each width at the bound
 // covariance (kind COV) or (sigma, rho, theta) (kind SRT) -> six scales; the
 // flags and the elongation clamp follow the four-directional map
-__device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, double eps, double eta) {
+__device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, double eps, double eta, double rel) {
     map6_result R;
     R.flag = 0;
     const double v0 = v0f, v1 = v1f, v2 = v2f;
@@ -463,7 +461,7 @@ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, dou
     // that every p_k can keep the share delta = 1e-3 of the trace
     double psi = fmod(atan2(s2, c2), 1.04719755119659774615);
     if (psi < 0.0) psi += 1.04719755119659774615;
-    const double r = (1.0 - 6.0 * MAP6_REL_BOUND) * 0.86602540378443864676 / cos(psi - 0.52359877559829887308);
+    const double r = (1.0 - 6.0 * rel) * 0.86602540378443864676 / cos(psi - 0.52359877559829887308);
     bool clamp = false;
     {
         const double U = (1.0 + r) / (1.0 - r);
@@ -487,8 +485,8 @@ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, dou
         Zc = 24.0 * d * c2;
         Zs = 24.0 * d * s2;
     }
-    // lower bound of p: eps, or the share MAP6_REL_BOUND of the trace T = sum p
-    const double bound = fmax(eps, MAP6_REL_BOUND * T);
+    // lower bound of p: eps, or the share rel of the trace T = sum p
+    const double bound = fmax(eps, rel * T);
     map6_p P = map6_active_set(T, Zc, Zs, bound);
     if (!P.ok) {
         R.flag |= 2;
@@ -516,7 +514,7 @@ __device__ __forceinline__ double sin_k(int k) {
 // per pixel: scales (FP64, six planes per batch entry) and the largest
 // footprint half-extents of each tile
 __global__ void k_map6(const float* __restrict__ params, int kind, long long HW, int B, int W, int tile, int tiles_x,
-                       int ntile, double eps, double eta, double ascale, double* __restrict__ scales,
+                       int ntile, double eps, double eta, double rel, double ascale, double* __restrict__ scales,
                        unsigned* __restrict__ tile_ext, unsigned* __restrict__ status) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= HW * B) return;
@@ -533,7 +531,7 @@ __global__ void k_map6(const float* __restrict__ params, int kind, long long HW,
         if (flag) raise_status(status, BSF_EBADSCALE);
     } else {
         const float* q = params + b * 3 * HW + p;
-        const map6_result R = map6_solve(kind, q[0], q[HW], q[2 * HW], eps, eta);
+        const map6_result R = map6_solve(kind, q[0], q[HW], q[2 * HW], eps, eta, rel);
         for (int k = 0; k < 6; ++k) a[k] = R.a[k] * ascale;
         flag = R.flag;
         if (flag & 1) raise_status(status, BSF_EINFEASIBLE);
@@ -554,10 +552,10 @@ __global__ void k_map6(const float* __restrict__ params, int kind, long long HW,
 
 // the scales of bsf_scales_from_cov for N = 6 (float32, six planes, flags)
 __global__ void k_map6_out(const float* __restrict__ params, int kind, long long npix, double eps, double eta,
-                           float* __restrict__ scales, uint8_t* __restrict__ flags) {
+                           double rel, float* __restrict__ scales, uint8_t* __restrict__ flags) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    const map6_result R = map6_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta);
+    const map6_result R = map6_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta, rel);
     for (int k = 0; k < 6; ++k) scales[k * npix + p] = (float)R.a[k];
     if (flags) flags[p] = (uint8_t)R.flag;
 }
@@ -992,18 +990,19 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
 
 
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
-                        double ascale, double* scales, unsigned* tile_ext, unsigned* status, cudaStream_t st) {
+                        double rel, double ascale, double* scales, unsigned* tile_ext, unsigned* status,
+                        cudaStream_t st) {
     const long long HW = (long long)H * W, n = HW * B;
     const int tiles_x = (W + tile - 1) / tile, tiles_y = (H + tile - 1) / tile;
     k_map6<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(params, kind, HW, B, W, tile, tiles_x, tiles_x * tiles_y, eps,
-                                                        eta, ascale, scales, tile_ext, status);
+                                                        eta, rel, ascale, scales, tile_ext, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, float* scales,
-                            uint8_t* flags, cudaStream_t st) {
+cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, double rel,
+                            float* scales, uint8_t* flags, cudaStream_t st) {
     if (npix == 0) return cudaSuccess;
-    k_map6_out<<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(params, kind, npix, eps, eta, scales, flags);
+    k_map6_out<<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(params, kind, npix, eps, eta, rel, scales, flags);
     return cudaGetLastError();
 }
 

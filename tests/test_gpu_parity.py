@@ -66,8 +66,41 @@ def test_preintegrate_fp64_form(dtype):
 
 
 # ------------------------------------------------------------------ scale map
+def _threshold_margins(p, kind, eps=1e-3, eta=1e-3):
+    """FP64 relative distance of every pixel to the two thresholds at which the
+    scale map's flags switch (Sec. 3.2.2): the elongation clamp rho > (1 - eta)
+    U(theta) of Prop. 3.1, and the feasibility of p >= eps (the interval
+    |d| + eps <= w <= min(a, c) - eps of the solution line).  A flag that the
+    FP32 map decides differently from the FP64 oracle is legitimate only at
+    such a threshold."""
+    v0, v1, v2 = (x.astype(np.float64).ravel() for x in p)
+    if kind == "srt":
+        lmax, lmin, th = v0 * v0, v0 * v0 / v1, v2
+    else:
+        tr, dd = v0 + v2, np.sqrt((v0 - v2) ** 2 + 4 * v1 * v1)
+        lmax, lmin = 0.5 * (tr + dd), 0.5 * (tr - dd)
+        th = 0.5 * np.arctan2(2 * v1, v0 - v2)
+    th = np.mod(th, np.pi)
+    U = np.array([O.U_bound(t) for t in th])
+    rc = (1 - eta) * U
+    m_clamp = np.abs(lmax / lmin / rc - 1.0)
+    clamp = lmax / lmin > rc
+    s = lmax + lmin
+    lmin_c = np.where(clamp, s / (1 + rc), lmin)
+    lmax_c = s - lmin_c
+    m, d = 0.5 * (lmax_c + lmin_c), 0.5 * (lmax_c - lmin_c)
+    c1, c2, c3 = 24 * (m + d * np.cos(2 * th)), 24 * d * np.sin(2 * th), 24 * (m - d * np.cos(2 * th))
+    lo, hi = np.abs(0.5 * c2) + eps, np.minimum(0.5 * c1, 0.5 * c3) - eps
+    m_feas = np.abs(hi - lo) / np.maximum(np.abs(hi), np.abs(lo))
+    return m_clamp, m_feas
+
+
 @pytest.mark.parametrize("kind", ["srt", "cov"])
-def test_scales_from_cov_parity(kind):
+def test_scales_from_cov_parity(kind, accuracy_record):
+    """The FP32 scale map against the FP64 oracle (Sec. 3.2.2, Prop. 3.1), on every
+    pixel of a 96 x 128 field with sigma 1-32 px and rho 1-8 (many pixels clamped):
+    flags identical except at a threshold (each mismatch listed with its distance
+    to it), and the largest scale error over ALL pixels bounded."""
     dev = _cuda()
     H, W = 96, 128
     p = synth.srt_field(H, W, seed=3, sigma=(1.0, 32.0), rho=(1.0, 8.0), theta="vector")
@@ -78,20 +111,56 @@ def test_scales_from_cov_parity(kind):
         p = np.stack([lmax * c * c + lmin * sn * sn, (lmax - lmin) * sn * c, lmin * c * c + lmax * sn * sn]
                      ).astype(np.float32)
     a_gpu, fl_gpu = api.scales_from_cov(torch.from_numpy(p).to(dev), kind=kind)
-    a_gpu = a_gpu.cpu().numpy().astype(np.float64)
+    a_gpu = a_gpu.cpu().numpy().astype(np.float64).reshape(4, -1)
+    fl_gpu = fl_gpu.cpu().numpy().ravel()
     a_ref, fl_ref = O.map4(p.astype(np.float64), O.KIND_SRT if kind == "srt" else O.KIND_COV)
-    ok = fl_ref == fl_gpu.cpu().numpy()
-    assert ok.mean() > 0.99
-    # scale error relative to the largest scale of the pixel (the filter depends on a_k to
-    # within its own footprint; see the end-to-end tests for the output bar)
+    a_ref, fl_ref = a_ref.reshape(4, -1), fl_ref.ravel()
+    assert (fl_ref & 1).sum() > 100  # the field exercises the clamp
+    m_clamp, m_feas = _threshold_margins(p, kind)
+    mism = np.flatnonzero(fl_ref != fl_gpu)
+    # FP32 inputs, an FP32 sin/cos of 2 theta with absolute error ~2^-21 and FP32
+    # rounding of rho and U put the GPU's decision within ~1e-5 of the threshold
+    report = [(int(i), int(fl_ref[i]), int(fl_gpu[i]), float(m_clamp[i]), float(m_feas[i])) for i in mism]
+    for i, fr, fg, mc, mf in report:
+        dist = mc if (fr ^ fg) & 1 else mf
+        assert dist < 2e-5, ("flag mismatch away from its threshold", report)
+    # scale error relative to the largest scale of the pixel (the filter depends on a_k
+    # within its own footprint), over every pixel whose flags agree
+    ok = fl_ref == fl_gpu
     rel = np.abs(a_gpu - a_ref).max(axis=0) / a_ref.max(axis=0)
-    assert np.percentile(rel[ok], 99.9) < 2e-5, np.percentile(rel[ok], 99.9)
+    worst = float(rel[ok].max())
+    accuracy_record[f"map4_{kind}"] = {"pixels": int(ok.size), "flag_mismatches": report,
+                                       "max_rel_scale_err": worst,
+                                       "p999_rel_scale_err": float(np.percentile(rel[ok], 99.9))}
+    print(f"map4 {kind}: {len(report)} flag mismatches at thresholds, max rel scale error {worst:.3e}")
+    assert worst < 5e-5, worst
     # the covariance of the GPU scales reproduces the target where no clamp applied
     sel = ok & (fl_ref == 0)
     pg = a_gpu[:, sel] ** 2
     c11 = (2 * pg[0] + pg[1] + pg[3]) / 24
     c11r = (2 * a_ref[0, sel] ** 2 + a_ref[1, sel] ** 2 + a_ref[3, sel] ** 2) / 24
     assert np.abs(c11 / c11r - 1).max() < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_filter_256_full_image_against_definition(dtype, accuracy_record):
+    """The 256 x 256 workload (sigma 2-8, rho 1-4, smooth fields), fused scale map
+    and stencil, compared at EVERY pixel with the oracle's map (Sec. 3.2.2) and
+    the plain definition (1): normwise bar 1e-5, worst pixel reported."""
+    f, p = synth.workload_inputs("u256_f32_n4")
+    if dtype == "u8":
+        f = np.clip(np.rint(f * 255.0), 0, 255).astype(np.uint8)
+    out, st = _run(f, p, "srt", max_scale=8.0)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    ref = O.direct4(f.astype(np.float64), a)
+    err = np.abs(out.astype(np.float64) - ref)
+    nerr = float(err.max() / np.abs(ref).max())
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    accuracy_record[f"full256_{dtype}"] = {"pixels": int(ref.size), "max_normwise": nerr,
+                                           "rms_over_max": float(np.sqrt(np.mean(err ** 2)) / np.abs(ref).max()),
+                                           "max_per_pixel_rel": float((err[big] / np.abs(ref[big])).max())}
+    assert nerr < TOL, nerr
 
 
 # ------------------------------------------------------------------ whole path
