@@ -346,6 +346,34 @@ def alg1_hex(f, a, idx=None, h: float = 0.5) -> np.ndarray:
     return res
 
 
+def alg1_hex_c(f, a, idx=None, h: float = 0.5) -> np.ndarray:
+    """``alg1_hex`` restated in C (``bsf_oracle6.c``): the same three steps in
+    the same order and in FP64, with step 3 visiting only the lattice points
+    inside the support of beta_b around each tap instead of testing the whole
+    box, and the pixels shared among the host threads.  This is the form fast
+    enough to time on a crop of a real workload (the benchmark's CPU baseline);
+    pinned against ``alg1_hex``."""
+    from . import _load, _d, _ptr, _dp, _i64p
+    f = _d(f)
+    H, W = f.shape
+    A = _d(np.asarray(a, float).reshape(6, H, W))
+    idx_a = np.arange(H * W, dtype=np.int64) if idx is None else np.ascontiguousarray(np.asarray(idx).ravel(),
+                                                                                       dtype=np.int64)
+    out = np.empty(idx_a.size)
+    rc = _load().bo_alg1_hex6(_ptr(f, _dp), H, W, _ptr(A, _dp), _ptr(idx_a, _i64p), idx_a.size, float(h),
+                              _ptr(out, _dp))
+    if rc != 0:
+        raise MemoryError("bo_alg1_hex6: lattice box too large")
+    return out
+
+
+def beta6_c(a, x1: float, x2: float) -> float:
+    """beta^6_a(x) as the C restatement evaluates it (truncated power, 64 corners)."""
+    from . import _load, _d, _ptr, _dp
+    a = _d(a)
+    return float(_load().bo_beta6(_ptr(a, _dp), float(x1), float(x2)))
+
+
 # ----------------------------------------------------------------------------
 # covariance -> scales for N directions
 # ----------------------------------------------------------------------------
@@ -407,12 +435,17 @@ def _solve_face(M, c, D, active, bound, scale):
         if dec <= 1e-30 * scale ** 4:
             break
         t = 1.0
-        while t > 1e-12:
-            pn = p0 + Z @ (u + t * step)
-            qn = pn * pn
-            if float(qn @ D @ qn) <= f0 - 0.25 * t * dec:
-                break
-            t *= 0.5
+        # backtracking (Armijo) only while the decrease is well above the rounding
+        # of the objective: near the optimum the test sees rounding noise alone and
+        # would shrink the step to nothing, while the full Newton step of a convex
+        # quartic converges there quadratically
+        if dec > 1e-11 * abs(f0):
+            while t > 1e-12:
+                pn = p0 + Z @ (u + t * step)
+                qn = pn * pn
+                if float(qn @ D @ qn) <= f0 - 0.25 * t * dec:
+                    break
+                t *= 0.5
         u = u + t * step
         if t * np.abs(step).max() <= 1e-16 * scale:
             break
