@@ -1,20 +1,24 @@
 """Benchmark of the space-variant elliptical box-spline filter on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ID]
 
-One step = the whole hot path over one synthetic 2048x2048 uint8 image with
-a per-pixel (sigma, rho, theta) field (sigma 1-32 px, rho 1-8, theta from a
-smooth vector field), N = 4 directions: the per-pixel scale map (Sec. 3.2.2),
-the pre-integration (Algorithm 1 step 2) and the 16-tap finite difference
-with Zwart-Powell interpolation (Algorithm 1 step 3), through the C ABI call
-bsf_filter.  Inputs are resident in HBM before the timed region; between
-timed steps a 512 MiB buffer is written to flush the 129 MB L2.
+One step = the whole hot path, through the C ABI call bsf_filter, over the
+default workload: a batch of 4 RGB 4096x4096 float32 images (uniform [0,1)
+plus three seeded gratings) with a per-pixel (sigma, rho, theta) field per
+image (sigma 2-48 px, rho 1-6, theta uniform), N = 6 directions: the scale
+map (Sec. 3.2.2 with the six-directional kurtosis norm), the transfer to the
+hexagonal lattice and the six running sums (Algorithm 1 step 2), and the
+64-tap finite difference (Algorithm 1 step 3).  --workload u2048_u8_n4 runs
+the 2048x2048 uint8 image with N = 4 (sigma 1-32, rho 1-8), and so on.
+Inputs are resident in HBM before the timed region; between timed steps a
+512 MiB buffer is written to flush the 129 MB L2.
 
 For N > 1 (torchrun), each rank runs an independent replica on its own GPU
 (the path has no exchange step); value = pixels of all ranks / max time.
 
---impl reference times the FP64 CPU oracle (Algorithm 1 restated, single
-thread) on a bounded crop of the same workload on the host cores.
+--impl reference times the FP64 CPU oracle (Algorithm 1 restated, with the
+oracle's own scale map) on the host cores, one bounded crop of the same
+workload per step.
 """
 from __future__ import annotations
 
@@ -33,9 +37,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "u2048_u8_n4"
+WORKLOAD = "b4c3_4096_f32_n6"
 METRIC = "Gpixels/s filtered (N=4,6) at ≤1e-5 rel err vs FP64 oracle; % HBM roofline; p50/p99"
-SIGMA_MAX = 32.0
 # algorithmic 32-bit integer operations per output pixel of the exact stencil,
 # counted from its formulation per tap: 56 for the 28 64-bit additions of the
 # nine-point ZP combinations, 22 for the eleven 64x32-bit products, 14 for the
@@ -51,6 +54,12 @@ STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
 # six directions: 64 taps x 24 lattice points x 15 coefficients x 5 twenty-bit limbs,
 # one int32 multiply-add each
 HEX6_IMAD_PER_PX = 64 * 24 * 15 * 5
+# the method's work per output pixel as the hot-path table counts it: N = 4, 16 taps x
+# (partition select + 7 ZP weights + 7 multiply-adds) ~ 1.0k operations; N = 6, 64 taps,
+# 2.5k-4k operations (the midpoint is used)
+METHOD_OPS_PER_PX = {4: 1000, 6: 3250}
+METHOD_OPS_NOTE = {4: "16 taps x (partition select + 7 ZP weights + 7 multiply-adds) ~ 1.0k ops/px",
+                   6: "64 taps, 2.5k-4k ops/px (midpoint 3250)"}
 # Benchmarked workloads: (params kind, largest sigma or scale, forward+backward).
 BENCH_WORKLOADS = {
     "u2048_u8_n4": ("srt", 32.0, False),
@@ -67,7 +76,8 @@ WORKLOAD_TEXT = {
     "b4c3_4096_f32_n4": "batch 4 x 3 channels x 4096x4096 f32 (uniform + 3 gratings), sigma 2-48 px, rho 1-6, "
                         "theta uniform, filtered with N=4, exact 128-bit fixed-point path",
     "b4c3_4096_f32_n6": "batch 4 x 3 channels x 4096x4096 f32 (uniform + 3 gratings), sigma 2-48 px, rho 1-6, "
-                        "theta uniform, N=6 (64-tap stencil) on the hexagonal lattice of spacing 0.5 px, FP64",
+                        "theta uniform, N=6 (64-tap stencil) on the hexagonal lattice of spacing 0.5 px, exact 128-bit "
+                        "window sums and coefficient sums, double-float remainder",
     "b8_1024_f32_scales": "batch 8 x 1024x1024 f32, learnable scale field a_k in [1,24]; one step = forward "
                           "filter + backward (gradients for image and scales)",
 }
@@ -185,6 +195,28 @@ def stencil_traffic():
         return None
 
 
+def preint_algorithmic_bytes(nimg: int, H: int, W: int, P: int, in_bytes: int, elem: int) -> int:
+    """Algorithmic HBM bytes of one pre-integration call over nimg images: every
+    buffer element written once, every image sample its strip needs read once.
+    Wide rows are cut into vertical strips exactly as the library does (a band
+    CTA holds at most 4096 int64/double or 3072 128-bit elements of a row, 2048
+    when a batch of 128-bit buffers fills several waves), so a strip reads the
+    image columns of its outputs +- P."""
+    many_waves = (H + 2 * P) * nimg > 64 * 152
+    maxw = (2048 if many_waves else 3072) if elem == 16 else 4096
+    Wfull = W + 2 * P
+    nstrip = 1 if Wfull <= maxw else -(-W // (maxw - 2 * P))
+    Ws = -(-W // nstrip)
+    tot = 0
+    for sidx in range(nstrip):
+        col0 = sidx * Ws
+        ws = W if nstrip == 1 else min(Ws, W - col0)
+        wp = ws + 2 * P
+        cols_read = min(W, col0 + ws + P) - max(0, col0 - P)
+        tot += nimg * ((H + 2 * P) * wp * elem + H * cols_read * in_bytes)
+    return tot
+
+
 def alu_peak_tops():
     """Issue-rate bound of 32-bit integer ALU work: 152 SMs x 128 lanes x max SM clock."""
     return 152 * 128 * 2.070e9 / 1e12
@@ -199,51 +231,139 @@ def _inputs(size=None, workload=WORKLOAD):
     return synth.batch_inputs(workload, seed=0, H=size, W=size)
 
 
-def cpu_baseline_run(f, p, crop=192, seed=0):
-    """The oracle (Algorithm 1 restated in FP64/int64, scale map in FP64) on a
-    crop of the workload; returns (pixels/s, seconds, description)."""
+def _map6_chunk(args):
+    """One worker's share of the oracle's six-directional map (spawned process)."""
+    from oracle import n6
+    params, kind = args
+    return n6.map6(params, kind)[0]
+
+
+class OracleRunner:
+    """The FP64 oracle on the host cores, for the CPU baseline and the reference
+    arm: Algorithm 1 restated (O-alg) with the oracle's own scale map, on a crop
+    of the workload's first image.  N = 4: ``map4`` + ``preint4`` + ``stencil4``
+    (C, OpenMP over rows and pixels).  N = 6: ``n6.map6`` (numpy, KKT map, in a
+    pool of spawned processes) + ``n6.alg1_hex_c`` (C, OpenMP over pixels).
+    ``cores``: the host threads / processes used."""
+
+    def __init__(self, N: int, u8: bool, sigma_max: float):
+        import oracle
+        oracle.build()
+        self.N, self.u8, self.smax = N, u8, sigma_max
+        self.threads = oracle.num_threads()
+        self.pool = None
+        if N == 6:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(os.cpu_count() or 1)
+            self.pool.map(_map6_chunk, [(np.ones((3, 1)), 2)] * (os.cpu_count() or 1))  # import in every worker
+        self.cores = max(self.threads, os.cpu_count() or 1) if N == 6 else self.threads
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+    def run(self, f, p, crop: int, seed: int):
+        """Filter one crop x crop crop (zero outside it) at a seeded offset;
+        returns seconds."""
+        import oracle
+        from oracle import n6
+        H, W = f.shape
+        rng = np.random.default_rng(seed)
+        y0 = int(rng.integers(0, H - crop + 1))
+        x0 = int(rng.integers(0, W - crop + 1))
+        fc = np.ascontiguousarray(f[y0:y0 + crop, x0:x0 + crop])
+        pc = np.ascontiguousarray(p[:, y0:y0 + crop, x0:x0 + crop]).astype(np.float64)
+        t = time.perf_counter()
+        if self.N == 4:
+            a, _ = oracle.map4(pc, oracle.KIND_SRT)
+            P = int(np.ceil(0.5 * 8.364 * self.smax)) + 4
+            if self.u8:
+                oracle.alg1_filter4(fc.astype(np.int64), a, P, integer=True)
+            else:
+                oracle.alg1_filter4(fc.astype(np.float64), a, P, integer=False)
+        else:
+            flat = pc.reshape(3, -1)
+            parts = np.array_split(np.arange(flat.shape[1]), 4 * len(self.pool._pool))
+            a = np.concatenate(self.pool.map(_map6_chunk, [(flat[:, ix], 2) for ix in parts if ix.size]), axis=1)
+            n6.alg1_hex_c(fc.astype(np.float64), a.reshape(6, crop, crop), None, 0.5)
+        return time.perf_counter() - t
+
+    def describe(self, crop: int, n: int) -> str:
+        if self.N == 4:
+            steps = ("oracle map4 + preint4 (int64 for u8, FP64 for f32) + stencil4 (FP64 ZP weights from the exact "
+                     "box spline), C with OpenMP")
+        else:
+            steps = ("oracle n6.map6 (KKT map, numpy, spawned processes) + n6.alg1_hex_c (transfer to the hexagonal "
+                     "lattice, six FP64 running sums, 64-tap stencil with the exact element, C with OpenMP)")
+        return f"{steps}; {n} crop(s) of {crop}x{crop} px of the workload's first image"
+
+
+def oracle_direct_rate(f, p, N: int, budget_s: float = 8.0, seed: int = 5):
+    """O-direct (the plain definition summed over each footprint) on sampled
+    pixels of the full first image: pixels/s with the oracle's scales.  N = 4:
+    C (``direct4``, OpenMP); N = 6: numpy (``n6.direct6_hex``, one pixel at a
+    time).  Pixels are added until the time budget is spent (at most 4096)."""
     import oracle
+    from oracle import n6
     H, W = f.shape
     rng = np.random.default_rng(seed)
-    y0 = int(rng.integers(0, H - crop))
-    x0 = int(rng.integers(0, W - crop))
-    fc = np.ascontiguousarray(f[y0:y0 + crop, x0:x0 + crop])
-    pc = np.ascontiguousarray(p[:, y0:y0 + crop, x0:x0 + crop]).astype(np.float64)
-    P = int(np.ceil(0.5 * 8.364 * SIGMA_MAX)) + 4
-    t = time.perf_counter()
-    a, _ = oracle.map4(pc, oracle.KIND_SRT)
-    out, bad = oracle.alg1_filter4(fc.astype(np.int64), a, P, integer=True)
-    dt = time.perf_counter() - t
-    desc = (f"oracle map4 + preint4_i64 + stencil4 (FP64 ZP weights from the exact box spline), "
-            f"single thread, one {crop}x{crop} crop of the 2048x2048 workload")
-    return crop * crop / dt, dt, desc
+    done, t_tot, batch = 0, 0.0, 16 if N == 6 else 512
+    f64 = f.astype(np.float64)
+    while done < 4096 and t_tot < budget_s:
+        n = 1 if N == 6 else batch
+        idx = rng.choice(H * W, size=n, replace=False)
+        t = time.perf_counter()
+        if N == 4:
+            a, _ = oracle.map4(p.reshape(3, -1)[:, idx].astype(np.float64)[:, :, None], oracle.KIND_SRT)
+            A = np.zeros((4, H * W))
+            A[:, idx] = a[:, :, 0]
+            oracle.direct4(f64, A.reshape(4, H, W), idx)
+        else:
+            a, _ = n6.map6(p.reshape(3, -1)[:, idx].astype(np.float64), 2)
+            y, x = divmod(int(idx[0]), W)
+            r = int(np.ceil(0.5 * np.sum(a[:, 0]))) + 2
+            ya, xa = max(0, y - r), max(0, x - r)
+            fc = f64[ya:min(H, y + r + 1), xa:min(W, x + r + 1)]
+            A = np.zeros((6,) + fc.shape)
+            A[:, y - ya, x - xa] = a[:, 0]
+            n6.direct6_hex(fc, A, np.array([(y - ya) * fc.shape[1] + (x - xa)]), 0.5, origin=(xa, ya))
+        t_tot += time.perf_counter() - t
+        done += n
+    return done / t_tot, done, t_tot
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores, on the workload of our arm:
+    every step filters one bounded crop of it (O-alg with the oracle's map)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    f, p = _inputs()
+    from paper_1003_2022_gb300 import synth as _synth
+    N = _synth.WORKLOADS[args.workload]["N"]
+    _, smax, _ = BENCH_WORKLOADS[args.workload]
+    f, p = _inputs(args.size, args.workload)
+    u8 = f.dtype == np.uint8
     f, p = f[0, 0], p[0]
-    import oracle
-    oracle.build()
-    for i in range(args.warmup):
-        cpu_baseline_run(f, p, crop=48, seed=1000 + i)
-    tot_px, tot_s = 0, 0.0
-    for i in range(args.steps):
-        v, dt, desc = cpu_baseline_run(f, p, crop=64, seed=i)
-        tot_px += 64 * 64
-        tot_s += dt
-    value = tot_px / tot_s / 1e9
+    crop = 32 if N == 6 else 96
+    runner = OracleRunner(N, u8, smax)
+    try:
+        for i in range(args.warmup):
+            runner.run(f, p, crop=crop // 2, seed=1000 + i)
+        tot_s = 0.0
+        for i in range(args.steps):
+            tot_s += runner.run(f, p, crop=crop, seed=i)
+    finally:
+        runner.close()
+    value = args.steps * crop * crop / tot_s / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "2048x2048 u8 image, N=4, sigma 1-32 px, rho 1-8, "
-                                                    "theta from a smooth vector field; one 64x64 crop per step",
-                                        "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": "Gpixels/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} crops of 64x64 px (one per step)"},
+        "data": "synthetic", "config": {"workload": WORKLOAD_TEXT[args.workload] + f"; one {crop}x{crop} crop "
+                                        "per step", "workload_id": args.workload, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "Gpixels/s", "cores": runner.cores, "kind": "oracle",
+                         "sample": runner.describe(crop, args.steps)},
         "e2e": {"value": value, "unit": "Gpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -331,7 +451,7 @@ def run_ours(args):
     f_h = torch.from_numpy(f_np).pin_memory()
     p_h = torch.from_numpy(p_np).pin_memory()
     o_h = torch.empty((B, C, H, W), dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 50))
+    e2e_steps = max(3, min(args.steps, 5 if N == 6 else 50))
     d2h = out.numel() * 4
     if train:
         # forward + backward: H2D of image and field, the two calls, D2H of output and gradients
@@ -383,39 +503,67 @@ def run_ours(args):
     npx = B * C * H * W
     value = replicas_value(npx * args.steps, t_max, ws) / 1e9
     e2e_value = ws * npx * e2e_steps / (e2e_ms / 1e3) / 1e9
-    # stencil launches in the timed region (one per strip and batch chunk of each forward call)
+    # stencil launches in the timed region (one per strip and batch chunk of each forward call;
+    # for N = 6 one per window chunk)
     n_st = max(nl, 1)
     st_ms = ms_st / n_st
-    ops_px = STENCIL_INT_OPS_PER_PX if u8 else STENCIL_INT_OPS_PER_PX_U128
     px_per_launch = npx * args.steps / n_st
-    achieved = ops_px * px_per_launch / (st_ms / 1e3) / 1e12
-    peak = alu_peak_tops()
-    traffic = stencil_traffic() if (args.workload == WORKLOAD and args.size in (None, 2048)
-                                    and args.precision == "exact") else None
-    kname = f"k_stencil4_exact<{'u64' if u8 else 'u128'},{kind_name.upper()}>"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kname,
-                "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
-                "peak_note": "152 SMs x 128 lanes x 2070 MHz, 32-bit integer ops (derived; an add-chain probe "
-                             "reached 37.1 Tops/s, a multiply-add chain 19.1 Tops/s)",
-                "int_ops_per_px": ops_px,
-                "algorithmic_bytes_per_launch": int((12 + 4 + 8 * (1 if u8 else 2)) * px_per_launch)}
-    # the HBM side of both kernels, against the measured copy bandwidth
     peaks, peak_src = _peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    P = api.halo_for(smax, kind_name)
-    elem = 8 if (u8 or args.precision != "exact") else 16
-    nstrip_one = (W + 2 * P) <= (4096 if elem == 8 else 3072)
-    pre_bytes = (H + 2 * P) * (W + 2 * P) * ((1 if u8 else 4) + elem) * B * C if nstrip_one else None
-    pre_ms = ms_pre / n_st
-    roofline["hbm"] = {
-        "peak_gbs": hbm_peak, "peak_source": peak_src,
-        "stencil_dram_gbs": traffic / (st_ms * 1e6) if traffic else None,
-        "stencil_frac": traffic / (st_ms * 1e6) / hbm_peak if traffic else None,
-        "preintegrate_algorithmic_bytes": pre_bytes,
-        "preintegrate_gbs": pre_bytes / (pre_ms * 1e6) if pre_bytes else None,
-        "preintegrate_frac": pre_bytes / (pre_ms * 1e6) / hbm_peak if pre_bytes else None,
-    }
+    peak = alu_peak_tops()
+    # the method's own work per output pixel (the finite difference with its
+    # interpolation, as the hot-path table counts it), not this implementation's
+    method_ops = METHOD_OPS_PER_PX[N]
+    achieved = method_ops * px_per_launch / (st_ms / 1e3) / 1e12
+    if N == 4:
+        impl_ops = STENCIL_INT_OPS_PER_PX if u8 else STENCIL_INT_OPS_PER_PX_U128
+        kname = f"k_stencil4_exact<{'u64' if u8 else 'u128'},{kind_name.upper()}>"
+        impl = {"what": "int32 operations of the exact integer form (64-bit or 128-bit emulation)",
+                "ops_per_px": impl_ops, "achieved_tops": impl_ops * px_per_launch / (st_ms / 1e3) / 1e12}
+        impl["frac"] = impl["achieved_tops"] / peak
+        traffic = stencil_traffic() if (args.workload == "u2048_u8_n4" and args.size in (None, 2048)
+                                        and args.precision == "exact") else None
+        alg_bytes = int((12 + 4 + 8 * (1 if u8 else 2)) * px_per_launch)
+    else:
+        impl_ops = HEX6_IMAD_PER_PX
+        kname = "k_hex6_stencil"
+        impl = {"what": "int32 multiply-adds of the exact coefficient sums: 64 taps x 24 lattice points x 15 "
+                        "coefficients x 5 twenty-bit limbs",
+                "ops_per_px": impl_ops, "achieved_tops": impl_ops * px_per_launch / (st_ms / 1e3) / 1e12,
+                "peak": 152 * 64 * 2.070e9 / 1e12,
+                "peak_note": "int32 multiply-add rate, 152 SMs x 64 per clock x 2070 MHz (derived)"}
+        impl["frac"] = impl["achieved_tops"] / impl["peak"]
+        traffic = None
+        alg_bytes = int((12 + 4 + 16) * px_per_launch)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "kernel_ms": st_ms, "launches_per_step": n_st / args.steps,
+                "preintegrate_ms": ms_pre / n_st,
+                "method_ops_per_px": method_ops,
+                "method_ops_note": METHOD_OPS_NOTE[N],
+                "peak_note": "derived: 152 SMs x 128 lanes x 2070 MHz, 32-bit integer or FP32 operations (an "
+                             "add-chain probe reached 37.1 Tops/s); MEASURED_PEAKS.json holds no integer peak",
+                "implementation": impl,
+                "algorithmic_bytes_per_launch": alg_bytes}
+    # the HBM side of both steps, against the measured copy bandwidth
+    if N == 4:
+        P = api.halo_for(smax, kind_name)
+        elem = 8 if (u8 or args.precision != "exact") else 16
+        pre_bytes = preint_algorithmic_bytes(B * C, H, W, P, 1 if u8 else 4, elem)
+        pre_ms = ms_pre / n_st
+        roofline["hbm"] = {
+            "peak_gbs": hbm_peak, "peak_source": peak_src,
+            "stencil_dram_gbs": traffic / (st_ms * 1e6) if traffic else None,
+            "stencil_frac": traffic / (st_ms * 1e6) / hbm_peak if traffic else None,
+            "stencil_algorithmic_frac": alg_bytes / (st_ms * 1e6) / hbm_peak,
+            "preintegrate_algorithmic_bytes": pre_bytes * args.steps / n_st,
+            "preintegrate_gbs": pre_bytes * args.steps / n_st / (pre_ms * 1e6),
+            "preintegrate_frac": pre_bytes * args.steps / n_st / (pre_ms * 1e6) / hbm_peak,
+        }
+    else:
+        roofline["hbm"] = {"peak_gbs": hbm_peak, "peak_source": peak_src,
+                           "stencil_algorithmic_frac": alg_bytes / (st_ms * 1e6) / hbm_peak,
+                           "preintegrate_note": "map, window transfer and six exact running sums per chunk: "
+                                                "compute-bound, not an HBM stream"}
     if args.precision != "exact":
         roofline["kernel"] = f"k_stencil4_f64<{kind_name.upper()}>"
         roofline["note"] = "all-FP64 form: the integer op count does not apply; compare kernel_ms"
@@ -430,28 +578,18 @@ def run_ours(args):
         chunks = -(-B // max(1, min(B, (16 << 30) // per)))
         launches += 13 * chunks * args.steps
     if N == 6:
-        # six directions: the stencil's exact integer part is 64 taps x 24 lattice points x 15
-        # coefficients, each the product of a small integer coefficient and a 96-bit window
-        # value in five 20-bit limbs (5 int32 multiply-adds into 32-bit sums), against the
-        # int32 multiply-add rate (152 SMs x 64 per clock x 2070 MHz)
-        ops_px6 = HEX6_IMAD_PER_PX
-        achieved6 = ops_px6 * px_per_launch / (st_ms / 1e3) / 1e12
-        peak6 = 152 * 64 * 2.070e9 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved6, "peak": peak6, "unit": "Tops/s",
-                    "frac": achieved6 / peak6, "traffic": None, "kernel": "k_hex6_stencil",
-                    "kernel_ms": st_ms, "preintegrate_ms": ms_pre / n_st,
-                    "peak_note": "int32 multiply-add rate, 152 SMs x 64 per clock x 2070 MHz (derived; a "
-                                 "multiply-add chain probe reached 19.1 Tops/s); int32 multiply-adds of the exact "
-                                 "coefficient sums, 64 taps x 24 points x 15 coefficients x 5 twenty-bit limbs",
-                    "int_madds_per_px": ops_px6,
-                    "launches_per_step": n_st / args.steps,
-                    "preintegrate_note": "scale map + window transfer and six exact running sums, per chunk"}
-        launches = args.steps + 2 * nl
+        launches = args.steps + 2 * nl  # the map once per call, then windows + stencil per chunk
+    if N == 6:
+        dtype_s = "int128+double-float"
+    elif args.precision == "exact":
+        dtype_s = "int64" if u8 else "int128"
+    else:
+        dtype_s = "f64"
     line = {
         "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if N == 6 else (("int64" if u8 else "int128") if args.precision == "exact" else "f64"),
+        "dtype": dtype_s,
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] if args.size is None else
                    f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
@@ -465,10 +603,21 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "how": e2e_how},
         "gpu_launches": launches,
     }
-    if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
-        v, dt, desc = cpu_baseline_run(f_np[0, 0], p_np[0], crop=args.cpu_crop)
-        line["cpu_baseline"] = {"value": v / 1e9, "unit": "Gpixels/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{desc}; {dt:.1f} s"}
+    if rank == 0 and not args.no_cpu_baseline and not train and args.precision == "exact":
+        runner = OracleRunner(N, u8, smax)
+        try:
+            crop = args.cpu_crop or (128 if N == 6 else 1024)
+            dt = runner.run(f_np[0, 0], p_np[0], crop=crop, seed=0)
+        finally:
+            runner.close()
+        line["cpu_baseline"] = {"value": crop * crop / dt / 1e9, "unit": "Gpixels/s", "cores": runner.cores,
+                                "kind": "oracle", "sample": f"{runner.describe(crop, 1)}; {dt:.1f} s",
+                                "nproc": os.cpu_count()}
+        rate, n_od, t_od = oracle_direct_rate(f_np[0, 0], p_np[0], N)
+        line["oracle_direct"] = {"value": rate, "unit": "pixels/s", "pixels": n_od, "seconds": t_od,
+                                 "cores": runner.threads if N == 4 else 1,
+                                 "what": "the plain definition summed over each sampled pixel's footprint "
+                                         "(with the oracle's scale map), full image"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -645,11 +794,12 @@ def run_sizes(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: about 30-60 s of work)")
+    ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="exact", choices=["exact", "fp64"])
-    ap.add_argument("--cpu-crop", type=int, default=1024)
+    ap.add_argument("--cpu-crop", type=int, default=None, help="side of the oracle's crop (default 128 for N=6, "
+                                                                "1024 for N=4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")
     ap.add_argument("--mode", default="filter", choices=["filter", "serve", "smooth", "sizes"])
@@ -659,6 +809,12 @@ def main():
     ap.add_argument("--hbm-gb", type=float, default=48.0)
     ap.add_argument("--pool-side", type=int, default=4096)
     args = ap.parse_args()
+    from paper_1003_2022_gb300 import synth as _synth
+    heavy = _synth.WORKLOADS[args.workload]["N"] == 6
+    if args.steps is None:
+        args.steps = 10 if heavy else (20 if args.workload.startswith("b4c3") else 200)
+    if args.warmup is None:
+        args.warmup = 3 if heavy else 10
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -48,6 +48,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bsf_oracle.c")
+_SRC6 = os.path.join(_HERE, "bsf_oracle6.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libbsf_oracle.so")
 
@@ -59,11 +60,14 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle C source into a shared library (gcc, -O2, no fast-math)."""
+    """Compile the oracle C sources into a shared library (gcc, -O2, no fast-math;
+    OpenMP for the loops over independent pixels and rows)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC6))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-fopenmp", "-o", tmp, _SRC, _SRC6,
+                               "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -95,6 +99,11 @@ def _load():
         lib.bo_U_bound.argtypes = [ctypes.c_double]
         lib.bo_num_threads.restype = ctypes.c_int
         lib.bo_num_threads.argtypes = []
+        lib.bo_beta6.restype = ctypes.c_double
+        lib.bo_beta6.argtypes = [_dp, ctypes.c_double, ctypes.c_double]
+        lib.bo_alg1_hex6.restype = ctypes.c_int
+        lib.bo_alg1_hex6.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i64p, ctypes.c_int64, ctypes.c_double,
+                                     _dp]
         _lib = lib
     return _lib
 

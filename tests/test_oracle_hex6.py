@@ -244,3 +244,33 @@ def test_map6_flags():
     lmin2 = s / (1 + (1 - 1e-3) * U)
     C2 = _cov(math.sqrt(s - lmin2), (s - lmin2) / lmin2, 0.2)
     assert np.allclose(O.covarianceN(D6, a[:, 1]), C2, rtol=1e-10, atol=1e-12)
+
+
+def test_c_restatement_of_algorithm1_equals_the_numpy_one():
+    """The C form of Algorithm 1 on the hexagonal lattice (used to time the CPU
+    baseline) against the numpy form and the definition on the transferred
+    image, on tiny images with h = 1/2 and 1/4: the same three steps, so the
+    results agree to the FP64 cancellation level of both (about 1e-9 of the
+    output here); a dropped term, a wrong sign or a transposed direction gives
+    errors of order one.  Its pointwise box spline equals betaN."""
+    from paper_1003_2022_gb300 import synth
+    th = n6.directions(6)
+    a = np.array([1.3, 0.7, 2.1, 1.1, 0.9, 1.6])
+    for x in [(0.1, 0.2), (-0.5, 0.3), (1.0, -0.4), (0.0, 0.0), (3.0, 3.0)]:
+        assert n6.beta6_c(a, *x) == pytest.approx(float(n6.betaN(th, a, np.array(x[0]), np.array(x[1]))),
+                                                  rel=1e-12, abs=1e-14)
+    for h, (H, W) in ((0.5, (9, 11)), (0.25, (6, 7))):
+        f = synth.image(H, W, seed=2, dtype="f32").astype(np.float64)
+        A = synth.scale_field(H, W, seed=3, lo=0.8, hi=3.0)
+        A6 = np.concatenate([A, A[:2] * 0.9]).astype(np.float64)
+        idx = np.array([0, 5, W + 3, H * W // 2, H * W - 1])
+        c = n6.alg1_hex_c(f, A6, idx, h)
+        py = n6.alg1_hex(f, A6, idx, h)
+        ref = n6.direct6_hex(f, A6, idx, h)
+        assert np.abs(c - py).max() < 2e-8 * np.abs(py).max()
+        assert np.abs(c - ref).max() < 2e-8 * np.abs(ref).max()
+    # every pixel of a tiny image (idx = None)
+    f = synth.image(5, 6, seed=4, dtype="u8").astype(np.float64)
+    A6 = np.full((6, 5, 6), 1.4)
+    full = n6.alg1_hex_c(f, A6, None, 0.5)
+    assert np.abs(full - n6.direct6_hex(f, A6, None, 0.5)).max() < 2e-8 * np.abs(full).max()
