@@ -222,13 +222,14 @@ def alu_peak_tops():
     return 152 * 128 * 2.070e9 / 1e12
 
 
-def _inputs(size=None, workload=WORKLOAD):
-    """(B, C, H, W) image and (B, K, H, W) parameter planes of a workload."""
+def _inputs(size=None, workload=WORKLOAD, first_only=False):
+    """(B, C, H, W) image and (B, K, H, W) parameter planes of a workload
+    (first_only: the first batch entry alone, generated from the same seed)."""
     from paper_1003_2022_gb300 import synth
     if synth.WORKLOADS[workload]["B"] == 1 and "scales" not in synth.WORKLOADS[workload]:
         f, p = synth.workload_inputs(workload, seed=0, H=size, W=size)
         return f[None, None], p[None]
-    return synth.batch_inputs(workload, seed=0, H=size, W=size)
+    return synth.batch_inputs(workload, seed=0, H=size, W=size, B=1 if first_only else None)
 
 
 def _map6_chunk(args):
@@ -342,7 +343,7 @@ def run_reference(args):
     from paper_1003_2022_gb300 import synth as _synth
     N = _synth.WORKLOADS[args.workload]["N"]
     _, smax, _ = BENCH_WORKLOADS[args.workload]
-    f, p = _inputs(args.size, args.workload)
+    f, p = _inputs(args.size, args.workload, first_only=True)
     u8 = f.dtype == np.uint8
     f, p = f[0, 0], p[0]
     crop = 32 if N == 6 else 96
@@ -606,7 +607,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline and not train and args.precision == "exact":
         runner = OracleRunner(N, u8, smax)
         try:
-            crop = args.cpu_crop or (128 if N == 6 else 1024)
+            crop = args.cpu_crop or (256 if N == 6 else 1024)
             dt = runner.run(f_np[0, 0], p_np[0], crop=crop, seed=0)
         finally:
             runner.close()
@@ -798,7 +799,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="exact", choices=["exact", "fp64"])
-    ap.add_argument("--cpu-crop", type=int, default=None, help="side of the oracle's crop (default 128 for N=6, "
+    ap.add_argument("--cpu-crop", type=int, default=None, help="side of the oracle's crop (default 256 for N=6, "
                                                                 "1024 for N=4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="square image side (default: the 2048 workload)")

@@ -133,7 +133,10 @@ def test_scales_from_cov_parity(kind, accuracy_record):
                                        "max_rel_scale_err": worst,
                                        "p999_rel_scale_err": float(np.percentile(rel[ok], 99.9))}
     print(f"map4 {kind}: {len(report)} flag mismatches at thresholds, max rel scale error {worst:.3e}")
-    assert worst < 5e-5, worst
+    # FP32 map: a component much smaller than the largest is a difference of terms of the size of
+    # the covariance (its rounding, ~1e-7 of the largest p, is amplified by a_max / a_k in the
+    # width); measured 8.3e-6 on this field
+    assert worst < 2e-5, worst
     # the covariance of the GPU scales reproduces the target where no clamp applied
     sel = ok & (fl_ref == 0)
     pg = a_gpu[:, sel] ** 2
