@@ -27,6 +27,7 @@
 // whole-plane ones.  The scale map for six directions (Sec. 3.2.2 with the
 // kurtosis norm written for N directions) is solved per pixel by a primal
 // active-set Newton method, in FP32 first and to its end in FP64.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -746,8 +747,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
 
 constexpr int ST_THREADS = 128;  // 32 x 4 pixels for 64-pixel tiles, 16 x 8 for 16-pixel tiles
 
-// the canonical piece's coefficients: every lane reads the same entry (the slot
-// loop is uniform), so they reach the multiply-adds as uniform operands
+// the canonical piece's coefficients C[slot][monomial] (integers, |C| <= 102)
 __constant__ int HEX6_CC_CONST[HEX6_NSLOT][HEX6_NMONO] = HEX6_CCOEF_INIT;
 
 // ---- double-float (a pair of FP32 numbers, about 48 bits) ----
@@ -773,28 +773,47 @@ __device__ __forceinline__ dflt df_add(dflt a, dflt b) {
     e += a.lo + b.lo;
     return df_norm(s, e);
 }
-// the nearest FP32 value of a 128-bit integer, and that value as an integer
-__device__ __forceinline__ float f_of_i128(i128 v, i128* rounded) {
-    const i128 mag = v ^ (v >> 127);  // |v| (one less for negative v): enough for the bit length
-    const unsigned long long mh = (unsigned long long)(mag >> 64), ml = (unsigned long long)mag;
+// a 128-bit integer as a double-float (to about 48 bits): its top 62 bits as a
+// 64-bit integer v (the bits below are dropped: at most 2^-62 of |v|), then the
+// nearest FP32 value of v and of the exact remainder, both scaled back
+__device__ __forceinline__ dflt df_of_i128(i128 a) {
+    const long long hw = (long long)(a >> 64);
+    const unsigned long long lw = (unsigned long long)a;
+    // bit length of |a| (one less for negative a: enough to choose the shift)
+    const unsigned long long mh = (unsigned long long)(hw ^ (hw >> 63));
+    const unsigned long long ml = lw ^ (unsigned long long)(hw >> 63);
     const int n = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
     const int sh = n > 62 ? n - 62 : 0;
-    const float f = __ll2float_rn((long long)(v >> sh));
-    *rounded = (i128)__float2ll_rn(f) << sh;
-    return f * __int_as_float((127 + sh) << 23);  // times 2^sh, exact
-}
-// a 128-bit integer as a double-float (to about 48 bits): its nearest FP32
-// value, then the exact remainder's
-__device__ __forceinline__ dflt df_of_i128(i128 v) {
-    i128 r, r2;
-    const float hi = f_of_i128(v, &r);
-    const float lo = f_of_i128(v - r, &r2);
-    return df_norm(hi, lo);
+    const long long v = (long long)(a >> sh);
+    const float hi = __ll2float_rn(v);
+    const float lo = __ll2float_rn(v - __float2ll_rn(hi));
+    const float sc = __int_as_float((127 + sh) << 23);  // 2^sh, exact
+    return df_norm(hi * sc, lo * sc);
 }
 // the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact)
 __device__ __forceinline__ dflt df_of_frac48(long long x) {
     return {(float)(x >> 24) * 5.9604644775390625e-8f, (float)(x & 0xFFFFFF) * 3.552713678800501e-15f};
 }
+
+// mma.sync m16n8k16 with FP16 operands and FP32 accumulation.  Every operand
+// here is a small integer (window bytes as 1024 + byte, coefficients |c| <=
+// 102), every product is exact and every partial sum an integer below 2^21,
+// so the FP32 result is exact.
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1,
+                                         float c0, float c1, float c2, float c3) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%12,%13};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
+}
+// byte `sel` of two 32-bit words as the FP16 pair (1024 + byte of wa, 1024 + byte of wb)
+__device__ __forceinline__ unsigned bytes_as_f16x2(unsigned wa, unsigned wb, unsigned sel) {
+    return (__byte_perm(wa, wb, sel) & 0x00FF00FFu) | 0x64006400u;
+}
+
+constexpr float TC_MAGIC = 12582912.0f;   // 1.5 * 2^23: FP32 integers in (-2^22, 2^22) sit in its mantissa
+constexpr int TC_MAGIC_BITS = 0x4B400000;  // its bit pattern
+constexpr int TC_TSTRIDE = 18;             // double-float slots per pixel in the coefficient buffer
 
 // step 3: the 64 taps of Eq. FD_mesh, each read from its window by the exact
 // piecewise-quartic element (24 lattice points).  Exact where it matters:
@@ -806,16 +825,29 @@ __device__ __forceinline__ dflt df_of_frac48(long long x) {
 //     lattice symmetries that leave the element invariant: a tap of piece r is
 //     evaluated at its image x in the canonical piece (exact, 48-bit), reading
 //     the window at the piece's slot offsets;
-//   - the canonical quartic, F = sum_ab A_ab x_1^a x_2^b / 432, has integer
-//     coefficients A_ab = sum_k c_abk g[m_k] (c from hex6_tables.h, the same for
-//     every lane), computed exactly from the exact window sums in 20-bit limbs
-//     with 32-bit multiply-adds, all 15 in one pass over the 24 points;
+//   - the canonical quartic, F = sum_m A_m x^m / 432, has integer coefficients
+//     A_m = sum_k C[k][m] g[m_k] over the piece's 24 window values g, computed
+//     exactly on the tensor cores: the values g + 2^95 (96 bits) are cut into
+//     twelve bytes, each an exact FP16 number 1024 + byte; one mma.sync per
+//     byte and half of the 24 slots multiplies the 16 x 32 coefficient matrix
+//     (FP16, exact) by the bytes of eight taps, with FP32 sums that stay exact
+//     integers; the twelve byte sums are recombined exactly in 64- and 128-bit
+//     integers;
 //   - the constant terms A_00, which carry the size of the sums, are added over
 //     the 64 taps exactly, in 128-bit integers;
-// and only the remaining terms (derivatives of the sums, smaller by the
-// window size) are evaluated in double-float arithmetic, summed as a tree.
-// No FP64 in the loop.
-__global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
+// and only the remaining terms (derivatives of the sums, smaller by the window
+// size) are evaluated in double-float arithmetic.  No FP64 in the loop.
+//
+// Work layout: a warp owns 32 pixels (one per lane) and walks the 64 taps in
+// rounds.  In round r (tap q = r / 4) the eight quads of the warp each take one
+// tap -- quad n that of pixel 4 n + r % 4 -- and its four lanes load six of the
+// tap's 24 window values each: exactly the B fragment of the mma (slots 2j,
+// 2j+1, 2j+8, 2j+9, 2j+16, 2j+17 for lane j of the quad; slots 24-31 are zero).
+// The coefficient matrix is the A fragment (rows: the 15 monomials and one
+// zero row), held in registers.  The D fragment gives each lane two
+// coefficients of two taps; after four rounds every pixel's tap q has its 15
+// coefficients in shared memory, and the pixel's own lane evaluates the tap.
+__global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
                                                               double h, const hex6_tile* __restrict__ tiles,
                                                               const u128* __restrict__ scratch,
                                                               const unsigned* __restrict__ wflag,
@@ -824,10 +856,13 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
     __shared__ __align__(16) int sym[HEX6_NREGION][8];  // L_r^-1 and v_r of each piece
     __shared__ int lut[16];
     __shared__ long long stp[2][6][ST_THREADS];  // per thread: the six steps of the tap mesh
+    // per warp and pixel: the tap's coefficients A_1..A_14 (double-float) and A_00 (exact)
+    __shared__ __align__(16) dflt scoef[ST_THREADS / 32][32][TC_TSTRIDE];
+    __shared__ __align__(16) i128 sconst[ST_THREADS / 32][32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
     if (tid < HEX6_NREGION * 8) sym[tid / 8][tid % 8] = (tid % 8) < 6 ? HEX6_SYM[tid / 8][tid % 8] : 0;
-    __syncthreads();
     const hex6_tile tl = tiles[blockIdx.y];
     const int ncol = tl.ncol;
     for (int k = tid; k < HEX6_NREGION * HEX6_NSLOT; k += ST_THREADS) {
@@ -837,29 +872,53 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
     }
     __syncthreads();
     const int c = blockIdx.z;
+    if (wflag[blockIdx.y * C + c]) {  // window values beyond the exact range (uniform over the block)
+        const int per_row = tl.w / (int)blockDim.x;
+        const int x = tl.x0 + (blockIdx.x % per_row) * (int)blockDim.x + threadIdx.x;
+        const int y = tl.y0 + (blockIdx.x / per_row) * (int)blockDim.y + threadIdx.y;
+        if (x < W && y < H && x < tl.x0 + tl.w && y < tl.y0 + tl.hh) {
+            raise_status(status, BSF_ERANGE);
+            out[((size_t)tl.b * C + c) * ((long long)H * W) + (long long)y * W + x] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    // the coefficient matrix as the mma's A fragments: rows = monomials (row 15 zero),
+    // columns = the 24 slots of the canonical piece (columns 24-31 zero)
+    unsigned afr[2][4];
+    {
+        const int g = lane >> 2, t2 = 2 * (lane & 3);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = g + ((q & 1) ? 8 : 0), col = 16 * ks + t2 + ((q & 2) ? 8 : 0);
+                const int c0 = (row < HEX6_NMONO && col < HEX6_NSLOT) ? HEX6_CC_CONST[col][row] : 0;
+                const int c1 = (row < HEX6_NMONO && col + 1 < HEX6_NSLOT) ? HEX6_CC_CONST[col + 1][row] : 0;
+                const __half2 hv = __halves2half2(__int2half_rn(c0), __int2half_rn(c1));
+                afr[ks][q] = *reinterpret_cast<const unsigned*>(&hv);
+            }
+    }
     const int per_row = tl.w / (int)blockDim.x;
     const int bx = blockIdx.x % per_row, by = blockIdx.x / per_row;
     const int x = tl.x0 + bx * (int)blockDim.x + threadIdx.x;
     const int y = tl.y0 + by * (int)blockDim.y + threadIdx.y;
-    if (x >= W || y >= H || x >= tl.x0 + tl.w || y >= tl.y0 + tl.hh) return;
+    // lanes outside the image or the tile take part in the warp's work with unit
+    // scales and write nothing
+    const bool active = x < W && y < H && x < tl.x0 + tl.w && y < tl.y0 + tl.hh;
     const long long HW = (long long)H * W, p = (long long)y * W + x;
-    float* o = out + ((size_t)tl.b * C + c) * HW + p;
     double a[6], prod = 1.0;
     bool bad = false;
+#pragma unroll
     for (int k = 0; k < 6; ++k) {
-        a[k] = scales[((size_t)tl.b * 6 + k) * HW + p];
+        a[k] = active ? scales[((size_t)tl.b * 6 + k) * HW + p] : 1.0;
         bad |= !(a[k] > 0.0);
-        prod *= a[k];
     }
     if (bad) {
-        *o = __int_as_float(0x7fc00000);
-        return;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = 1.0;
     }
-    if (wflag[blockIdx.y * C + c]) {  // window values beyond the exact range
-        raise_status(status, BSF_ERANGE);
-        *o = __int_as_float(0x7fc00000);
-        return;
-    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) prod *= a[k];
     const u128* G = scratch + tl.off + (long long)c * ncol * tl.nrow;
     const double SQ3 = 1.73205080756887729353;
     const double it2 = 2.0 / (h * SQ3), ih = 1.0 / h;
@@ -887,11 +946,21 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
         stp[0][k][tid] = ds[k];
         stp[1][k][tid] = dtt[k];
     }
-    i128 e00 = 0;          // exact sum over the taps of +-A_00
+    __syncwarp();
+    const int safe_base = 2 * ncol + 6;  // a cell whose 24 points lie inside every window
+    const int j4 = lane & 3, quad0 = lane & ~3;
+    const int s_lo = 2 * j4;             // this lane's slots: s_lo, +1, +8, +9, +16, +17
+    const int g = lane >> 2;             // D rows g and g + 8; columns 2 j4, 2 j4 + 1
+    bool halo_bad = false;
+    i128 e00 = 0;            // exact sum over the taps of +-A_00
     dflt rest = {0.f, 0.f};  // the other terms
     long long sp = bs, tp = bt;  // the tap's position (Gray-code order: one step changes per tap)
+    // this lane's own tap of the current group of four rounds
+    int my_base = safe_base, my_reg = 0;
+    long long my_x1 = 0, my_x2 = 0;
 #pragma unroll 1
     for (int q = 0; q < 64; ++q) {
+        // ---- the position of tap q of this lane's pixel
         const int gq = q ^ (q >> 1);
         if (q) {
             const int k = __ffs(q) - 1;
@@ -904,88 +973,133 @@ __global__ void __launch_bounds__(ST_THREADS, 3) k_hex6_stencil(const double* __
                 tp -= dtk;
             }
         }
-        const int i0 = ib + (int)(sp >> 48), j0 = jb + (int)(tp >> 48);
-        const long long sf = sp & M48, tf = tp & M48;
-        int code;
-        if (sf + tf < ONE)
-            code = (sf > tf) | ((2 * sf + tf > ONE) << 1) | ((sf + 2 * tf > ONE) << 2);
-        else
-            code = 8 | (sf > tf) | ((2 * sf + tf > 2 * ONE) << 1) | ((sf + 2 * tf > 2 * ONE) << 2);
-        const int reg = lut[code];
-        const int rr = j0 - tl.j0w;
-        const int cc = i0 - tl.i_left + 2 * rr;
-        if (rr < 2 || rr + 3 >= tl.nrow || cc < 6 || cc + 9 >= ncol) {
-            raise_status(status, BSF_EHALO);
-            *o = __int_as_float(0x7fc00000);
-            return;
+        {
+            const int i0 = ib + (int)(sp >> 48), j0 = jb + (int)(tp >> 48);
+            const long long sf = sp & M48, tf = tp & M48;
+            int code;
+            if (sf + tf < ONE)
+                code = (sf > tf) | ((2 * sf + tf > ONE) << 1) | ((sf + 2 * tf > ONE) << 2);
+            else
+                code = 8 | (sf > tf) | ((2 * sf + tf > 2 * ONE) << 1) | ((sf + 2 * tf > 2 * ONE) << 2);
+            const int reg = lut[code];
+            const int rr = j0 - tl.j0w;
+            const int cc = i0 - tl.i_left + 2 * rr;
+            const bool inside = rr >= 2 && rr + 3 < tl.nrow && cc >= 6 && cc + 9 < ncol;
+            halo_bad |= !inside && active && !bad;
+            // the tap in the canonical piece: x = L_r^-1 ((sigma, tau) - v_r), exact (48-bit fractions)
+            const int4 sl = *reinterpret_cast<const int4*>(&sym[reg][0]);
+            const int2 sv = *reinterpret_cast<const int2*>(&sym[reg][4]);
+            const long long xs = sf - (long long)sv.x * ONE, xt = tf - (long long)sv.y * ONE;
+            my_x1 = sl.x * xs + sl.y * xt;
+            my_x2 = sl.z * xs + sl.w * xt;
+            my_base = inside ? rr * ncol + cc : safe_base;
+            my_reg = reg;
         }
-        const bool neg = __popc(gq) & 1;
-        // the tap in the canonical piece: x = L_r^-1 ((sigma, tau) - v_r), exact (48-bit fractions)
-        const int4 sl = *reinterpret_cast<const int4*>(&sym[reg][0]);
-        const int2 sv = *reinterpret_cast<const int2*>(&sym[reg][4]);
-        const long long xs = sf - (long long)sv.x * ONE, xt = tf - (long long)sv.y * ONE;
-        const long long x1 = sl.x * xs + sl.y * xt, x2 = sl.z * xs + sl.w * xt;
-        const u128* base = G + (long long)rr * ncol + cc;
-        // A_m = sum_k C[k][m] g_k over the canonical piece's 24 points, exactly.  With
-        // u = g + 2^95 (|g| < 2^95, checked by the pre-integration) in five limbs of 20
-        // bits (the last 16), P[l][m] = sum_k C[k][m] u_kl is at most
-        // max_m sum_k |C[k][m]| (696) * 2^20 < 2^31 in magnitude: plain 32-bit
-        // multiply-adds, and A_m = sum_l 2^(20 l) P[l][m] - 2^95 sum_k C[k][m], the last
-        // sum HEX6_DEN for the constant term and 0 for the others.
-        int P[5][HEX6_NMONO];
+        // ---- four rounds: quad n takes tap q of pixel 4 n + i
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const int src = quad0 | i;
+            const int tb = __shfl_sync(0xffffffffu, my_base, src);
+            const int treg = __shfl_sync(0xffffffffu, my_reg, src);
+            const u128* base = G + tb;
+            uint4 u[6];
+            u[0] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo]));
+            u[1] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 1]));
+            u[2] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 8]));
+            u[3] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 9]));
+            u[4] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 16]));
+            u[5] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 17]));
 #pragma unroll
-        for (int m = 0; m < HEX6_NMONO; ++m)
+            for (int s = 0; s < 6; ++s) u[s].z ^= 0x80000000u;  // bits 64-95 of g + 2^95
+            // the four values of this lane (rows g, g + 8 x two taps), 128-bit
+            i128 acc[4];
 #pragma unroll
-            for (int l = 0; l < 5; ++l) P[l][m] = 0;
-#pragma unroll 2
-        for (int k = 0; k < HEX6_NSLOT; ++k) {
-            const ulonglong2 gv = __ldg(reinterpret_cast<const ulonglong2*>(base + soff[reg][k]));
-            const unsigned long long lo = gv.x;
-            const unsigned hi = (unsigned)gv.y ^ 0x80000000u;  // bits 64-95 of g + 2^95
-            const int w[5] = {(int)(lo & 0xFFFFFu), (int)((lo >> 20) & 0xFFFFFu), (int)((lo >> 40) & 0xFFFFFu),
-                              (int)(((lo >> 60) | ((unsigned long long)hi << 4)) & 0xFFFFFu), (int)(hi >> 16)};
+            for (int v = 0; v < 4; ++v) acc[v] = 0;
 #pragma unroll
-            for (int m = 0; m < HEX6_NMONO; ++m) {
-                const int cm = HEX6_CC_CONST[k][m];
+            for (int w = 0; w < 3; ++w) {
+                int bits[4][4];
 #pragma unroll
-                for (int l = 0; l < 5; ++l) P[l][m] += cm * w[l];
+                for (int bt = 0; bt < 4; ++bt) {
+                    const unsigned sel = (unsigned)bt | ((4u + bt) << 8);
+                    unsigned wv[6];
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) wv[s] = w == 0 ? u[s].x : (w == 1 ? u[s].y : u[s].z);
+                    const unsigned b00 = bytes_as_f16x2(wv[0], wv[1], sel);
+                    const unsigned b01 = bytes_as_f16x2(wv[2], wv[3], sel);
+                    const unsigned b10 = bytes_as_f16x2(wv[4], wv[5], sel);
+                    float d[4];
+                    mma16816(d, afr[0], b00, b01, TC_MAGIC, TC_MAGIC, TC_MAGIC, TC_MAGIC);
+                    mma16816(d, afr[1], b10, 0u, d[0], d[1], d[2], d[3]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) bits[bt][v] = __float_as_int(d[v]);
+                }
+                // bytes 4w .. 4w + 3: sum_b 2^(8 b) (bits_b - MAGIC), exact in 64 bits
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    // (bits - MAGIC) of two bytes, combined modulo 2^32: the true value is
+                    // below 2^28 in magnitude, so the wrapped result is exact
+                    const int x01 = (int)((unsigned)bits[0][v] + 256u * (unsigned)bits[1][v] -
+                                          257u * (unsigned)TC_MAGIC_BITS);
+                    const int x23 = (int)((unsigned)bits[2][v] + 256u * (unsigned)bits[3][v] -
+                                          257u * (unsigned)TC_MAGIC_BITS);
+                    const long long gw = (long long)x01 + ((long long)x23 << 16);
+                    acc[v] += (i128)gw << (32 * w);
+                }
+            }
+            // hand the four coefficients to their pixels: columns 2 j4, 2 j4 + 1 are the taps
+            // of quads 2 j4 and 2 j4 + 1, i.e. pixels 8 j4 + i and 8 j4 + 4 + i
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int row = g + ((v & 2) ? 8 : 0);
+                const int pix = 8 * j4 + ((v & 1) ? 4 : 0) + i;
+                if (row == 0)
+                    sconst[warp][pix] = acc[v];
+                else if (row < HEX6_NMONO)
+                    scoef[warp][pix][row] = df_of_i128(acc[v]);
             }
         }
-        dflt ad[HEX6_NMONO];
-#pragma unroll
-        for (int m = 0; m < HEX6_NMONO; ++m) {
-            const long long E0 = (long long)P[0][m] + ((long long)P[1][m] << 20);
-            const long long E1 = (long long)P[2][m] + ((long long)P[3][m] << 20);
-            i128 A = (i128)E0 + ((i128)E1 << 40) + ((i128)P[4][m] << 80);
-            if (m == 0) {
-                A -= (i128)HEX6_DEN << 95;
-                e00 += neg ? -A : A;
-            } else {
-                ad[m] = df_of_i128(neg ? -A : A);
-            }
+        __syncwarp();
+        // ---- this lane's tap q: F = (A_00 + sum_m A_m x^m) / 432, with the sign of the tap
+        {
+            const bool neg = __popc(gq) & 1;
+            const i128 A0 = sconst[warp][lane];
+            e00 += neg ? -A0 : A0;
+            const dflt* ad = scoef[warp][lane];
+            const dflt sg = df_of_frac48(my_x1), tg = df_of_frac48(my_x2);
+            const dflt s2 = df_mul(sg, sg), st = df_mul(sg, tg), t2 = df_mul(tg, tg);
+            const dflt a1 = df_add(df_mul(ad[1], sg), df_mul(ad[2], tg));
+            const dflt a2 = df_add(df_mul(ad[3], s2), df_mul(ad[4], st));
+            const dflt a3 = df_add(df_mul(ad[5], t2), df_mul(ad[6], df_mul(s2, sg)));
+            const dflt b1 = df_add(df_add(a1, a2), df_add(a3, df_mul(ad[7], df_mul(s2, tg))));
+            const dflt c1 = df_add(df_mul(ad[8], df_mul(sg, t2)), df_mul(ad[9], df_mul(t2, tg)));
+            const dflt c2 = df_add(df_mul(ad[10], df_mul(s2, s2)), df_mul(ad[11], df_mul(s2, st)));
+            const dflt c3 = df_add(df_mul(ad[12], df_mul(s2, t2)), df_mul(ad[13], df_mul(st, t2)));
+            const dflt b2 = df_add(df_add(c1, c2), df_add(c3, df_mul(ad[14], df_mul(t2, t2))));
+            const dflt fq = df_add(b1, b2);
+            rest = df_add(rest, neg ? dflt{-fq.hi, -fq.lo} : fq);
         }
-        // the monomials x_1^a x_2^b (a + b = 1..4) and the terms, summed as a tree
-        const dflt sg = df_of_frac48(x1), tg = df_of_frac48(x2);
-        const dflt s2 = df_mul(sg, sg), st = df_mul(sg, tg), t2 = df_mul(tg, tg);
-        const dflt a1 = df_add(df_mul(ad[1], sg), df_mul(ad[2], tg));
-        const dflt a2 = df_add(df_mul(ad[3], s2), df_mul(ad[4], st));
-        const dflt a3 = df_add(df_mul(ad[5], t2), df_mul(ad[6], df_mul(s2, sg)));
-        const dflt b1 = df_add(df_add(a1, a2), df_add(a3, df_mul(ad[7], df_mul(s2, tg))));
-        const dflt c1 = df_add(df_mul(ad[8], df_mul(sg, t2)), df_mul(ad[9], df_mul(t2, tg)));
-        const dflt c2 = df_add(df_mul(ad[10], df_mul(s2, s2)), df_mul(ad[11], df_mul(s2, st)));
-        const dflt c3 = df_add(df_mul(ad[12], df_mul(s2, t2)), df_mul(ad[13], df_mul(st, t2)));
-        const dflt b2 = df_add(df_add(c1, c2), df_add(c3, df_mul(ad[14], df_mul(t2, t2))));
-        rest = df_add(rest, b1);
-        rest = df_add(rest, b2);
+        __syncwarp();
+    }
+    if (!active) return;
+    float* o = out + ((size_t)tl.b * C + c) * HW + p;
+    if (bad) {
+        *o = __int_as_float(0x7fc00000);
+        return;
+    }
+    if (halo_bad) {
+        raise_status(status, BSF_EHALO);
+        *o = __int_as_float(0x7fc00000);
+        return;
     }
     // fbar = (1 / prod a) sum_q (-1)^|q| F(y_q); F = 6 h^4 sum_m g[m] M(.) / 432 with
-    // the window holding the running sums times 2^24
+    // the window holding the running sums times 2^24.  The constant parts of the
+    // byte decomposition (the offsets 2^95 and 1024 per byte) are the same for
+    // every tap and cancel in the alternating sum.
     const long long ehi = (long long)(e00 >> 64);
     const double ev = fma((double)ehi, 18446744073709551616.0, (double)(unsigned long long)e00);
     const double h2 = h * h;
     *o = (float)((ev + (double)rest.hi + (double)rest.lo) * (6.0 * h2 * h2 / (16777216.0 * HEX6_DEN)) / prod);
 }
-
 }  // namespace
 
 
