@@ -98,6 +98,12 @@ typedef int bsf_status;
 #define BSF_PARAM_COV 1
 #define BSF_PARAM_SRT 2
 
+/* boundary conditions (the paper asks only for "appropriate boundary conditions", Sec. 2.1) */
+#define BSF_BOUNDARY_ZERO 0     /* f = 0 outside the image (default) */
+#define BSF_BOUNDARY_REFLECT 1  /* f extended by half-sample symmetric reflection: f[-1-i] = f[i],
+                                   f[n+i] = f[n-1-i], repeated with period 2n for footprints wider
+                                   than the image */
+
 /* arithmetic forms of the path */
 #define BSF_PREC_EXACT 0  /* integer pre-integration (int64 for u8; 128-bit fixed point with 32
                              fractional bits for f32) and an exact integer finite difference at
@@ -132,6 +138,11 @@ typedef struct {
                          [0, 1/6).  The 1e-5 accuracy of the six-directional path is stated for
                          the default: 0 leaves only eps, whose tiny widths cost the stencil's
                          rounded part accuracy (BSF_EINVAL outside the range). */
+    int boundary;     /* BSF_BOUNDARY_ZERO (default) or BSF_BOUNDARY_REFLECT: how the image is
+                         continued beyond its edges.  Honoured by bsf_filter, bsf_filter_host and
+                         bsf_filter_noalloc (N = 4 and 6); bsf_preintegrate / bsf_apply take no
+                         options and use zero; bsf_filter_backward returns BSF_EUNSUPPORTED for
+                         reflect. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -223,6 +234,19 @@ bsf_status bsf_scales_from_cov(bsf_ctx* ctx, const float* params, int kind, int6
  * for FP64). */
 bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, int precision,
                             size_t* bytes);
+
+/* Scratch the context needs for bsf_filter at this shape (the paper has no
+ * counterpart: this sizes the device memory a caller must leave free, or
+ * budget, before the first call).  Host-only: nothing is allocated or
+ * launched, ctx may be NULL.  N = 4: exact, given opts->halo or
+ * opts->max_scale (the pre-integrated buffers of one launch, the scan carries,
+ * and for opts->iterations > 1 the intermediate image).  N = 6: an upper bound
+ * from opts->max_scale (the windows depend on the per-pixel footprints; the
+ * planner never holds more than 8 GiB of windows at once).  Host buffers of
+ * bsf_filter_host are not included.  Errors: BSF_EINVAL (bad shape or kind,
+ * neither halo nor max_scale), BSF_EUNSUPPORTED (N). */
+bsf_status bsf_query_workspace(bsf_ctx* ctx, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,
+                               int kind, const bsf_opts* opts, size_t* bytes);
 
 /* Step (a), Algorithm 1 step 2 (RS1-RS4 of Sec. 3.1) for ONE H x W image:
  * writes the pre-integrated buffer (zero padding P on every side, every

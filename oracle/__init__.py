@@ -10,7 +10,10 @@ Every function follows a passage of Chaudhury, Munoz-Barrutia and Unser,
 * ``beta4`` / ``beta4_lines``: the four-directional radially-uniform box spline
   of Eq. (const) (Sec. 2.2.1), evaluated exactly in two independent ways.
 * ``direct4``: the plain definition fbar[n] = sum_k f[k] beta_{a(n)}(n-k)
-  (Eq. SVF_2D with the Dirac-comb image used to derive Eq. keyeqn).
+  (Eq. SVF_2D with the Dirac-comb image used to derive Eq. keyeqn);
+  ``pad_reflect`` / ``direct4_reflect``: the same with the image continued by
+  half-sample symmetric reflection instead of zeros (the paper leaves the
+  boundary condition open).
 * ``preint4_i64`` / ``preint4_f64``: Algorithm 1 step 2 (Sec. 3.1, RS1-RS4).
 * ``stencil4``: Algorithm 1 step 3 (Table 1, Eq. final_eqn, App. F).
 * ``direct4_iterated``: the iterated box-spline filter of Sec. 3.3.
@@ -176,6 +179,32 @@ def direct4(f, a, idx=None) -> np.ndarray:
     _load().bo_direct4(_ptr(f, _dp), H, W, _ptr(a, _dp),
                        _ptr(ii, _i64p) if ii is not None else None, n, _ptr(out, _dp))
     return out.reshape(H, W) if n < 0 else out
+
+
+def pad_reflect(f, P: int) -> np.ndarray:
+    """The image continued by half-sample symmetric reflection, P samples on
+    every side: f[-1-i] = f[i] and f[n+i] = f[n-1-i], repeated with period 2n
+    when P exceeds the image (reading R21 of the paper's open "appropriate
+    boundary conditions", Sec. 2.1; the zero extension is the default)."""
+    return np.pad(np.asarray(f), int(P), mode="symmetric")
+
+
+def direct4_reflect(f, a, idx=None) -> np.ndarray:
+    """O-direct with the reflected boundary: the plain definition on the image
+    padded by reflection (``pad_reflect``) far enough to hold every footprint,
+    evaluated at the original pixels (their scales; the pad's scales are never
+    used)."""
+    f = _d(f)
+    H, W = f.shape
+    a = _d(a)
+    P = int(np.ceil(0.5 * np.max(a[0] + (a[1] + a[3]) / SQRT2 + a[2]))) + 3
+    fp = pad_reflect(f, P)
+    ap = np.pad(a, ((0, 0), (P, P), (P, P)), mode="edge")
+    Wp = W + 2 * P
+    ii = np.arange(H * W) if idx is None else np.asarray(idx, np.int64).ravel()
+    jj = (ii // W + P) * Wp + (ii % W + P)
+    out = direct4(fp, ap, jj)
+    return out.reshape(H, W) if idx is None else out
 
 
 def adjoint4(g, a, idx) -> np.ndarray:

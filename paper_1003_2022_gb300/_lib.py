@@ -31,6 +31,9 @@ BSF_PARAM_SCALES = 0
 BSF_PARAM_COV = 1
 BSF_PARAM_SRT = 2
 
+BSF_BOUNDARY_ZERO = 0
+BSF_BOUNDARY_REFLECT = 1
+
 BSF_PREC_EXACT = 0
 BSF_PREC_FP64 = 1
 
@@ -39,7 +42,7 @@ EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
     "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward", "bsf_filter_host",
-    "bsf_host_sync", "bsf_structure_cov",
+    "bsf_host_sync", "bsf_structure_cov", "bsf_query_workspace",
 ]
 
 
@@ -54,6 +57,7 @@ class bsf_opts(ctypes.Structure):
         ("iterations", ctypes.c_int),
         ("hex_spacing", ctypes.c_float),
         ("rel_bound", ctypes.c_float),
+        ("boundary", ctypes.c_int),
     ]
 
 
@@ -112,6 +116,8 @@ def load(path: str | None = None):
     lib.bsf_structure_cov.restype = i32
     lib.bsf_structure_cov.argtypes = [vp, vp, i32, i64, i64, i64, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       vp, vp]
+    lib.bsf_query_workspace.restype = i32
+    lib.bsf_query_workspace.argtypes = [vp, i32, i64, i64, i64, i64, i32, i32, op, ctypes.POINTER(ctypes.c_size_t)]
     lib.bsf_status_string.restype = ctypes.c_char_p
     lib.bsf_status_string.argtypes = [i32]
     _lib = lib
@@ -160,6 +166,15 @@ def bsf_scales_from_cov(ctx, params, kind, npix, N, opts, scales, flags, stream)
 def bsf_buffer_bytes(dtype, H, W, N, halo, precision) -> int:
     n = ctypes.c_size_t()
     check(load().bsf_buffer_bytes(dtype, H, W, N, halo, precision, ctypes.byref(n)), "bsf_buffer_bytes")
+    return n.value
+
+
+def bsf_query_workspace(ctx, dtype, B, C, H, W, N, kind, opts) -> int:
+    """Scratch bytes the context needs for bsf_filter at this shape (host-only)."""
+    n = ctypes.c_size_t()
+    check(load().bsf_query_workspace(ctx, dtype, B, C, H, W, N, kind,
+                                     ctypes.byref(opts) if opts is not None else None, ctypes.byref(n)),
+          "bsf_query_workspace")
     return n.value
 
 

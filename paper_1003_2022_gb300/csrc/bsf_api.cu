@@ -121,6 +121,7 @@ void bsf_default_opts(bsf_opts* o) {
     o->iterations = 1;
     o->hex_spacing = 0.5f;
     o->rel_bound = 1e-3f;
+    o->boundary = BSF_BOUNDARY_ZERO;
 }
 
 const char* bsf_status_string(bsf_status s) {
@@ -307,33 +308,35 @@ static bsf_status resolve_halo(bsf_ctx* c, const float* params, int kind, int64_
 
 static cudaError_t run_scan(int mode, int dtype, const void* img, long long img_stride, int nimg, int H, int W, int P,
                             void* G, long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0,
-                            int Ws = 0) {
+                            int Ws = 0, int reflect = 0) {
     if (mode == MODE_U64)
         return launch_scan4<MODE_U64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st, col0, Ws);
+                                               work, st, col0, Ws, reflect);
     if (mode == MODE_U128)
         return launch_scan4<MODE_U128, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                              work, st, col0, Ws);
+                                              work, st, col0, Ws, reflect);
     if (dtype == BSF_U8)
         return launch_scan4<MODE_F64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st, col0, Ws);
+                                               work, st, col0, Ws, reflect);
     return launch_scan4<MODE_F64, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch, work, st,
-                                         col0, Ws);
+                                         col0, Ws, reflect);
 }
 
 static bool dims_ok(int64_t H, int64_t W) {
     return H > 0 && W > 0 && H <= (1 << 20) && W <= (1 << 20);
 }
 
-// one pass of the filter (the caller holds the context lock)
-static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
-                              const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
-                              float ascale = 1.f) {
-    const int64_t HW = H * W;
-    int P = 0;
-    bsf_status s = resolve_halo(c, params, kind, B, HW, o, st, &P);
-    if (s != BSF_OK) return s;
-    const int mode = mode_of(dtype, o.precision);
+// Buffer layout of the four-directional path for a batch: the padded buffer
+// per image, vertical strips where a row is wider than one band CTA holds, and
+// the images per launch (shared by filter_pass and bsf_query_workspace).
+struct n4_layout {
+    int mode, nstrip, Ws, Hp, Wp, pitch;
+    size_t per_img;  // bytes of one image's buffer
+    int64_t bchunk;  // batch entries per launch
+};
+static bsf_status n4_layout_of(int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int P, int precision,
+                               n4_layout* L) {
+    const int mode = mode_of(dtype, precision);
     // Rows wider than one band CTA can hold are cut into vertical strips.  The
     // filter at a pixel depends only on f inside its footprint, so each strip is
     // pre-integrated from the image columns it needs (its outputs +- P) and the
@@ -353,6 +356,24 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
     const size_t budget = (size_t)16 << 30;
     int64_t bchunk = std::max<int64_t>(1, (int64_t)(budget / (per_img * (size_t)C)));
     bchunk = std::min<int64_t>(bchunk, B);
+    *L = n4_layout{mode, nstrip, Ws, Hp, Wp, pitch, per_img, bchunk};
+    return BSF_OK;
+}
+
+// one pass of the filter (the caller holds the context lock)
+static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t B, int64_t C, int64_t H, int64_t W,
+                              const float* params, int kind, const bsf_opts& o, float* out, cudaStream_t st,
+                              float ascale = 1.f) {
+    const int64_t HW = H * W;
+    int P = 0;
+    bsf_status s = resolve_halo(c, params, kind, B, HW, o, st, &P);
+    if (s != BSF_OK) return s;
+    n4_layout lay;
+    const bsf_status ls = n4_layout_of(dtype, B, C, H, W, P, o.precision, &lay);
+    if (ls != BSF_OK) return ls;
+    const int mode = lay.mode, nstrip = lay.nstrip, Ws = lay.Ws, Hp = lay.Hp, Wp = lay.Wp, pitch = lay.pitch;
+    const size_t per_img = lay.per_img;
+    const int64_t bchunk = lay.bchunk;
     const int K = (kind == BSF_PARAM_SCALES) ? 4 : 3;
     const size_t esz = (dtype == BSF_U8) ? 1 : 4;
     for (int64_t b0 = 0; b0 < B; b0 += bchunk) {
@@ -368,7 +389,8 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
             const int ws = nstrip == 1 ? (int)W : std::min(Ws, (int)W - col0);
             BSF_TRY(prof_mark(c, 0, st));
             BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf,
-                             (long long)Hp * pitch, pitch, c->work, st, col0, nstrip == 1 ? 0 : ws));
+                             (long long)Hp * pitch, pitch, c->work, st, col0, nstrip == 1 ? 0 : ws,
+                             o.boundary == BSF_BOUNDARY_REFLECT));
             stencil_args a;
             a.col0 = col0;
             a.Ws = nstrip == 1 ? 0 : ws;
@@ -442,7 +464,7 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
         const hex6_chunk& ch = chunks[i];
         const int n = (int)(ch.last - ch.first);
         BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
-                                   c->h6_win, (unsigned*)c->h6_flag, st));
+                                   c->h6_win, (unsigned*)c->h6_flag, st, o.boundary == BSF_BOUNDARY_REFLECT));
         BSF_TRY(prof_mark(c, 1, st));
         BSF_TRY(launch_hex6_stencil((const double*)c->h6_scales, (int)C, (int)H, (int)W, tl[ch.first].w,
                                     tl[ch.first].hh, h, dt + ch.first, n, c->h6_win, (const unsigned*)c->h6_flag, out,
@@ -466,6 +488,7 @@ static bsf_status filter_args(bsf_ctx* c, const void* image, int dtype, int64_t 
     if (opts) *o = *opts;
     if (o->precision != BSF_PREC_EXACT && o->precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (o->iterations < 1 || o->iterations > 64) return BSF_EINVAL;
+    if (o->boundary != BSF_BOUNDARY_ZERO && o->boundary != BSF_BOUNDARY_REFLECT) return BSF_EINVAL;
     if (N == 6 && !(o->rel_bound >= 0.f && o->rel_bound < 1.f / 6.f)) return BSF_EINVAL;
     if (N == 6 && !(o->hex_spacing == 1.f || o->hex_spacing == 0.5f || o->hex_spacing == 0.25f ||
                     o->hex_spacing == 0.125f))
@@ -516,6 +539,55 @@ static bsf_status filter_locked(bsf_ctx* c, const void* image, int dtype, int64_
         BSF_TRY(cudaStreamSynchronize(st));
         if (h & (1u << BSF_EINFEASIBLE)) return BSF_EINFEASIBLE;
     }
+    return BSF_OK;
+}
+
+bsf_status bsf_query_workspace(bsf_ctx* c, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N, int kind,
+                               const bsf_opts* opts, size_t* bytes) {
+    (void)c;
+    if (!bytes || B <= 0 || C <= 0 || !dims_ok(H, W)) return BSF_EINVAL;
+    if (dtype != BSF_U8 && dtype != BSF_F32) return BSF_EINVAL;
+    if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
+    if (N != 4 && N != 6) return BSF_EUNSUPPORTED;
+    bsf_opts o;
+    bsf_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.iterations < 1 || o.iterations > 64) return BSF_EINVAL;
+    const int64_t HW = H * W;
+    size_t total = o.iterations > 1 ? (size_t)B * C * HW * sizeof(float) : 0;  // intermediate image
+    if (N == 4) {
+        int P = o.halo;
+        if (P <= 0) {
+            // the halo rule of the filter; without halo or max_scale it depends on the field
+            if (!(o.max_scale > 0.f) || o.max_scale > 1e5f) return BSF_EINVAL;
+            const float ext = (kind == BSF_PARAM_SCALES) ? 2.41422f * o.max_scale : 8.3640f * o.max_scale;
+            P = (int)ceilf(0.5f * ext) + 4;
+        }
+        if (P > kMaxHalo) return BSF_EINVAL;
+        n4_layout lay;
+        const bsf_status ls = n4_layout_of(dtype, B, C, H, W, P, o.precision, &lay);
+        if (ls != BSF_OK) return ls;
+        const int nimg = (int)(lay.bchunk * C);
+        const scan_plan plan = make_scan_plan(lay.Hp, lay.Wp, nimg, elem_bytes(lay.mode));
+        if (!plan.ok) return BSF_EINVAL;
+        total += lay.per_img * (size_t)nimg + plan.work_bytes;
+    } else {
+        // an upper bound: the per-pixel scales and block extents, and windows of
+        // 16 x 16 tiles at the largest footprint the bound allows (the planner's
+        // 64-pixel tiles and tile groups need less per pixel), capped by its 8 GiB
+        // chunk; tile records and window flags for every 16 x 16 tile
+        if (!(o.max_scale > 0.f) || o.max_scale > 1e5f) return BSF_EINVAL;
+        const double amax = kind == BSF_PARAM_SCALES ? (double)o.max_scale : sqrt(24.0) * o.max_scale;
+        const double e = 0.5 * amax * 3.7320508075688772;  // sum_k |cos theta_k| = sum_k sin theta_k = 2 + sqrt3
+        const int64_t tiles = B * ((H + 15) / 16) * ((W + 15) / 16);
+        hex6_tile t;
+        hex6_window(0, 0, 16, 16, (int)H, (int)W, e, e, (double)o.hex_spacing, &t);
+        const double win = (double)tiles * C * t.ncol * t.nrow * 16.0;
+        total += (size_t)B * 6 * HW * sizeof(double) + (size_t)tiles * 2 * sizeof(unsigned) +
+                 (size_t)tiles * (sizeof(hex6_tile) + C * sizeof(unsigned)) +
+                 (size_t)std::min(win, (double)((size_t)8 << 30));
+    }
+    *bytes = total;
     return BSF_OK;
 }
 
@@ -673,6 +745,7 @@ bsf_status bsf_filter_backward(bsf_ctx* c, const void* image, int dtype, int64_t
     bsf_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != BSF_PREC_EXACT) return BSF_EUNSUPPORTED;
+    if (o.boundary != BSF_BOUNDARY_ZERO) return BSF_EUNSUPPORTED;  // the adjoint is written for f = 0 outside
     if (o.iterations < 1 || o.iterations > 64) return BSF_EINVAL;
     std::lock_guard<std::mutex> lock(c->mu);
     BSF_TRY(cudaSetDevice(c->device));

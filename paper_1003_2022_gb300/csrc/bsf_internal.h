@@ -29,10 +29,20 @@ int scan_max_width(size_t elem_bytes, bool narrow = false);
 // Pre-integration (RS1-RS4) of nimg images of H x W (stride img_stride
 // elements) into buffers of Hp x pitch elements (stride G_stride elements).
 // The buffer covers the image columns [col0 - P, col0 + Ws + P) (Ws <= 0:
-// the whole width, col0 = 0), f taken as zero outside the image.
+// the whole width, col0 = 0), f taken as zero outside the image, or (reflect)
+// as its half-sample symmetric extension over the whole buffer.
 template <int MODE, class InT>
 cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
-                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0, int Ws = 0);
+                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0, int Ws = 0,
+                         int reflect = 0);
+
+// index i of the half-sample symmetric extension of 0..n-1 (period 2n: -1 -> 0, n -> n-1)
+__host__ __device__ __forceinline__ int reflect_index(int i, int n) {
+    const int p = 2 * n;
+    int k = i % p;
+    if (k < 0) k += p;
+    return k < n ? k : p - 1 - k;
+}
 
 struct stencil_args {
     int col0 = 0;          // first output column of the strip the buffer covers
@@ -109,7 +119,8 @@ cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int 
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, double rel,
                             float* scales, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st);
+                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st,
+                               int reflect = 0);
 cudaError_t launch_hex6_stencil(const double* scales, int C, int H, int W, int tile_w, int tile_h, double h,
                                 const hex6_tile* tiles, int ntiles, const void* scratch, const unsigned* wflag,
                                 float* out, unsigned* status, cudaStream_t st);

@@ -589,7 +589,8 @@ __device__ __forceinline__ int pidx(int c) { return c + c / PRE_CPT; }
 template <class InT>
 __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restrict__ img, int C, int H, int W,
                                                              double h, const hex6_tile* __restrict__ tiles,
-                                                             u128* __restrict__ scratch, unsigned* __restrict__ wflag) {
+                                                             u128* __restrict__ scratch, unsigned* __restrict__ wflag,
+                                                             int reflect) {
     extern __shared__ u128 smq[];
     const hex6_tile tl = tiles[blockIdx.x];
     const int c = blockIdx.y;
@@ -638,14 +639,20 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
                 const float dx0 = kxf - px;
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
-                    const int ky = ky0 + dy;
-                    if (ky < 0 || ky >= H) continue;
+                    int ky = ky0 + dy;
+                    if (reflect)
+                        ky = reflect_index(ky, H);  // the image's half-sample symmetric extension
+                    else if (ky < 0 || ky >= H)
+                        continue;
                     const float ddy = (dy0 + (float)dy) * ih;
                     const float dt = 2.f * rs3 * ddy;
 #pragma unroll
                     for (int dx = 0; dx < 2; ++dx) {
-                        const int kx = kx0 + dx;
-                        if (kx < 0 || kx >= W) continue;
+                        int kx = kx0 + dx;
+                        if (reflect)
+                            kx = reflect_index(kx, W);
+                        else if (kx < 0 || kx >= W)
+                            continue;
                         // lattice coordinates of pixel - lattice point; weight = the hat of the point
                         const float ds = (dx0 + (float)dx) * ih - rs3 * ddy;
                         const float w = 1.f - fmaxf(fabsf(ds), fmaxf(fabsf(dt), fabsf(ds + dt)));
@@ -773,6 +780,18 @@ __device__ __forceinline__ dflt df_add(dflt a, dflt b) {
     e += a.lo + b.lo;
     return df_norm(s, e);
 }
+// a * b + c in double-float
+__device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    e += (p - (s - bb)) + (c.hi - bb);
+    e += c.lo;
+    return df_norm(s, e);
+}
 // a 128-bit integer as a double-float (to about 48 bits): its top 62 bits as a
 // 64-bit integer v (the bits below are dropped: at most 2^-62 of |v|), then the
 // nearest FP32 value of v and of the exact remainder, both scaled back
@@ -813,7 +832,7 @@ __device__ __forceinline__ unsigned bytes_as_f16x2(unsigned wa, unsigned wb, uns
 
 constexpr float TC_MAGIC = 12582912.0f;   // 1.5 * 2^23: FP32 integers in (-2^22, 2^22) sit in its mantissa
 constexpr int TC_MAGIC_BITS = 0x4B400000;  // its bit pattern
-constexpr int TC_TSTRIDE = 18;             // double-float slots per pixel in the coefficient buffer
+constexpr int TC_PSTRIDE = 17;             // 128-bit slots per pixel in the coefficient buffer
 
 // step 3: the 64 taps of Eq. FD_mesh, each read from its window by the exact
 // piecewise-quartic element (24 lattice points).  Exact where it matters:
@@ -856,9 +875,10 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __
     __shared__ __align__(16) int sym[HEX6_NREGION][8];  // L_r^-1 and v_r of each piece
     __shared__ int lut[16];
     __shared__ long long stp[2][6][ST_THREADS];  // per thread: the six steps of the tap mesh
-    // per warp and pixel: the tap's coefficients A_1..A_14 (double-float) and A_00 (exact)
-    __shared__ __align__(16) dflt scoef[ST_THREADS / 32][32][TC_TSTRIDE];
-    __shared__ __align__(16) i128 sconst[ST_THREADS / 32][32];
+    // per warp and pixel: the tap's 16 coefficient rows, exact.  Row m of pixel P sits in slot
+    // m ^ (2 (P >> 3)) of a 17-slot record: the four lanes that write the same row of
+    // different pixels, and the eight consecutive pixels that read, hit distinct banks.
+    __shared__ __align__(16) i128 scoefx[ST_THREADS / 32][32][TC_PSTRIDE];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
@@ -1011,71 +1031,75 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __
             u[5] = __ldg(reinterpret_cast<const uint4*>(base + soff[treg][s_lo + 17]));
 #pragma unroll
             for (int s = 0; s < 6; ++s) u[s].z ^= 0x80000000u;  // bits 64-95 of g + 2^95
-            // the four values of this lane (rows g, g + 8 x two taps), 128-bit
-            i128 acc[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = 0;
+            // the four values of this lane (rows g, g + 8 x two taps): per group of four
+            // bytes, gsum[w][v] = sum_b 2^(8 b) (byte sum b), exact in 64 bits
+            long long gsum[3][4];
 #pragma unroll
             for (int w = 0; w < 3; ++w) {
-                int bits[4][4];
+                unsigned b00[4], b01[4], b10[4];
 #pragma unroll
                 for (int bt = 0; bt < 4; ++bt) {
                     const unsigned sel = (unsigned)bt | ((4u + bt) << 8);
                     unsigned wv[6];
 #pragma unroll
-                    for (int s = 0; s < 6; ++s) wv[s] = w == 0 ? u[s].x : (w == 1 ? u[s].y : u[s].z);
-                    const unsigned b00 = bytes_as_f16x2(wv[0], wv[1], sel);
-                    const unsigned b01 = bytes_as_f16x2(wv[2], wv[3], sel);
-                    const unsigned b10 = bytes_as_f16x2(wv[4], wv[5], sel);
-                    float d[4];
-                    mma16816(d, afr[0], b00, b01, TC_MAGIC, TC_MAGIC, TC_MAGIC, TC_MAGIC);
-                    mma16816(d, afr[1], b10, 0u, d[0], d[1], d[2], d[3]);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) bits[bt][v] = __float_as_int(d[v]);
+                    for (int s6 = 0; s6 < 6; ++s6) wv[s6] = w == 0 ? u[s6].x : (w == 1 ? u[s6].y : u[s6].z);
+                    b00[bt] = bytes_as_f16x2(wv[0], wv[1], sel);
+                    b01[bt] = bytes_as_f16x2(wv[2], wv[3], sel);
+                    b10[bt] = bytes_as_f16x2(wv[4], wv[5], sel);
                 }
-                // bytes 4w .. 4w + 3: sum_b 2^(8 b) (bits_b - MAGIC), exact in 64 bits
+                float d[4][4];
+#pragma unroll
+                for (int bt = 0; bt < 4; ++bt)
+                    mma16816(d[bt], afr[0], b00[bt], b01[bt], TC_MAGIC, TC_MAGIC, TC_MAGIC, TC_MAGIC);
+#pragma unroll
+                for (int bt = 0; bt < 4; ++bt)
+                    mma16816(d[bt], afr[1], b10[bt], 0u, d[bt][0], d[bt][1], d[bt][2], d[bt][3]);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     // (bits - MAGIC) of two bytes, combined modulo 2^32: the true value is
                     // below 2^28 in magnitude, so the wrapped result is exact
-                    const int x01 = (int)((unsigned)bits[0][v] + 256u * (unsigned)bits[1][v] -
-                                          257u * (unsigned)TC_MAGIC_BITS);
-                    const int x23 = (int)((unsigned)bits[2][v] + 256u * (unsigned)bits[3][v] -
-                                          257u * (unsigned)TC_MAGIC_BITS);
-                    const long long gw = (long long)x01 + ((long long)x23 << 16);
-                    acc[v] += (i128)gw << (32 * w);
+                    const unsigned b0 = __float_as_uint(d[0][v]), b1 = __float_as_uint(d[1][v]);
+                    const unsigned b2 = __float_as_uint(d[2][v]), b3 = __float_as_uint(d[3][v]);
+                    const int x01 = (int)(b0 + 256u * b1 - 257u * (unsigned)TC_MAGIC_BITS);
+                    const int x23 = (int)(b2 + 256u * b3 - 257u * (unsigned)TC_MAGIC_BITS);
+                    gsum[w][v] = (long long)x01 + (long long)x23 * 65536;
                 }
             }
             // hand the four coefficients to their pixels: columns 2 j4, 2 j4 + 1 are the taps
-            // of quads 2 j4 and 2 j4 + 1, i.e. pixels 8 j4 + i and 8 j4 + 4 + i
+            // of quads 2 j4 and 2 j4 + 1, i.e. pixels 8 j4 + i and 8 j4 + 4 + i.  The value is
+            // gsum0 + 2^32 gsum1 + 2^64 gsum2, assembled from 64-bit halves with one carry.
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
+                const unsigned long long g0 = (unsigned long long)gsum[0][v];
+                const unsigned long long lo = g0 + ((unsigned long long)gsum[1][v] << 32);
+                const unsigned long long carry = lo < g0 ? 1ull : 0ull;
+                const unsigned long long hi = (unsigned long long)(gsum[0][v] >> 63) +
+                                              (unsigned long long)(gsum[1][v] >> 32) +
+                                              (unsigned long long)gsum[2][v] + carry;
                 const int row = g + ((v & 2) ? 8 : 0);
                 const int pix = 8 * j4 + ((v & 1) ? 4 : 0) + i;
-                if (row == 0)
-                    sconst[warp][pix] = acc[v];
-                else if (row < HEX6_NMONO)
-                    scoef[warp][pix][row] = df_of_i128(acc[v]);
+                scoefx[warp][pix][row ^ (2 * j4)] = (i128)(((u128)hi << 64) | lo);
             }
         }
         __syncwarp();
-        // ---- this lane's tap q: F = (A_00 + sum_m A_m x^m) / 432, with the sign of the tap
+        // ---- this lane's tap q: F = (A_00 + sum_m A_m x^m) / 432, with the sign of the tap;
+        // the quartic by Horner's rule in x1 over polynomials in x2 (monomial order of the
+        // tables: 1, x1, x2, x1^2, x1 x2, x2^2, x1^3, x1^2 x2, x1 x2^2, x2^3, x1^4, ...)
         {
             const bool neg = __popc(gq) & 1;
-            const i128 A0 = sconst[warp][lane];
+            const i128* rec = scoefx[warp][lane];
+            const int sw = 2 * (lane >> 3);
+            const i128 A0 = rec[0 ^ sw];
             e00 += neg ? -A0 : A0;
-            const dflt* ad = scoef[warp][lane];
+            dflt ad[HEX6_NMONO];
+#pragma unroll
+            for (int m = 1; m < HEX6_NMONO; ++m) ad[m] = df_of_i128(rec[m ^ sw]);
             const dflt sg = df_of_frac48(my_x1), tg = df_of_frac48(my_x2);
-            const dflt s2 = df_mul(sg, sg), st = df_mul(sg, tg), t2 = df_mul(tg, tg);
-            const dflt a1 = df_add(df_mul(ad[1], sg), df_mul(ad[2], tg));
-            const dflt a2 = df_add(df_mul(ad[3], s2), df_mul(ad[4], st));
-            const dflt a3 = df_add(df_mul(ad[5], t2), df_mul(ad[6], df_mul(s2, sg)));
-            const dflt b1 = df_add(df_add(a1, a2), df_add(a3, df_mul(ad[7], df_mul(s2, tg))));
-            const dflt c1 = df_add(df_mul(ad[8], df_mul(sg, t2)), df_mul(ad[9], df_mul(t2, tg)));
-            const dflt c2 = df_add(df_mul(ad[10], df_mul(s2, s2)), df_mul(ad[11], df_mul(s2, st)));
-            const dflt c3 = df_add(df_mul(ad[12], df_mul(s2, t2)), df_mul(ad[13], df_mul(st, t2)));
-            const dflt b2 = df_add(df_add(c1, c2), df_add(c3, df_mul(ad[14], df_mul(t2, t2))));
-            const dflt fq = df_add(b1, b2);
+            const dflt p0 = df_mul(tg, df_fma(tg, df_fma(tg, df_fma(tg, ad[14], ad[9]), ad[5]), ad[2]));
+            const dflt p1 = df_fma(tg, df_fma(tg, df_fma(tg, ad[13], ad[8]), ad[4]), ad[1]);
+            const dflt p2 = df_fma(tg, df_fma(tg, ad[12], ad[7]), ad[3]);
+            const dflt p3 = df_fma(tg, ad[11], ad[6]);
+            const dflt fq = df_fma(sg, df_fma(sg, df_fma(sg, df_fma(sg, ad[10], p3), p2), p1), p0);
             rest = df_add(rest, neg ? dflt{-fq.hi, -fq.lo} : fq);
         }
         __syncwarp();
@@ -1121,7 +1145,8 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 }
 
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
-                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st) {
+                               int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st,
+                               int reflect) {
     const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
     // as many threads as the widest window of the chunk needs (PRE_CPT columns each, whole
     // warps): narrow windows take small blocks, several of them per SM
@@ -1136,11 +1161,11 @@ cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int 
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
         k_hex6_preint<uint8_t><<<grid, nthr, smem, st>>>((const uint8_t*)img, C, H, W, h, tiles, (u128*)scratch,
-                                                                 wflag);
+                                                                 wflag, reflect);
     } else {
         cudaFuncSetAttribute(k_hex6_preint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);
         k_hex6_preint<float><<<grid, nthr, smem, st>>>((const float*)img, C, H, W, h, tiles, (u128*)scratch,
-                                                               wflag);
+                                                               wflag, reflect);
     }
     return cudaGetLastError();
 }

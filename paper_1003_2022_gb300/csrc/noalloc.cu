@@ -40,6 +40,8 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     if (kind != BSF_PARAM_SCALES && kind != BSF_PARAM_COV && kind != BSF_PARAM_SRT) return BSF_EINVAL;
     if (opts->precision != BSF_PREC_EXACT && opts->precision != BSF_PREC_FP64) return BSF_EINVAL;
     if (opts->iterations > 1) return BSF_EINVAL;
+    if (opts->boundary != BSF_BOUNDARY_ZERO && opts->boundary != BSF_BOUNDARY_REFLECT) return BSF_EINVAL;
+    const int refl = opts->boundary == BSF_BOUNDARY_REFLECT;
     if (N != 4) return BSF_EUNSUPPORTED;
     // the halo must come from the options (no device reduction, which would need a result word)
     int P = opts->halo;
@@ -81,16 +83,16 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     // read, so nothing left from a previous call needs clearing
     if (mode == MODE_U64)
         e = launch_scan4<MODE_U64, uint8_t>((const uint8_t*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                            work, st);
+                                            work, st, 0, 0, refl);
     else if (mode == MODE_U128)
         e = launch_scan4<MODE_U128, float>((const float*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                           work, st);
+                                           work, st, 0, 0, refl);
     else if (dtype == BSF_U8)
         e = launch_scan4<MODE_F64, uint8_t>((const uint8_t*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                            work, st);
+                                            work, st, 0, 0, refl);
     else
         e = launch_scan4<MODE_F64, float>((const float*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                          work, st);
+                                          work, st, 0, 0, refl);
     if (e != cudaSuccess) return BSF_ECUDA;
     stencil_args a;
     a.buf = G;

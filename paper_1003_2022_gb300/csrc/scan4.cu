@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
                                                int col0, int P, int Hp, int Wp, int pitch, int band_h, int nb,
                                                const typename mode_traits<MODE>::T* __restrict__ carry,
                                                typename mode_traits<MODE>::T* __restrict__ local,
-                                               typename mode_traits<MODE>::T* __restrict__ G, long long G_stride) {
+                                               typename mode_traits<MODE>::T* __restrict__ G, long long G_stride,
+                                               int reflect) {
     typedef typename mode_traits<MODE>::T T;
     const int b = blockIdx.x, im = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -90,7 +91,11 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
             const int ic = c0 + j - P + col0;
-            dst[j] = (y < y1 && iy >= 0 && iy < H && ic >= 0 && ic < W) ? f[(size_t)iy * W + ic] : InT(0);
+            if (reflect)  // the symmetric extension fills the whole buffer (columns c0 + j < Wp)
+                dst[j] = (y < y1 && c0 + j < Wp) ? f[(size_t)reflect_index(iy, H) * W + reflect_index(ic, W)]
+                                                 : InT(0);
+            else
+                dst[j] = (y < y1 && iy >= 0 && iy < H && ic >= 0 && ic < W) ? f[(size_t)iy * W + ic] : InT(0);
         }
     };
     InT pre[D][CPT];
@@ -379,31 +384,31 @@ int scan_max_width(size_t elem_bytes, bool narrow) {
 template <int MODE, class InT, int CPT>
 static void launch_band(const scan_plan& p, const InT* img, long long img_stride, int nimg, int H, int W, int col0,
                         int P, int Hp, int Wp, int pitch, const void* carry, void* local, void* G, long long G_stride,
-                        cudaStream_t st) {
+                        cudaStream_t st, int reflect) {
     typedef typename mode_traits<MODE>::T T;
     // allow up to 96 KiB of g2 state; the attribute belongs to the current device, so it is
     // set on every launch (a cheap host call) rather than once per process
     cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     dim3 grid(p.nb, nimg);
     k_band<MODE, InT, CPT><<<grid, p.threads, p.smem, st>>>(img, img_stride, H, W, col0, P, Hp, Wp, pitch, p.band_h, p.nb,
-                                                        (const T*)carry, (T*)local, (T*)G, G_stride);
+                                                        (const T*)carry, (T*)local, (T*)G, G_stride, reflect);
 }
 
 template <int MODE, class InT>
 static void launch_band_cpt(const scan_plan& p, const InT* img, long long img_stride, int nimg, int H, int W, int col0,
                             int P, int Hp, int Wp, int pitch, const void* carry, void* local, void* G,
-                            long long G_stride, cudaStream_t st) {
+                            long long G_stride, cudaStream_t st, int reflect) {
     switch (p.cpt) {
-        case 1: launch_band<MODE, InT, 1>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st); break;
-        case 2: launch_band<MODE, InT, 2>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st); break;
-        case 4: launch_band<MODE, InT, 4>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st); break;
-        default: launch_band<MODE, InT, 8>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st); break;
+        case 1: launch_band<MODE, InT, 1>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st, reflect); break;
+        case 2: launch_band<MODE, InT, 2>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st, reflect); break;
+        case 4: launch_band<MODE, InT, 4>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st, reflect); break;
+        default: launch_band<MODE, InT, 8>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, carry, local, G, G_stride, st, reflect); break;
     }
 }
 
 template <int MODE, class InT>
 cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
-                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0, int Ws) {
+                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0, int Ws, int reflect) {
     typedef typename mode_traits<MODE>::T T;
     if (Ws <= 0) Ws = W;
     const int Hp = H + 2 * P, Wp = Ws + 2 * P;
@@ -416,7 +421,8 @@ cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, 
     T* PP1 = P1 + row;
     T* Q1 = PP1 + row;
     T* P2 = Q1 + row;
-    launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, nullptr, L, nullptr, 0, st);
+    launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, nullptr, L, nullptr, 0, st,
+                               reflect);
     const int nlines = Wp + (Hp - min(p.band_h, Hp));  // diagonal / anti-diagonal lines crossing the band ends
     const int wpb = 8;                                 // warps (lines) per 256-thread block
     k_scan_s1<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, Hp, Wp, p.band_h, p.nb);
@@ -425,15 +431,16 @@ cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, 
     k_scan_s2<T><<<dim3((Wp + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, Hp, Wp, p.band_h, p.nb);
     k_prefix2<T, 8><<<dim3(p.nb, nimg), pthreads, 0, st>>>(S, P2, Wp, p.nb);
     k_scan_sg<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, PP1, Q1, P2, Hp, Wp, p.band_h, p.nb);
-    launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, S, nullptr, G, G_stride, st);
+    launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, S, nullptr, G, G_stride, st,
+                               reflect);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_scan4<MODE_U64, uint8_t>(const uint8_t*, long long, int, int, int, int, void*, long long,
-                                                     int, void*, cudaStream_t, int, int);
+                                                     int, void*, cudaStream_t, int, int, int);
 template cudaError_t launch_scan4<MODE_U128, float>(const float*, long long, int, int, int, int, void*, long long, int,
-                                                    void*, cudaStream_t, int, int);
+                                                    void*, cudaStream_t, int, int, int);
 template cudaError_t launch_scan4<MODE_F64, uint8_t>(const uint8_t*, long long, int, int, int, int, void*, long long,
-                                                     int, void*, cudaStream_t, int, int);
+                                                     int, void*, cudaStream_t, int, int, int);
 template cudaError_t launch_scan4<MODE_F64, float>(const float*, long long, int, int, int, int, void*, long long, int,
-                                                   void*, cudaStream_t, int, int);
+                                                   void*, cudaStream_t, int, int, int);

@@ -6,6 +6,8 @@ buffer sizes, status strings, argument validation) are exercised.
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -87,3 +89,33 @@ def test_halo_bounds_rejected_before_any_device_call(lib):
     assert e.value.code == lib.BSF_EINVAL
     assert lib.bsf_buffer_bytes(lib.BSF_U8, 1 << 20, 1 << 20, 4, 1 << 20, lib.BSF_PREC_EXACT) \
         == (3 << 20) * (3 << 20) * 8
+
+
+def test_query_workspace_host_only(lib):
+    """bsf_query_workspace needs no context and no device: the N=4 figure is the
+    pre-integrated buffers of one launch plus the scan carries; N=6 a bound."""
+    o = lib.default_opts()
+    o.max_scale = 32.0
+    n4 = lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 2048, 2048, 4, lib.BSF_PARAM_SRT, o)
+    P = int(np.ceil(0.5 * 8.364 * 32)) + 4
+    Lp = 2048 + 2 * P
+    buf = Lp * Lp * 8
+    carries = 10 * (-(-Lp // 8)) * Lp * 8  # ten carry rows per band, bands of at least 8 rows
+    assert buf <= n4 <= buf + carries
+    n4f = lib.bsf_query_workspace(None, lib.BSF_F32, 1, 1, 2048, 2048, 4, lib.BSF_PARAM_SRT, o)
+    assert n4f > 1.9 * buf  # 16-byte elements
+    o.iterations = 2
+    assert lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 2048, 2048, 4, lib.BSF_PARAM_SRT, o) == n4 + 2048 * 2048 * 4
+    o.iterations = 1
+    o.max_scale = 48.0
+    n6 = lib.bsf_query_workspace(None, lib.BSF_F32, 4, 3, 4096, 4096, 6, lib.BSF_PARAM_SRT, o)
+    assert n6 >= 4 * 6 * 4096 * 4096 * 8
+    o.max_scale = 0.0
+    with pytest.raises(lib.BsfError) as e:
+        lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 64, 64, 4, lib.BSF_PARAM_SRT, o)
+    assert e.value.code == lib.BSF_EINVAL
+    o.halo = 20
+    assert lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 64, 64, 4, lib.BSF_PARAM_SRT, o) >= 104 * 104 * 8
+    with pytest.raises(lib.BsfError) as e:
+        lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 64, 64, 5, lib.BSF_PARAM_SRT, o)
+    assert e.value.code == lib.BSF_EUNSUPPORTED

@@ -300,3 +300,26 @@ def test_paper_eps_bound_error_is_reported(accuracy_record):
           f"max normwise error {err:.3e}")
     assert pinned > 0
     assert err < 1e-2, err
+
+
+def test_reflect_boundary():
+    """Six directions with the reflected boundary: against the definition on the
+    transferred reflection-padded image (the pad placed so that the lattice
+    stays anchored at the image origin)."""
+    H, W = 48, 56
+    f = synth.image(H, W, seed=71, dtype="f32")
+    p = synth.srt_field(H, W, seed=71, sigma=(1.5, 4.0), rho=(1.0, 4.0))
+    got, st = _run(f, p, "srt", boundary="reflect")
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    idx = _sample(H, W, 30, seed=71)
+    a, _ = n6.map6(p.reshape(3, -1)[:, idx].astype(np.float64), 2)
+    P = 40
+    fp = O.pad_reflect(f.astype(np.float64), P)
+    A = np.zeros((6, H + 2 * P, W + 2 * P))
+    py, px = idx // W + P, idx % W + P
+    A[:, py, px] = a
+    pidx = py * (W + 2 * P) + px
+    ref = n6.direct6_hex(fp, A, pidx, 0.5, origin=(-P, -P))
+    assert _nerr(got.ravel()[idx], ref) < TOL
+    got0, _ = _run(f, p, "srt")
+    assert _nerr(got0.ravel()[idx], ref) > 1e-4  # borders differ with the zero boundary

@@ -428,3 +428,41 @@ def test_preintegrate_rejects_rows_wider_than_a_band():
     with pytest.raises(L.BsfError) as e:
         api.preintegrate(f, halo=8)
     assert e.value.code == L.BSF_EINVAL
+
+
+# ------------------------------------------------------------------ reflected boundary
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_reflect_boundary_matches_padded_definition(dtype):
+    """opts.boundary = reflect: the image continued by half-sample symmetric
+    reflection (reading R21).  Every pixel against the oracle's definition on
+    the reflection-padded image, with footprints that reach well past the
+    borders; a 5 x 7 image with 20 px kernels needs several periods of the
+    reflection."""
+    H, W = 40, 52
+    f = synth.image(H, W, seed=61, dtype=dtype)
+    p = synth.srt_field(H, W, seed=61, sigma=(1.0, 6.0), rho=(1.0, 4.0))
+    out, st = _run(f, p, "srt", max_scale=6.0, boundary="reflect")
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+    ref = O.direct4_reflect(f.astype(np.float64), a)
+    assert _nerr(out, ref) < TOL
+    # the zero boundary differs at the borders: the option is really applied
+    out0, _ = _run(f, p, "srt", max_scale=6.0)
+    assert _nerr(out0, ref) > 1e-3
+    fs = synth.image(5, 7, seed=62, dtype=dtype)
+    asml = np.random.default_rng(62).uniform(8.0, 20.0, size=(4, 5, 7)).astype(np.float32)
+    outs, st = _run(fs, asml, "scales", max_scale=20.0, boundary="reflect")
+    assert st == 0
+    assert _nerr(outs, O.direct4_reflect(fs.astype(np.float64), asml.astype(np.float64))) < TOL
+
+
+def test_reflect_boundary_constant_image_exact_everywhere():
+    """With the reflected boundary a constant image is reproduced at every
+    pixel, borders included, for scales of unit lattice mass (a1, a3 integers)."""
+    H, W = 30, 34
+    f = np.full((H, W), 200, dtype=np.uint8)
+    a = np.empty((4, H, W), dtype=np.float32)
+    a[0], a[1], a[2], a[3] = 3.0, 2.3, 2.0, 1.7
+    out, st = _run(f, a, "scales", max_scale=3.0, boundary="reflect")
+    assert st == 0
+    assert np.abs(out - 200.0).max() < 200.0 * 1e-6

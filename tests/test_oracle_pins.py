@@ -508,3 +508,27 @@ def test_beta4_is_c1_but_not_c2():
     assert np.abs(np.diff(d1)).max() < 50 * h          # first derivative continuous
     assert np.abs(np.diff(d2)).max() > 1e-2            # second derivative jumps somewhere
     assert np.abs(b).max() > 0.05
+
+
+def test_reflected_boundary_definition():
+    """The reflected boundary (reading R21): the padding is f[-1-i] = f[i],
+    f[n+i] = f[n-1-i], periodic beyond one reflection; a constant image stays
+    exactly constant at EVERY pixel for scales with unit lattice mass (a1, a3
+    integers), where the zero boundary loses mass at the borders; away from the
+    borders the two boundaries agree."""
+    x = np.arange(5.0)
+    pad = O.pad_reflect(x[None, :], 6)[6]
+    want = [x[(i % 10) if (i % 10) < 5 else 9 - (i % 10)] for i in range(-6, 11)]
+    assert np.array_equal(pad, want)
+    H, W = 9, 11
+    f = np.full((H, W), 3.0)
+    a = np.zeros((4, H, W))
+    a[0], a[1], a[2], a[3] = 3.0, 2.3, 2.0, 1.7
+    assert np.abs(O.direct4_reflect(f, a) - 3.0).max() < 1e-12
+    assert np.abs(O.direct4(f, a) - 3.0).max() > 0.5
+    rng = np.random.default_rng(2)
+    H, W = 24, 26
+    f = rng.uniform(0, 1, (H, W))
+    a = rng.uniform(0.5, 2.0, (4, H, W))
+    inner = np.array([y * W + x for y in range(6, H - 6) for x in range(6, W - 6)])
+    assert np.abs(O.direct4_reflect(f, a, inner) - O.direct4(f, a, inner)).max() < 1e-13

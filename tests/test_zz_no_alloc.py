@@ -4,7 +4,8 @@ loops where cudaMalloc/cudaFree would synchronise the device).
 
 Its output must equal the regular bsf_filter output on the same inputs,
 within the parity tolerance of the other tests, on two calls in a row (the
-second reusing the shared fixed scratch that the first left behind).  Oversize
+second reusing the shared fixed scratch that the first left behind), and the
+oracle's plain definition on sampled pixels.  Oversize
 images must be refused with BSF_ENOSCRATCH.  This file is collected last on
 purpose, and also passes when run alone in a fresh process.
 """
@@ -45,6 +46,31 @@ def test_noalloc_matches_filter_on_two_calls(dtype):
         got, want = out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
         assert np.isfinite(got).all()
         assert np.abs(got - want).max() / np.abs(want).max() <= TOL
+        # and against the oracle's plain definition itself on sampled pixels
+        import oracle as O
+        fn, pn = f.cpu().numpy().astype(np.float64), p.cpu().numpy().astype(np.float64)
+        a, _ = O.map4(pn, O.KIND_SRT)
+        idx = np.random.default_rng(seed).choice(H * W, size=64, replace=False)
+        ref_o = O.direct4(fn, a, idx)
+        assert np.abs(got.ravel()[idx] - ref_o).max() / np.abs(ref_o).max() <= TOL
+
+
+def test_noalloc_reflect_boundary_matches_filter():
+    """The reflected boundary through the allocation-free entry point equals
+    bsf_filter with the same option."""
+    dev = _dev()
+    torch.cuda.set_device(dev)
+    H, W = 96, 88
+    opts = api.make_opts(max_scale=5.0, boundary="reflect")
+    f = torch.from_numpy(synth.image(H, W, seed=8, dtype="u8")).to(dev)
+    p = torch.from_numpy(synth.srt_field(H, W, seed=8, sigma=(1.0, 5.0), rho=(1.0, 4.0))).to(dev)
+    ref = api.filter(f, p, kind="srt", max_scale=5.0, boundary="reflect")
+    out = torch.full((H, W), float("nan"), dtype=torch.float32, device=dev)
+    rc = L.bsf_filter_noalloc(f.data_ptr(), L.BSF_U8, H, W, 4, p.data_ptr(), L.BSF_PARAM_SRT, opts, out.data_ptr(),
+                              int(torch.cuda.current_stream(dev).cuda_stream))
+    assert rc == L.BSF_OK, L.status_string(rc)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(out, ref)
 
 
 def test_noalloc_refuses_oversize_image():
