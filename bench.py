@@ -400,7 +400,8 @@ def run_ours(args):
         gsc = torch.empty_like(p)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     ctx = api.context(dev)
-    opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=smax)
+    opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=smax,
+                         hex_spacing=args.hex_spacing)
     stream = torch.cuda.current_stream(dev)
     sptr = int(stream.cuda_stream)
 
@@ -594,7 +595,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload] if args.size is None else
                    f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
-                   "workload_id": args.workload,
+                   "workload_id": args.workload, **({"hex_spacing": args.hex_spacing} if N == 6 else {}),
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))},
@@ -668,9 +669,11 @@ def run_serve(args):
         srv.close()
     line = {"metric": METRIC, "value": st["gpixels_per_s"], "unit": "Gpixels/s", "n_gpus": 1,
             "steps": args.requests, "warmup": 8, "ms_per_step": 1e3 * st["makespan_s"] / args.requests,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128+double-float",
+            "data": "synthetic",
             "config": {"workload": f"serving stream: {args.requests} requests, side log-uniform 256-{S}, 1 or 3 "
-                                   "channels f32, N in {4,6} (N=6 on the hexagonal lattice, FP64), sigma 1-40, rho 1-8, "
+                                   "channels f32, N in {4,6} (N=6 on the hexagonal lattice, exact integer + double-float), "
+                                   "sigma 1-40, rho 1-8, "
                                    "Poisson arrivals at 0.7x saturation", "slots": args.slots,
                        "hbm_budget_gb": args.hbm_gb, "arrival_rate_per_s": rate,
                        "saturation_gpixels_per_s": sat["gpixels_per_s"]},
@@ -809,6 +812,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--hbm-gb", type=float, default=48.0)
     ap.add_argument("--pool-side", type=int, default=4096)
+    ap.add_argument("--hex-spacing", type=float, default=0.5, help="N=6: lattice spacing h (1, 0.5, 0.25, 0.125)")
     args = ap.parse_args()
     from paper_1003_2022_gb300 import synth as _synth
     heavy = _synth.WORKLOADS[args.workload]["N"] == 6
