@@ -222,14 +222,15 @@ def alu_peak_tops():
     return 152 * 128 * 2.070e9 / 1e12
 
 
-def _inputs(size=None, workload=WORKLOAD, first_only=False):
+def _inputs(size=None, workload=WORKLOAD, first_only=False, sigma_max=None):
     """(B, C, H, W) image and (B, K, H, W) parameter planes of a workload
     (first_only: the first batch entry alone, generated from the same seed)."""
     from paper_1003_2022_gb300 import synth
     if synth.WORKLOADS[workload]["B"] == 1 and "scales" not in synth.WORKLOADS[workload]:
         f, p = synth.workload_inputs(workload, seed=0, H=size, W=size)
         return f[None, None], p[None]
-    return synth.batch_inputs(workload, seed=0, H=size, W=size, B=1 if first_only else None)
+    sig = None if sigma_max is None else (synth.WORKLOADS[workload]["sigma"][0], sigma_max)
+    return synth.batch_inputs(workload, seed=0, H=size, W=size, B=1 if first_only else None, sigma=sig)
 
 
 def _map6_chunk(args):
@@ -386,7 +387,9 @@ def run_ours(args):
     from paper_1003_2022_gb300 import synth as _synth
     kind_name, smax, train = BENCH_WORKLOADS[args.workload]
     N = _synth.WORKLOADS[args.workload]["N"]
-    f_np, p_np = _inputs(args.size, args.workload)
+    f_np, p_np = _inputs(args.size, args.workload, sigma_max=args.sigma_max)
+    if args.sigma_max is not None:
+        smax = args.sigma_max
     B, C, H, W = f_np.shape
     u8 = f_np.dtype == np.uint8
     dtype = L.BSF_U8 if u8 else L.BSF_F32
@@ -596,6 +599,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_TEXT[args.workload] if args.size is None else
                    f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
                    "workload_id": args.workload, **({"hex_spacing": args.hex_spacing} if N == 6 else {}),
+                   **({"sigma_max": args.sigma_max} if args.sigma_max is not None else {}),
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))},
@@ -813,6 +817,7 @@ def main():
     ap.add_argument("--hbm-gb", type=float, default=48.0)
     ap.add_argument("--pool-side", type=int, default=4096)
     ap.add_argument("--hex-spacing", type=float, default=0.5, help="N=6: lattice spacing h (1, 0.5, 0.25, 0.125)")
+    ap.add_argument("--sigma-max", type=float, default=None, help="batched workloads: cap the size field at this sigma")
     args = ap.parse_args()
     from paper_1003_2022_gb300 import synth as _synth
     heavy = _synth.WORKLOADS[args.workload]["N"] == 6

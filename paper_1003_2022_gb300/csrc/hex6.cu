@@ -79,6 +79,63 @@ struct m6c<float> {
     static __device__ __forceinline__ float z(int k, int l) { return MAP6_ZF[k][l]; }
 };
 
+// ---- double-float (a pair of FP32 numbers, about 48 bits) ----
+struct dflt {
+    float hi, lo;
+};
+__device__ __forceinline__ dflt df_norm(float s, float e) {
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+    // two-sum of the high parts, then the low parts
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return df_norm(s, e);
+}
+// a * b + c in double-float
+__device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    e += (p - (s - bb)) + (c.hi - bb);
+    e += c.lo;
+    return df_norm(s, e);
+}
+// a 128-bit integer as a double-float (to about 48 bits): its top 62 bits as a
+// 64-bit integer v (the bits below are dropped: at most 2^-62 of |v|), then the
+// nearest FP32 value of v and of the exact remainder, both scaled back
+__device__ __forceinline__ dflt df_of_i128(i128 a) {
+    const long long hw = (long long)(a >> 64);
+    const unsigned long long lw = (unsigned long long)a;
+    // bit length of |a| (one less for negative a: enough to choose the shift)
+    const unsigned long long mh = (unsigned long long)(hw ^ (hw >> 63));
+    const unsigned long long ml = lw ^ (unsigned long long)(hw >> 63);
+    const int n = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
+    const int sh = n > 62 ? n - 62 : 0;
+    const long long v = (long long)(a >> sh);
+    const float hi = __ll2float_rn(v);
+    const float lo = __ll2float_rn(v - __float2ll_rn(hi));
+    const float sc = __int_as_float((127 + sh) << 23);  // 2^sh, exact
+    return df_norm(hi * sc, lo * sc);
+}
+// the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact)
+__device__ __forceinline__ dflt df_of_frac48(long long x) {
+    return {(float)(x >> 24) * 5.9604644775390625e-8f, (float)(x & 0xFFFFFF) * 3.552713678800501e-15f};
+}
+
 // ||K||^2 for six directions: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m)
 // = (S0^2 + |S1|^2) / 2, S0 = sum q_k, S1 = sum q_k exp(2 i theta_k), q = p^2
 template <class R>
@@ -320,6 +377,178 @@ __device__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int&
     }
 }
 
+// ---- the last Newton steps of the map in double-float ----
+__device__ __forceinline__ dflt df_of_double(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+__device__ __forceinline__ double double_of_df(dflt a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dflt df_scale(dflt a, float c) {  // c a power of two or a small integer
+    return df_norm(a.hi * c, fmaf(a.hi, c, -(a.hi * c)) + a.lo * c);
+}
+// the constants cos 2 theta_k, sin 2 theta_k and z_kl as double-float: 0, +-1/2, +-1 are exact,
+// sqrt(3)/2 is split into its nearest float and the rest (folded at compile time once the
+// loops over k are unrolled)
+constexpr float M6_R3H = 0.8660253882408142f, M6_R3L = 1.5543625053737742e-08f;
+__device__ __forceinline__ constexpr int m6_c2n(int k) { return k == 0 ? 2 : k == 1 ? 1 : k == 2 ? -1 : k == 3 ? -2 : k == 4 ? -1 : 1; }
+__device__ __forceinline__ constexpr int m6_s2n(int k) { return (k == 1 || k == 2) ? 1 : (k == 4 || k == 5) ? -1 : 0; }
+__device__ __forceinline__ dflt m6_dc2(int k) { return {0.5f * (float)m6_c2n(k), 0.f}; }
+__device__ __forceinline__ dflt m6_ds2(int k) { return {(float)m6_s2n(k) * M6_R3H, (float)m6_s2n(k) * M6_R3L}; }
+// z_k = (cos 4 theta_k, sin 4 theta_k, (-1)^k)
+__device__ __forceinline__ dflt m6_dz(int k, int l) {
+    if (l == 0) return {(k == 0 || k == 3) ? 1.f : -0.5f, 0.f};
+    if (l == 1) {
+        const float sg = (k == 1 || k == 4) ? 1.f : (k == 2 || k == 5) ? -1.f : 0.f;
+        return {sg * M6_R3H, sg * M6_R3L};
+    }
+    return {(k & 1) ? -1.f : 1.f, 0.f};
+}
+
+// Newton steps on the face of the working set found by the FP32 iteration, with the
+// gradient, the iterate t and p = pbar + Z t in double-float (about 48 bits) and the
+// reduced Hessian in FP32: each step then removes the error of t down to the
+// gradient's accuracy (an FP32 Hessian only slows the convergence to a factor of
+// about 1e-7 per step).  Three steps from the FP32 solution reach the rounding level
+// of the double-float gradient.  Returns p in double.
+__device__ void map6_polish(const double pbar_d[6], double lb, const double t_d[3], int wmask, int nw,
+                            double p_out[6]) {
+    dflt pbar[6], t[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pbar[k] = df_of_double(pbar_d[k]);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) t[l] = df_of_double(t_d[l]);
+    // the free directions of the face (FP32, orthonormal): the same construction as the
+    // FP32 iteration
+    float za[3] = {0, 0, 0}, zb[3] = {0, 0, 0};
+    int seen = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if ((wmask >> k) & 1) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (seen == 0) za[l] = MAP6_ZF[k][l];
+                if (seen == 1) zb[l] = MAP6_ZF[k][l];
+            }
+            ++seen;
+        }
+    const int d = 3 - nw;
+    float N[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (nw == 1) {
+        const float zn = sqrtf(za[0] * za[0] + za[1] * za[1] + za[2] * za[2]);
+        const float n1[3] = {za[0] / zn, za[1] / zn, za[2] / zn};
+        const int e = (fabsf(n1[1]) < fabsf(n1[0])) ? ((fabsf(n1[2]) < fabsf(n1[1])) ? 2 : 1)
+                                                     : ((fabsf(n1[2]) < fabsf(n1[0])) ? 2 : 0);
+        const float dd = e == 0 ? n1[0] : (e == 1 ? n1[1] : n1[2]);
+        float u[3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) u[l] = (l == e ? 1.f : 0.f) - dd * n1[l];
+        const float un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) u[l] /= un;
+        const float v[3] = {n1[1] * u[2] - n1[2] * u[1], n1[2] * u[0] - n1[0] * u[2], n1[0] * u[1] - n1[1] * u[0]};
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            N[l][0] = u[l];
+            N[l][1] = v[l];
+        }
+    } else if (nw == 2) {
+        const float n[3] = {za[1] * zb[2] - za[2] * zb[1], za[2] * zb[0] - za[0] * zb[2], za[0] * zb[1] - za[1] * zb[0]};
+        const float nn = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) N[l][0] = n[l] / nn;
+    }
+    dflt p[6];
+    for (int it = 0; it < 3 && d > 0; ++it) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            p[k] = df_fma(m6_dz(k, 2), t[2], df_fma(m6_dz(k, 1), t[1], df_fma(m6_dz(k, 0), t[0], pbar[k])));
+        // gradient of ||K||^2 = (S0^2 + Sr^2 + Si^2)/2 in t, S = sum q_k (1, c2_k, s2_k), q = p^2
+        dflt q[6], s0 = {0.f, 0.f}, sr = {0.f, 0.f}, si = {0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            q[k] = df_mul(p[k], p[k]);
+            s0 = df_add(s0, q[k]);
+            sr = df_fma(m6_dc2(k), q[k], sr);
+            si = df_fma(m6_ds2(k), q[k], si);
+        }
+        dflt g[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            // dK/dp_k = 4 p_k (s0 + c2_k sr + s2_k si) / 2
+            const dflt dq = df_fma(m6_ds2(k), si, df_fma(m6_dc2(k), sr, s0));
+            const dflt gp = df_scale(df_mul(p[k], dq), 2.f);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) g[l] = df_fma(m6_dz(k, l), gp, g[l]);
+        }
+        // reduced gradient (double-float) and Hessian (FP32) on the face
+        dflt gr[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float Hr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, grf[3] = {0, 0, 0}, du[3] = {0, 0, 0};
+        float pf[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pf[k] = p[k].hi;
+        float Hm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        {
+            float f0 = 0, fr = 0, fi = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float qq = pf[k] * pf[k];
+                f0 += qq;
+                fr += qq * MAP6_C2F[k];
+                fi += qq * MAP6_S2F[k];
+            }
+            float sg[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float dq = 0.5f * (f0 + MAP6_C2F[k] * fr + MAP6_S2F[k] * fi);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const float z = MAP6_ZF[k][l];
+                    sg[l] += pf[k] * z;
+                    mr[l] += MAP6_C2F[k] * pf[k] * z;
+                    mi[l] += MAP6_S2F[k] * pf[k] * z;
+#pragma unroll
+                    for (int m = 0; m <= l; ++m) Hm[l][m] += 4.f * dq * z * MAP6_ZF[k][m];
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+#pragma unroll
+                for (int m = 0; m <= l; ++m) {
+                    Hm[l][m] += 4.f * (sg[l] * sg[m] + mr[l] * mr[m] + mi[l] * mi[m]);
+                    Hm[m][l] = Hm[l][m];
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a >= d) continue;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) gr[a] = df_fma(dflt{-N[l][a], 0.f}, g[l], gr[a]);
+            grf[a] = gr[a].hi + gr[a].lo;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b >= d) continue;
+                float sab = 0;
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) sab += N[l][a] * Hm[l][m] * N[m][b];
+                Hr[a][b] = sab;
+            }
+        }
+        if (!spd_solve(d, Hr, grf, du)) break;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const float st = N[l][0] * du[0] + (d > 1 ? N[l][1] * du[1] : 0.f) + (d > 2 ? N[l][2] * du[2] : 0.f);
+            t[l] = df_add(t[l], dflt{st, 0.f});
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        p[k] = df_fma(m6_dz(k, 2), t[2], df_fma(m6_dz(k, 1), t[1], df_fma(m6_dz(k, 0), t[0], pbar[k])));
+        p_out[k] = double_of_df(p[k]);
+    }
+}
+
 struct map6_p {
     double p[6];
     bool ok;
@@ -347,10 +576,22 @@ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
         return res;
     }
     const double zr = Zc / den, zi = Zs / den;
-    double ang = atan2(zi, zr);
-    if (ang < 0.0) ang += 6.28318530717958647693;
-    int ka = (int)(ang / PI3);
-    ka = ka < 0 ? 0 : (ka > 5 ? 5 : ka);
+    // the sector [k pi/3, (k+1) pi/3) holding the angle of (zr, zi): the one whose bisector
+    // k pi/3 + pi/6 (30, 90, 150, 210, 270, 330 degrees) has the largest projection
+    int ka = 0;
+    {
+        const double R3 = 0.86602540378443864676;
+        const double d0 = R3 * zr + 0.5 * zi, d1 = zi, d2 = -R3 * zr + 0.5 * zi;
+        const double pr[6] = {d0, d1, d2, -d0, -d1, -d2};
+        double best = pr[0];
+#pragma unroll
+        for (int k = 1; k < 6; ++k)
+            if (pr[k] > best) {
+                best = pr[k];
+                ka = k;
+            }
+    }
+    (void)PI3;
     const int kb = (ka + 1) % 6;
     const double dt = MAP6_C2[ka] * MAP6_S2[kb] - MAP6_S2[ka] * MAP6_C2[kb];
     const double la = (zr * MAP6_S2[kb] - zi * MAP6_C2[kb]) / dt;
@@ -415,8 +656,7 @@ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
 #pragma unroll
                 for (int l = 0; l < 3; ++l) t[l] += mu[i] * MAP6_Z[idx[i]][l];
     }
-    map6_newton<double>(pbar, lb, T, t, wmask, nw, 60, 1e-12, 1e-10, 1e-10);
-    p_of_t(pbar, t, p);
+    map6_polish(pbar, lb, t, wmask, nw, p);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if ((wmask >> k) & 1) p[k] = lb;
@@ -460,9 +700,11 @@ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, dou
     // elongation bound for six directions: the normalised traceless part lies in
     // the regular hexagon with vertices exp(2 i theta_k), scaled by 1 - 6 delta so
     // that every p_k can keep the share delta = 1e-3 of the trace
-    double psi = fmod(atan2(s2, c2), 1.04719755119659774615);
-    if (psi < 0.0) psi += 1.04719755119659774615;
-    const double r = (1.0 - 6.0 * rel) * 0.86602540378443864676 / cos(psi - 0.52359877559829887308);
+    // cos(psi - pi/6), psi = 2 theta mod pi/3: the largest |projection| of (cos 2 theta,
+    // sin 2 theta) on the directions 30, 90, 150 degrees (the bisectors of the sectors)
+    const double R3 = 0.86602540378443864676;
+    const double cpsi = fmax(fabs(R3 * c2 + 0.5 * s2), fmax(fabs(s2), fabs(0.5 * s2 - R3 * c2)));
+    const double r = (1.0 - 6.0 * rel) * R3 / cpsi;
     bool clamp = false;
     {
         const double U = (1.0 + r) / (1.0 - r);
@@ -499,7 +741,12 @@ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, dou
         }
         for (int k = 0; k < 6; ++k) P.p[k] = fmax(P.p[k], bound);
     }
-    for (int k = 0; k < 6; ++k) R.a[k] = sqrt(fmax(P.p[k], 0.0));
+    // a_k = sqrt(p_k): the FP32 root and one Newton step in FP64 (about 48 correct bits)
+    for (int k = 0; k < 6; ++k) {
+        const double pk = fmax(P.p[k], 0.0);
+        const float r0 = sqrtf((float)pk);
+        R.a[k] = r0 > 0.f ? (double)r0 + fma(-(double)r0, (double)r0, pk) * (double)(0.5f / r0) : 0.0;
+    }
     return R;
 }
 
@@ -756,63 +1003,6 @@ constexpr int ST_THREADS = 128;  // 32 x 4 pixels for 64-pixel tiles, 16 x 8 for
 
 // the canonical piece's coefficients C[slot][monomial] (integers, |C| <= 102)
 __constant__ int HEX6_CC_CONST[HEX6_NSLOT][HEX6_NMONO] = HEX6_CCOEF_INIT;
-
-// ---- double-float (a pair of FP32 numbers, about 48 bits) ----
-struct dflt {
-    float hi, lo;
-};
-__device__ __forceinline__ dflt df_norm(float s, float e) {
-    const float hi = s + e;
-    return {hi, e - (hi - s)};
-}
-__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return df_norm(p, e);
-}
-__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
-    // two-sum of the high parts, then the low parts
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e += a.lo + b.lo;
-    return df_norm(s, e);
-}
-// a * b + c in double-float
-__device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    const float s = p + c.hi;
-    const float bb = s - p;
-    e += (p - (s - bb)) + (c.hi - bb);
-    e += c.lo;
-    return df_norm(s, e);
-}
-// a 128-bit integer as a double-float (to about 48 bits): its top 62 bits as a
-// 64-bit integer v (the bits below are dropped: at most 2^-62 of |v|), then the
-// nearest FP32 value of v and of the exact remainder, both scaled back
-__device__ __forceinline__ dflt df_of_i128(i128 a) {
-    const long long hw = (long long)(a >> 64);
-    const unsigned long long lw = (unsigned long long)a;
-    // bit length of |a| (one less for negative a: enough to choose the shift)
-    const unsigned long long mh = (unsigned long long)(hw ^ (hw >> 63));
-    const unsigned long long ml = lw ^ (unsigned long long)(hw >> 63);
-    const int n = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
-    const int sh = n > 62 ? n - 62 : 0;
-    const long long v = (long long)(a >> sh);
-    const float hi = __ll2float_rn(v);
-    const float lo = __ll2float_rn(v - __float2ll_rn(hi));
-    const float sc = __int_as_float((127 + sh) << 23);  // 2^sh, exact
-    return df_norm(hi * sc, lo * sc);
-}
-// the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact)
-__device__ __forceinline__ dflt df_of_frac48(long long x) {
-    return {(float)(x >> 24) * 5.9604644775390625e-8f, (float)(x & 0xFFFFFF) * 3.552713678800501e-15f};
-}
 
 // mma.sync m16n8k16 with FP16 operands and FP32 accumulation.  Every operand
 // here is a small integer (window bytes as 1024 + byte, coefficients |c| <=

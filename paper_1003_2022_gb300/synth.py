@@ -169,11 +169,15 @@ def workload_inputs(name: str, seed: int = 0, H: int | None = None, W: int | Non
     return f, p
 
 
-def batch_inputs(name: str, seed: int = 0, H: int | None = None, W: int | None = None, B: int | None = None):
+def batch_inputs(name: str, seed: int = 0, H: int | None = None, W: int | None = None, B: int | None = None,
+                 sigma: tuple | None = None):
     """Images (B, C, H, W) and parameter planes (B, K, H, W) of a batched
     workload: K = 3 (sigma, rho, theta) planes, or K = 4 scale planes for the
-    learnable-scale workload.  Batch entry b uses the sub-seed seed + b."""
-    cfg = WORKLOADS[name]
+    learnable-scale workload.  Batch entry b uses the sub-seed seed + b.
+    sigma: another (lo, hi) range of the size field than the workload's."""
+    cfg = dict(WORKLOADS[name])
+    if sigma is not None:
+        cfg["sigma"] = tuple(sigma)
     H = H or cfg["H"]
     W = W or cfg["W"]
     B = B or cfg["B"]
