@@ -88,6 +88,7 @@ typedef int bsf_status;
 #define BSF_EBADSCALE 7       /* device: a scale or covariance was not finite/positive */
 #define BSF_ERANGE 8          /* device: a kernel (N=4) or image values (N=6) too large for the exact integer form */
 #define BSF_ENOSCRATCH 9      /* bsf_filter_noalloc: the image needs more than its fixed scratch */
+#define BSF_ETIMEOUT 10       /* device: a bounded wait between the pre-integration's row bands gave up */
 
 /* image element types */
 #define BSF_U8 0
@@ -325,6 +326,15 @@ bsf_status bsf_profile_end(bsf_ctx* ctx, double* ms_preintegrate, double* ms_ste
 #define BSF_NOALLOC_SCRATCH_BYTES (32u << 20)
 bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H, int64_t W, int N, const float* params,
                               int kind, const bsf_opts* opts, float* out, void* stream);
+
+/* Bound, in polls, of the device-side waits between the pre-integration's row
+ * bands (the four-directional carries run as one kernel whose blocks wait for
+ * each other at grid barriers; every block is resident, so the waits end).
+ * Process-wide; 0 restores the default of 2^22 polls (about a quarter of a
+ * second).  A wait that runs out raises BSF_ETIMEOUT in the device status word
+ * and its kernel leaves early: the output is then wrong, but nothing hangs.
+ * The paper has no counterpart; the call exists to exercise that path. */
+void bsf_set_wait_limit(unsigned polls);
 
 /* Static description of a status code. */
 const char* bsf_status_string(bsf_status s);

@@ -22,6 +22,7 @@ BSF_EINFEASIBLE = 6
 BSF_EBADSCALE = 7
 BSF_ERANGE = 8
 BSF_ENOSCRATCH = 9
+BSF_ETIMEOUT = 10
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 BSF_U8 = 0
@@ -42,7 +43,7 @@ EXPORTS = [
     "bsf_default_opts", "bsf_create", "bsf_destroy", "bsf_filter", "bsf_scales_from_cov",
     "bsf_buffer_bytes", "bsf_preintegrate", "bsf_apply", "bsf_get_device_status", "bsf_status_string",
     "bsf_profile_begin", "bsf_profile_end", "bsf_filter_noalloc", "bsf_filter_backward", "bsf_filter_host",
-    "bsf_host_sync", "bsf_structure_cov", "bsf_query_workspace",
+    "bsf_host_sync", "bsf_structure_cov", "bsf_query_workspace", "bsf_set_wait_limit",
 ]
 
 
@@ -118,6 +119,8 @@ def load(path: str | None = None):
                                       vp, vp]
     lib.bsf_query_workspace.restype = i32
     lib.bsf_query_workspace.argtypes = [vp, i32, i64, i64, i64, i64, i32, i32, op, ctypes.POINTER(ctypes.c_size_t)]
+    lib.bsf_set_wait_limit.restype = None
+    lib.bsf_set_wait_limit.argtypes = [ctypes.c_uint]
     lib.bsf_status_string.restype = ctypes.c_char_p
     lib.bsf_status_string.argtypes = [i32]
     _lib = lib
@@ -212,6 +215,11 @@ def bsf_filter_noalloc(image, dtype, H, W, N, params, kind, opts, out, stream) -
     """Allocation-free filter of one image (scratch is a fixed array inside the library)."""
     return load().bsf_filter_noalloc(image, dtype, H, W, N, params, kind,
                                      ctypes.byref(opts) if opts is not None else None, out, stream)
+
+
+def bsf_set_wait_limit(polls: int) -> None:
+    """Bound of the device waits between row bands (0: the default)."""
+    load().bsf_set_wait_limit(int(polls))
 
 
 def bsf_profile_begin(ctx) -> None:

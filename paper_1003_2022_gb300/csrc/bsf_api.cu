@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <atomic>
+
 #include "bsf_common.cuh"
 #include "bsf_internal.h"
 
@@ -108,7 +110,13 @@ static int mode_of(int dtype, int precision) {
 
 static size_t elem_bytes(int mode) { return mode == MODE_U128 ? 16 : 8; }
 
+// bound of the device waits between row bands (polls; 0 = the kernel's default)
+static std::atomic<unsigned> g_wait_limit{0};
+unsigned bsf_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 extern "C" {
+
+void bsf_set_wait_limit(unsigned polls) { g_wait_limit.store(polls, std::memory_order_relaxed); }
 
 void bsf_default_opts(bsf_opts* o) {
     if (!o) return;
@@ -136,6 +144,7 @@ const char* bsf_status_string(bsf_status s) {
         case BSF_EBADSCALE: return "a scale or covariance was not finite and positive";
         case BSF_ERANGE: return "a kernel too large for the exact integer form";
         case BSF_ENOSCRATCH: return "the image does not fit the fixed scratch of bsf_filter_noalloc";
+        case BSF_ETIMEOUT: return "a bounded device wait between row bands of the pre-integration gave up";
         default: return "unknown status";
     }
 }
@@ -308,18 +317,18 @@ static bsf_status resolve_halo(bsf_ctx* c, const float* params, int kind, int64_
 
 static cudaError_t run_scan(int mode, int dtype, const void* img, long long img_stride, int nimg, int H, int W, int P,
                             void* G, long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0,
-                            int Ws = 0, int reflect = 0) {
+                            int Ws = 0, int reflect = 0, unsigned* status = nullptr) {
     if (mode == MODE_U64)
         return launch_scan4<MODE_U64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st, col0, Ws, reflect);
+                                               work, st, col0, Ws, reflect, status, bsf_wait_limit());
     if (mode == MODE_U128)
         return launch_scan4<MODE_U128, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                              work, st, col0, Ws, reflect);
+                                              work, st, col0, Ws, reflect, status, bsf_wait_limit());
     if (dtype == BSF_U8)
         return launch_scan4<MODE_F64, uint8_t>((const uint8_t*)img, img_stride, nimg, H, W, P, G, G_stride, pitch,
-                                               work, st, col0, Ws, reflect);
+                                               work, st, col0, Ws, reflect, status, bsf_wait_limit());
     return launch_scan4<MODE_F64, float>((const float*)img, img_stride, nimg, H, W, P, G, G_stride, pitch, work, st,
-                                         col0, Ws, reflect);
+                                         col0, Ws, reflect, status, bsf_wait_limit());
 }
 
 static bool dims_ok(int64_t H, int64_t W) {
@@ -390,7 +399,7 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
             BSF_TRY(prof_mark(c, 0, st));
             BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf,
                              (long long)Hp * pitch, pitch, c->work, st, col0, nstrip == 1 ? 0 : ws,
-                             o.boundary == BSF_BOUNDARY_REFLECT));
+                             o.boundary == BSF_BOUNDARY_REFLECT, c->d_status));
             stencil_args a;
             a.col0 = col0;
             a.Ws = nstrip == 1 ? 0 : ws;
@@ -722,7 +731,7 @@ static bsf_status backward_pass(bsf_ctx* c, const void* x, int dtype, int64_t B,
         }
         const char* img0 = (const char*)x + (size_t)(b0 * C) * HW * esz;
         BSF_TRY(run_scan(mode, dtype, img0, (long long)HW, nimg, (int)H, (int)W, P, c->buf, (long long)Hp * pitch,
-                         pitch, c->work, st));
+                         pitch, c->work, st, 0, 0, 0, c->d_status));
         BSF_TRY(launch_grad4(mode, c->buf, (long long)Hp * pitch, Hp, Wp, pitch, P, (int)H, (int)W, (int)C, nimg,
                              scales + (size_t)b0 * 4 * HW, gout + (size_t)(b0 * C) * HW,
                              gscales ? gscales + (size_t)b0 * 4 * HW : nullptr, hb, ascale, c->d_status, st));
@@ -813,7 +822,7 @@ bsf_status bsf_preintegrate(bsf_ctx* c, const void* image, int dtype, int64_t H,
     if (!plan.ok) return BSF_EINVAL;  // a row wider than one band CTA holds (bsf_filter uses strips)
     BSF_TRY(grow(&c->work, &c->work_bytes, plan.work_bytes));
     BSF_TRY(run_scan(mode, dtype, image, (long long)H * W, 1, (int)H, (int)W, halo, buffer, (long long)Hp * Wp, Wp,
-                     c->work, (cudaStream_t)stream));
+                     c->work, (cudaStream_t)stream, 0, 0, 0, c->d_status));
     return BSF_OK;
 }
 

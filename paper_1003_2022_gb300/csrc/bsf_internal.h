@@ -30,11 +30,17 @@ int scan_max_width(size_t elem_bytes, bool narrow = false);
 // elements) into buffers of Hp x pitch elements (stride G_stride elements).
 // The buffer covers the image columns [col0 - P, col0 + Ws + P) (Ws <= 0:
 // the whole width, col0 = 0), f taken as zero outside the image, or (reflect)
-// as its half-sample symmetric extension over the whole buffer.
+// as its half-sample symmetric extension over the whole buffer.  The carries
+// between row bands run as one cooperative kernel whose grid barriers give up
+// after spin_limit polls (0: the default bound) and raise BSF_ETIMEOUT in
+// *status (if given) instead of waiting forever.
 template <int MODE, class InT>
 cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
                          long long G_stride, int pitch, void* work, cudaStream_t st, int col0 = 0, int Ws = 0,
-                         int reflect = 0);
+                         int reflect = 0, unsigned* status = nullptr, unsigned spin_limit = 0);
+
+// the process-wide bound of the device waits between row bands (bsf_set_wait_limit; 0 = default)
+unsigned bsf_wait_limit();
 
 // index i of the half-sample symmetric extension of 0..n-1 (period 2n: -1 -> 0, n -> n-1)
 __host__ __device__ __forceinline__ int reflect_index(int i, int n) {

@@ -1056,7 +1056,7 @@ constexpr int TC_PSTRIDE = 17;             // 128-bit slots per pixel in the coe
 // zero row), held in registers.  The D fragment gives each lane two
 // coefficients of two taps; after four rounds every pixel's tap q has its 15
 // coefficients in shared memory, and the pixel's own lane evaluates the tap.
-__global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
+__global__ void __launch_bounds__(ST_THREADS, 5) k_hex6_stencil(const double* __restrict__ scales, int C, int H, int W,
                                                               double h, const hex6_tile* __restrict__ tiles,
                                                               const u128* __restrict__ scratch,
                                                               const unsigned* __restrict__ wflag,
@@ -1068,7 +1068,8 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __
     // per warp and pixel: the tap's 16 coefficient rows, exact.  Row m of pixel P sits in slot
     // m ^ (2 (P >> 3)) of a 17-slot record: the four lanes that write the same row of
     // different pixels, and the eight consecutive pixels that read, hit distinct banks.
-    __shared__ __align__(16) i128 scoefx[ST_THREADS / 32][32][TC_PSTRIDE];
+    __shared__ __align__(16) dflt sdf[ST_THREADS / 32][32][TC_PSTRIDE];
+    __shared__ __align__(16) i128 sc0[ST_THREADS / 32][32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid < 16) lut[tid] = HEX6_REGION_LUT[tid];
@@ -1268,7 +1269,9 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __
                                               (unsigned long long)gsum[2][v] + carry;
                 const int row = g + ((v & 2) ? 8 : 0);
                 const int pix = 8 * j4 + ((v & 1) ? 4 : 0) + i;
-                scoefx[warp][pix][row ^ (2 * j4)] = (i128)(((u128)hi << 64) | lo);
+                const i128 av = (i128)(((u128)hi << 64) | lo);
+                sdf[warp][pix][row ^ (2 * j4)] = df_of_i128(av);
+                if (row == 0) sc0[warp][pix] = av;
             }
         }
         __syncwarp();
@@ -1277,13 +1280,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_hex6_stencil(const double* __
         // tables: 1, x1, x2, x1^2, x1 x2, x2^2, x1^3, x1^2 x2, x1 x2^2, x2^3, x1^4, ...)
         {
             const bool neg = __popc(gq) & 1;
-            const i128* rec = scoefx[warp][lane];
+            const dflt* rec = sdf[warp][lane];
             const int sw = 2 * (lane >> 3);
-            const i128 A0 = rec[0 ^ sw];
+            const i128 A0 = sc0[warp][lane];
             e00 += neg ? -A0 : A0;
             dflt ad[HEX6_NMONO];
 #pragma unroll
-            for (int m = 1; m < HEX6_NMONO; ++m) ad[m] = df_of_i128(rec[m ^ sw]);
+            for (int m = 1; m < HEX6_NMONO; ++m) ad[m] = rec[m ^ sw];
             const dflt sg = df_of_frac48(my_x1), tg = df_of_frac48(my_x2);
             const dflt p0 = df_mul(tg, df_fma(tg, df_fma(tg, df_fma(tg, ad[14], ad[9]), ad[5]), ad[2]));
             const dflt p1 = df_fma(tg, df_fma(tg, df_fma(tg, ad[13], ad[8]), ad[4]), ad[1]);

@@ -83,16 +83,16 @@ extern "C" bsf_status bsf_filter_noalloc(const void* image, int dtype, int64_t H
     // read, so nothing left from a previous call needs clearing
     if (mode == MODE_U64)
         e = launch_scan4<MODE_U64, uint8_t>((const uint8_t*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                            work, st, 0, 0, refl);
+                                            work, st, 0, 0, refl, nullptr, bsf_wait_limit());
     else if (mode == MODE_U128)
         e = launch_scan4<MODE_U128, float>((const float*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                           work, st, 0, 0, refl);
+                                           work, st, 0, 0, refl, nullptr, bsf_wait_limit());
     else if (dtype == BSF_U8)
         e = launch_scan4<MODE_F64, uint8_t>((const uint8_t*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                            work, st, 0, 0, refl);
+                                            work, st, 0, 0, refl, nullptr, bsf_wait_limit());
     else
         e = launch_scan4<MODE_F64, float>((const float*)image, H * W, 1, (int)H, (int)W, P, G, Hp * Wp, (int)Wp,
-                                          work, st, 0, 0, refl);
+                                          work, st, 0, 0, refl, nullptr, bsf_wait_limit());
     if (e != cudaSuccess) return BSF_ECUDA;
     stencil_args a;
     a.buf = G;

@@ -196,10 +196,9 @@ __device__ __forceinline__ void warp_band_scan(int b_lo, int b_hi, GetV getv, Pu
 
 // Phase 2a: diagonal lines, x_b = X - (Ylast - Y_b):  S1_b[x_b] = L1_b[x_b] + S1_{b-1}[x_{b-1}]
 template <class T>
-__global__ void k_scan_s1(const T* __restrict__ L, T* __restrict__ S, int Hp, int Wp, int band_h, int nb) {
-    const int im = blockIdx.y;
+__device__ void scan_s1_line(int X, int im, const T* __restrict__ L, T* __restrict__ S, int Hp, int Wp, int band_h,
+                             int nb) {
     const int Ylast = Hp - 1, Y0 = band_last_row(0, band_h, Hp);
-    const int X = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (X >= Wp + (Ylast - Y0)) return;
     // valid bands: 0 <= X - (Ylast - Y_b) < Wp, x increasing in b
     int b_lo = max(0, (Ylast - X + 1) / band_h - 1), b_hi = min(nb - 1, (Ylast - X + Wp) / band_h + 1);
@@ -218,10 +217,8 @@ __global__ void k_scan_s1(const T* __restrict__ L, T* __restrict__ S, int Hp, in
 
 // Phase 2c: columns:  S2_b[x] = L2_b[x] + sum_{j=1..h_b} S1_{b-1}[x-j] + S2_{b-1}[x]
 template <class T>
-__global__ void k_scan_s2(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1, int Hp, int Wp,
-                          int band_h, int nb) {
-    const int im = blockIdx.y;
-    const int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+__device__ void scan_s2_col(int x, int im, const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1, int Hp,
+                            int Wp, int band_h, int nb) {
     if (x >= Wp) return;
     warp_band_scan<T>(0, nb - 1,
         [&](int b) {
@@ -241,12 +238,11 @@ __global__ void k_scan_s2(const T* __restrict__ L, T* __restrict__ S, const T* _
 //           + sum_{j=j0..h} ( S2_{b-1}[x+h-j] + sum_{k=1..j} S1_{b-1}[x+h-j-k] ),
 //   j0 = max(1, x+h-Wp+1)  (RS4 stops at the right buffer edge)
 template <class T>
-__global__ void k_scan_sg(const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1,
-                          const T* __restrict__ PP1, const T* __restrict__ Q1, const T* __restrict__ P2, int Hp,
-                          int Wp, int band_h, int nb) {
-    const int im = blockIdx.y;
+__device__ void scan_sg_line(int t, int im, const T* __restrict__ L, T* __restrict__ S, const T* __restrict__ P1,
+                             const T* __restrict__ PP1, const T* __restrict__ Q1, const T* __restrict__ P2, int Hp,
+                             int Wp, int band_h, int nb) {
     const int Ylast = Hp - 1, Y0 = band_last_row(0, band_h, Hp);
-    const int X = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) - (Ylast - Y0);
+    const int X = t - (Ylast - Y0);
     if (X >= Wp) return;
     // valid bands: 0 <= X + (Ylast - Y_b) < Wp, x decreasing in b
     int b_lo = max(0, (X + Ylast - Wp + 1) / band_h - 1), b_hi = min(nb - 1, (X + Ylast) / band_h + 1);
@@ -312,10 +308,8 @@ __device__ void block_row_scan(int n, Get get, Put put, T* smem /* 32 */) {
 
 // Phase 2b: P1 = prefix(S1), PP1 = prefix(P1), Q1[x] = P1[x] + Q1[x-2]
 template <class T, int ITEMS>
-__global__ void k_prefix1(const T* __restrict__ S, T* __restrict__ P1, T* __restrict__ PP1, T* __restrict__ Q1,
-                          int Wp, int nb) {
-    __shared__ T sm[32];
-    const int b = blockIdx.x, im = blockIdx.y;
+__device__ void prefix1_band(int b, int im, const T* __restrict__ S, T* __restrict__ P1, T* __restrict__ PP1,
+                             T* __restrict__ Q1, int Wp, int nb, T* sm, unsigned char* sm3_raw) {
     const T* s1 = S + ((size_t)im * nb + b) * 3 * (size_t)Wp;
     const size_t pb = ((size_t)im * nb + b) * (size_t)Wp;
     T* p1 = P1 + pb;
@@ -325,7 +319,6 @@ __global__ void k_prefix1(const T* __restrict__ S, T* __restrict__ P1, T* __rest
     // over pairs i: (P1[2i], P1[2i+1], P1[2i] + P1[2i+1]) -> Q1[2i], Q1[2i+1], PP1[2i+1];
     // PP1[2i] = PP1[2i+1] - P1[2i+1]
     // raw storage: V3 has a constructor, which shared memory does not run
-    __shared__ __align__(16) unsigned char sm3_raw[32 * sizeof(V3<T>)];
     V3<T>* sm3 = reinterpret_cast<V3<T>*>(sm3_raw);
     block_row_scan<V3<T>, ITEMS / 2>((Wp + 1) / 2,
         [&](int i) {
@@ -345,12 +338,70 @@ __global__ void k_prefix1(const T* __restrict__ S, T* __restrict__ P1, T* __rest
 }
 
 // Phase 2d: P2 = prefix(S2)
-template <class T, int ITEMS> __global__ void k_prefix2(const T* __restrict__ S, T* __restrict__ P2, int Wp, int nb) {
-    __shared__ T sm[32];
-    const int b = blockIdx.x, im = blockIdx.y;
+template <class T, int ITEMS>
+__device__ void prefix2_band(int b, int im, const T* __restrict__ S, T* __restrict__ P2, int Wp, int nb, T* sm) {
     const T* s2 = S + ((size_t)im * nb + b) * 3 * (size_t)Wp + Wp;
     T* p2 = P2 + ((size_t)im * nb + b) * (size_t)Wp;
     block_row_scan<T, ITEMS>(Wp, [&](int i) { return s2[i]; }, [&](int i, T v) { p2[i] = v; }, sm);
+}
+
+// Grid barrier of the carry kernel: every block is resident (cooperative
+// launch), thread 0 of each block counts in and waits for the count of this
+// barrier.  The wait is bounded: after CARRY_SPIN_LIMIT polls it raises
+// BSF_ETIMEOUT and the block leaves the kernel (the buffer is then wrong and the
+// status says so; nothing hangs).
+constexpr unsigned CARRY_SPIN_LIMIT = 1u << 22;
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, unsigned* status, unsigned spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        for (unsigned it = 0;; ++it) {
+            const unsigned v = *(volatile unsigned*)ctr;
+            if (v >= target) break;
+            if (it >= spin_limit) {
+                if (status) atomicOr(status, 1u << BSF_ETIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Phase 2 in one launch: the five steps (diagonal lines, row prefixes of g1,
+// columns, row prefixes of g2, anti-diagonal lines) as grid-stride loops over
+// their lines or bands, separated by grid barriers.
+constexpr int CARRY_THREADS = 512;
+template <class T>
+__global__ void __launch_bounds__(CARRY_THREADS) k_carries(const T* __restrict__ L, T* __restrict__ S,
+                                                          T* __restrict__ P1, T* __restrict__ PP1,
+                                                          T* __restrict__ Q1, T* __restrict__ P2, int Hp, int Wp,
+                                                          int band_h, int nb, int nimg, unsigned* bar,
+                                                          unsigned* status, unsigned spin_limit) {
+    __shared__ T sm[32];
+    __shared__ __align__(16) unsigned char sm3_raw[32 * sizeof(V3<T>)];
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * wpb + warp, nwarps = gridDim.x * wpb;
+    const int nlines = Wp + (Hp - min(band_h, Hp));  // diagonal / anti-diagonal lines crossing the band ends
+    unsigned target = 0;
+    for (int t = gw; t < nlines * nimg; t += nwarps) scan_s1_line<T>(t % nlines, t / nlines, L, S, Hp, Wp, band_h, nb);
+    if (!grid_barrier(bar, target += gridDim.x, status, spin_limit)) return;
+    for (int t = blockIdx.x; t < nb * nimg; t += gridDim.x)
+        prefix1_band<T, 8>(t % nb, t / nb, S, P1, PP1, Q1, Wp, nb, sm, sm3_raw);
+    if (!grid_barrier(bar, target += gridDim.x, status, spin_limit)) return;
+    for (int t = gw; t < Wp * nimg; t += nwarps) scan_s2_col<T>(t % Wp, t / Wp, L, S, P1, Hp, Wp, band_h, nb);
+    if (!grid_barrier(bar, target += gridDim.x, status, spin_limit)) return;
+    for (int t = blockIdx.x; t < nb * nimg; t += gridDim.x) prefix2_band<T, 8>(t % nb, t / nb, S, P2, Wp, nb, sm);
+    if (!grid_barrier(bar, target += gridDim.x, status, spin_limit)) return;
+    for (int t = gw; t < nlines * nimg; t += nwarps)
+        scan_sg_line<T>(t % nlines, t / nlines, L, S, P1, PP1, Q1, P2, Hp, Wp, band_h, nb);
 }
 
 }  // namespace
@@ -372,7 +423,7 @@ scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes) {
     p.smem = (size_t)p.threads * p.cpt * elem_bytes;
     p.ok = p.threads <= band_maxt(wide, p.cpt);
     const size_t row = (size_t)nimg * p.nb * Wp * elem_bytes;
-    p.work_bytes = row * 10;  // L (3), S (3), P1, PP1, Q1, P2
+    p.work_bytes = row * 10 + 256;  // L (3), S (3), P1, PP1, Q1, P2, and the carry kernel's barrier word
     return p;
 }
 
@@ -408,7 +459,8 @@ static void launch_band_cpt(const scan_plan& p, const InT* img, long long img_st
 
 template <int MODE, class InT>
 cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, int W, int P, void* G,
-                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0, int Ws, int reflect) {
+                         long long G_stride, int pitch, void* work, cudaStream_t st, int col0, int Ws, int reflect,
+                         unsigned* status, unsigned spin_limit) {
     typedef typename mode_traits<MODE>::T T;
     if (Ws <= 0) Ws = W;
     const int Hp = H + 2 * P, Wp = Ws + 2 * P;
@@ -423,24 +475,34 @@ cudaError_t launch_scan4(const InT* img, long long img_stride, int nimg, int H, 
     T* P2 = Q1 + row;
     launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, nullptr, L, nullptr, 0, st,
                                reflect);
-    const int nlines = Wp + (Hp - min(p.band_h, Hp));  // diagonal / anti-diagonal lines crossing the band ends
-    const int wpb = 8;                                 // warps (lines) per 256-thread block
-    k_scan_s1<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, Hp, Wp, p.band_h, p.nb);
-    const int pthreads = min(1024, ((Wp + 7) / 8 + 31) / 32 * 32);
-    k_prefix1<T, 8><<<dim3(p.nb, nimg), pthreads, 0, st>>>(S, P1, PP1, Q1, Wp, p.nb);
-    k_scan_s2<T><<<dim3((Wp + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, Hp, Wp, p.band_h, p.nb);
-    k_prefix2<T, 8><<<dim3(p.nb, nimg), pthreads, 0, st>>>(S, P2, Wp, p.nb);
-    k_scan_sg<T><<<dim3((nlines + wpb - 1) / wpb, nimg), 256, 0, st>>>(L, S, P1, PP1, Q1, P2, Hp, Wp, p.band_h, p.nb);
+    // phase 2: one cooperative launch (every block resident, grid barriers between the steps)
+    unsigned* bar = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(work) + (p.work_bytes - 256));
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_carries<T>, CARRY_THREADS, 0)) != cudaSuccess)
+        return e;
+    const int nlines = Wp + (Hp - min(p.band_h, Hp));
+    const long long want_w = (long long)max(nlines, Wp) * nimg;  // warps of the line steps
+    const long long want = max((want_w + CARRY_THREADS / 32 - 1) / (CARRY_THREADS / 32), (long long)p.nb * nimg);
+    const int grid = (int)max(1LL, min((long long)occ * nsm, want));
+    int Hp_ = Hp, Wp_ = Wp, bh = p.band_h, nb = p.nb, ni = nimg;
+    unsigned spin = spin_limit ? spin_limit : CARRY_SPIN_LIMIT;
+    void* args[] = {&L, &S, &P1, &PP1, &Q1, &P2, &Hp_, &Wp_, &bh, &nb, &ni, &bar, &status, &spin};
+    e = cudaLaunchCooperativeKernel((const void*)k_carries<T>, dim3(grid), dim3(CARRY_THREADS), args, 0, st);
+    if (e != cudaSuccess) return e;
     launch_band_cpt<MODE, InT>(p, img, img_stride, nimg, H, W, col0, P, Hp, Wp, pitch, S, nullptr, G, G_stride, st,
                                reflect);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_scan4<MODE_U64, uint8_t>(const uint8_t*, long long, int, int, int, int, void*, long long,
-                                                     int, void*, cudaStream_t, int, int, int);
+                                                     int, void*, cudaStream_t, int, int, int, unsigned*, unsigned);
 template cudaError_t launch_scan4<MODE_U128, float>(const float*, long long, int, int, int, int, void*, long long, int,
-                                                    void*, cudaStream_t, int, int, int);
+                                                    void*, cudaStream_t, int, int, int, unsigned*, unsigned);
 template cudaError_t launch_scan4<MODE_F64, uint8_t>(const uint8_t*, long long, int, int, int, int, void*, long long,
-                                                     int, void*, cudaStream_t, int, int, int);
+                                                     int, void*, cudaStream_t, int, int, int, unsigned*, unsigned);
 template cudaError_t launch_scan4<MODE_F64, float>(const float*, long long, int, int, int, int, void*, long long, int,
-                                                   void*, cudaStream_t, int, int, int);
+                                                   void*, cudaStream_t, int, int, int, unsigned*, unsigned);

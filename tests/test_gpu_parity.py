@@ -466,3 +466,25 @@ def test_reflect_boundary_constant_image_exact_everywhere():
     out, st = _run(f, a, "scales", max_scale=3.0, boundary="reflect")
     assert st == 0
     assert np.abs(out - 200.0).max() < 200.0 * 1e-6
+
+
+def test_carry_waits_are_bounded():
+    """The carries between the pre-integration's row bands run as one kernel whose
+    blocks wait for each other at grid barriers.  Those waits are bounded: with a
+    limit of one poll, blocks give up, BSF_ETIMEOUT is raised and the call returns
+    (nothing hangs); with the default limit the next call is bit-exact again."""
+    dev = _cuda()
+    H, W, P = 1900, 2100, 120
+    f = synth.image(H, W, seed=77, dtype="u8")
+    img = torch.from_numpy(f).to(dev)
+    api.device_status(dev)
+    L.bsf_set_wait_limit(1)
+    try:
+        api.preintegrate(img, halo=P)
+        st = api.device_status(dev)
+    finally:
+        L.bsf_set_wait_limit(0)
+    assert st & (1 << L.BSF_ETIMEOUT)
+    buf = api.preintegrate(img, halo=P)
+    assert api.device_status(dev) == 0
+    assert np.array_equal(buf.cpu().numpy(), O.preint4_i64(f.astype(np.int64), P))
