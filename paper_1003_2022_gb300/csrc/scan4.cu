@@ -63,39 +63,50 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
     __shared__ T s_tot[2][32];
     __shared__ T s_eg1[2][32];
     __shared__ T s_eG[2][32];
-    // the vertical sum g2 is column-local: it lives in shared memory, one
-    // slot per column, touched only by the thread that owns the column
+    // the vertical sum g2 is column-local: each thread keeps its columns' states in
+    // registers, except for the widest 128-bit form, whose registers would spill: there
+    // they sit in shared memory (one slot per column, touched only by its thread)
+    constexpr bool kG2Smem = MODE == MODE_U128 && CPT >= 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* g2 = reinterpret_cast<T*>(smem_raw) + c0;
-
-    T g1[CPT], gG[CPT];
+    T g1[CPT], g2r[kG2Smem ? 1 : CPT], gG[CPT];
+    auto g2 = [&](int j) -> T& {
+        if constexpr (kG2Smem) return reinterpret_cast<T*>(smem_raw)[c0 + j];
+        else return g2r[j];
+    };
     if (carry != nullptr && b > 0) {
         const T* S = carry + ((size_t)im * nb + (b - 1)) * 3 * (size_t)Wp;
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
             const int c = c0 + j;
             g1[j] = c < Wp ? S[c] : T(0);
-            g2[j] = c < Wp ? S[Wp + c] : T(0);
+            g2(j) = c < Wp ? S[Wp + c] : T(0);
             gG[j] = c < Wp ? S[2 * Wp + c] : T(0);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) g1[j] = g2[j] = gG[j] = T(0);
+        for (int j = 0; j < CPT; ++j) g1[j] = g2(j) = gG[j] = T(0);
     }
 
     const InT* f = img + (size_t)im * img_stride;
     // samples of the next D rows are kept in flight in a register ring
     constexpr int D = 2;
+    // the image columns of this thread that lie inside the image (fixed for the band)
+    const int ic0 = c0 - P + col0;
+    unsigned colmask = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) colmask |= (ic0 + j >= 0 && ic0 + j < W) ? (1u << j) : 0u;
     auto fetch = [&](int y, InT* dst) {
         const int iy = y - P;
+        if (reflect) {  // the symmetric extension fills the whole buffer (columns c0 + j < Wp)
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            const int ic = c0 + j - P + col0;
-            if (reflect)  // the symmetric extension fills the whole buffer (columns c0 + j < Wp)
-                dst[j] = (y < y1 && c0 + j < Wp) ? f[(size_t)reflect_index(iy, H) * W + reflect_index(ic, W)]
+            for (int j = 0; j < CPT; ++j)
+                dst[j] = (y < y1 && c0 + j < Wp) ? f[(size_t)reflect_index(iy, H) * W + reflect_index(ic0 + j, W)]
                                                  : InT(0);
-            else
-                dst[j] = (y < y1 && iy >= 0 && iy < H && ic >= 0 && ic < W) ? f[(size_t)iy * W + ic] : InT(0);
+        } else {
+            const bool rowok = y < y1 && iy >= 0 && iy < H;
+            const InT* rowp = f + (size_t)(rowok ? iy : 0) * W + ic0;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) dst[j] = (rowok && ((colmask >> j) & 1u)) ? rowp[j] : InT(0);
         }
     };
     InT pre[D][CPT];
@@ -135,13 +146,13 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
 #pragma unroll
             for (int j = 0; j < CPT; ++j) ng1[j] = (v[j] + off) + (j == 0 ? left : g1[j - 1]);
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) g2[j] += ng1[j];
+            for (int j = 0; j < CPT; ++j) g2(j) += ng1[j];
             T ngG[CPT];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
                 T nb_ = (j + 1 < CPT) ? gG[j + 1] : right;
                 if (c0 + j + 1 >= Wp) nb_ = T(0);
-                ngG[j] = g2[j] + nb_;
+                ngG[j] = g2(j) + nb_;
             }
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
@@ -163,7 +174,7 @@ __global__ void __launch_bounds__(band_bounds<MODE, CPT>::MAXT) k_band(const InT
             const int c = c0 + j;
             if (c < Wp) {
                 L[c] = g1[j];
-                L[Wp + c] = g2[j];
+                L[Wp + c] = g2(j);
                 L[2 * Wp + c] = gG[j];
             }
         }
@@ -183,14 +194,25 @@ template <class T> __device__ __forceinline__ T at0(const T* a, int i) { return 
 template <class T, class GetV, class Put>
 __device__ __forceinline__ void warp_band_scan(int b_lo, int b_hi, GetV getv, Put put) {
     const int lane = threadIdx.x & 31;
+    // the values of four chunks of 32 bands are loaded before they are scanned: the loads
+    // do not depend on the running sum, so their latencies overlap
+    constexpr int PF = 4;
     T carry = T(0);
-    for (int base = b_lo; base <= b_hi; base += 32) {
-        const int b = base + lane;
-        const bool ok = b <= b_hi;
-        const T v = ok ? getv(b) : T(0);
-        const T inc = warp_incl_scan(v, lane);
-        if (ok) put(b, carry + inc);
-        carry += shfl_idx_T(inc, 31);
+    for (int base = b_lo; base <= b_hi; base += 32 * PF) {
+        T v[PF];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int b = base + 32 * k + lane;
+            v[k] = b <= b_hi ? getv(b) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            if (base + 32 * k > b_hi) break;  // uniform over the warp
+            const int b = base + 32 * k + lane;
+            const T inc = warp_incl_scan(v[k], lane);
+            if (b <= b_hi) put(b, carry + inc);
+            carry += shfl_idx_T(inc, 31);
+        }
     }
 }
 
@@ -420,7 +442,8 @@ scan_plan make_scan_plan(int Hp, int Wp, int nimg, size_t elem_bytes) {
     p.cpt = 1;
     while (p.cpt < 8 && ((Wp + p.cpt - 1) / p.cpt + 31) / 32 * 32 > band_maxt(wide, p.cpt)) p.cpt *= 2;
     p.threads = ((Wp + p.cpt - 1) / p.cpt + 31) / 32 * 32;
-    p.smem = (size_t)p.threads * p.cpt * elem_bytes;
+    // the band kernel keeps its state in registers, but for the widest 128-bit form
+    p.smem = (wide && p.cpt >= 8) ? (size_t)p.threads * p.cpt * elem_bytes : 0;
     p.ok = p.threads <= band_maxt(wide, p.cpt);
     const size_t row = (size_t)nimg * p.nb * Wp * elem_bytes;
     p.work_bytes = row * 10 + 256;  // L (3), S (3), P1, PP1, Q1, P2, and the carry kernel's barrier word
@@ -437,10 +460,9 @@ static void launch_band(const scan_plan& p, const InT* img, long long img_stride
                         int P, int Hp, int Wp, int pitch, const void* carry, void* local, void* G, long long G_stride,
                         cudaStream_t st, int reflect) {
     typedef typename mode_traits<MODE>::T T;
-    // allow up to 96 KiB of g2 state; the attribute belongs to the current device, so it is
-    // set on every launch (a cheap host call) rather than once per process
-    cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     dim3 grid(p.nb, nimg);
+    if (p.smem > 48 * 1024)
+        cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     k_band<MODE, InT, CPT><<<grid, p.threads, p.smem, st>>>(img, img_stride, H, W, col0, P, Hp, Wp, pitch, p.band_h, p.nb,
                                                         (const T*)carry, (T*)local, (T*)G, G_stride, reflect);
 }
