@@ -243,7 +243,8 @@ bsf_status bsf_buffer_bytes(int dtype, int64_t H, int64_t W, int N, int halo, in
  * opts->max_scale (the pre-integrated buffers of one launch, the scan carries,
  * and for opts->iterations > 1 the intermediate image).  N = 6: an upper bound
  * from opts->max_scale (the windows depend on the per-pixel footprints; the
- * planner never holds more than 8 GiB of windows at once).  Host buffers of
+ * planner holds at most two chunks of 8 GiB of windows: one pre-integrated
+ * while the stencil reads the other).  Host buffers of
  * bsf_filter_host are not included.  Errors: BSF_EINVAL (bad shape or kind,
  * neither halo nor max_scale), BSF_EUNSUPPORTED (N). */
 bsf_status bsf_query_workspace(bsf_ctx* ctx, int dtype, int64_t B, int64_t C, int64_t H, int64_t W, int N,

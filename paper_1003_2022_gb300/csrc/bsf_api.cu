@@ -53,24 +53,34 @@ struct bsf_ctx {
     size_t h6_win_bytes = 0;
     void* h6_flag = nullptr;  // per (tile, channel) of a chunk: window values beyond the exact range
     size_t h6_flag_bytes = 0;
+    // the windows of chunk i + 1 are pre-integrated on a side stream into the second of two
+    // buffers while the stencil of chunk i runs on the caller's stream
+    cudaStream_t h6_side = nullptr;
+    cudaEvent_t h6_ev_tiles = nullptr, h6_ev_pre[2] = {nullptr, nullptr}, h6_ev_st[2] = {nullptr, nullptr};
     bool profiling;
-    size_t prof_used;                                // event triples recorded since begin
-    std::vector<std::array<cudaEvent_t, 3>> prof;    // pool of event triples
+    size_t prof_used;                                // event sets recorded since begin
+    // per launch: [0] pre-integration start, [1] its end (= stencil start unless [3] is used),
+    // [2] stencil end, [3] stencil start when the two run on different streams
+    std::vector<std::array<cudaEvent_t, 4>> prof;
+    std::vector<char> prof_split;
 };
 
 static cudaError_t prof_mark(bsf_ctx* c, int which, cudaStream_t st) {
     if (!c->profiling) return cudaSuccess;
     if (which == 0) {
         if (c->prof_used == c->prof.size()) {
-            std::array<cudaEvent_t, 3> t;
-            for (int i = 0; i < 3; ++i) {
+            std::array<cudaEvent_t, 4> t;
+            for (int i = 0; i < 4; ++i) {
                 cudaError_t e = cudaEventCreate(&t[i]);
                 if (e != cudaSuccess) return e;
             }
             c->prof.push_back(t);
+            c->prof_split.push_back(0);
         }
+        c->prof_split[c->prof_used] = 0;
         ++c->prof_used;
     }
+    if (which == 3) c->prof_split[c->prof_used - 1] = 1;
     return cudaEventRecord(c->prof[c->prof_used - 1][which], st);
 }
 
@@ -213,7 +223,10 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     for (cudaStream_t s_ : {c->s_h2d, c->s_comp, c->s_d2h})
         if (s_) cudaStreamDestroy(s_);
     for (auto& t : c->prof)
-        for (int i = 0; i < 3; ++i) cudaEventDestroy(t[i]);
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(t[i]);
+    if (c->h6_side) cudaStreamDestroy(c->h6_side);
+    for (cudaEvent_t e : {c->h6_ev_tiles, c->h6_ev_pre[0], c->h6_ev_pre[1], c->h6_ev_st[0], c->h6_ev_st[1]})
+        if (e) cudaEventDestroy(e);
     delete c;
     return BSF_OK;
 }
@@ -235,7 +248,7 @@ bsf_status bsf_profile_end(bsf_ctx* c, double* ms_pre, double* ms_st, int* nlaun
         BSF_TRY(cudaEventSynchronize(c->prof[i][2]));
         float t0 = 0, t1 = 0;
         BSF_TRY(cudaEventElapsedTime(&t0, c->prof[i][0], c->prof[i][1]));
-        BSF_TRY(cudaEventElapsedTime(&t1, c->prof[i][1], c->prof[i][2]));
+        BSF_TRY(cudaEventElapsedTime(&t1, c->prof[i][c->prof_split[i] ? 3 : 1], c->prof[i][2]));
         a += t0;
         b += t1;
     }
@@ -463,23 +476,44 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     for (auto& ch : chunks) win = std::max(win, ch.bytes);
     if (tl.empty()) return BSF_OK;
     BSF_TRY(grow(&c->h6_tiles, &c->h6_tiles_bytes, tl.size() * sizeof(hex6_tile)));
-    BSF_TRY(grow(&c->h6_win, &c->h6_win_bytes, win));
+    // two window buffers: chunk i + 1 is pre-integrated on the side stream while the stencil
+    // of chunk i runs on st; a buffer is reused only after the stencil that read it
+    const size_t win_al = (win + 255) & ~(size_t)255;
+    BSF_TRY(grow(&c->h6_win, &c->h6_win_bytes, 2 * win_al));
     size_t most = 0;
     for (auto& ch : chunks) most = std::max(most, ch.last - ch.first);
-    BSF_TRY(grow(&c->h6_flag, &c->h6_flag_bytes, most * (size_t)C * sizeof(unsigned)));
+    const size_t flag_al = (most * (size_t)C * sizeof(unsigned) + 255) & ~(size_t)255;
+    BSF_TRY(grow(&c->h6_flag, &c->h6_flag_bytes, 2 * flag_al));
+    if (!c->h6_side) {
+        BSF_TRY(cudaStreamCreateWithFlags(&c->h6_side, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&c->h6_ev_tiles, &c->h6_ev_pre[0], &c->h6_ev_pre[1], &c->h6_ev_st[0], &c->h6_ev_st[1]})
+            BSF_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    cudaStream_t side = c->h6_side;
     BSF_TRY(cudaMemcpyAsync(c->h6_tiles, tl.data(), tl.size() * sizeof(hex6_tile), cudaMemcpyHostToDevice, st));
+    // the side stream starts after everything enqueued on st so far (the image, the scales, the tiles)
+    BSF_TRY(cudaEventRecord(c->h6_ev_tiles, st));
+    BSF_TRY(cudaStreamWaitEvent(side, c->h6_ev_tiles, 0));
     const hex6_tile* dt = (const hex6_tile*)c->h6_tiles;
     for (size_t i = 0; i < chunks.size(); ++i) {
         const hex6_chunk& ch = chunks[i];
         const int n = (int)(ch.last - ch.first);
+        const int k = (int)(i & 1);
+        void* win_k = (char*)c->h6_win + k * win_al;
+        unsigned* flag_k = (unsigned*)((char*)c->h6_flag + k * flag_al);
+        if (i >= 2) BSF_TRY(cudaStreamWaitEvent(side, c->h6_ev_st[k], 0));
+        if (i > 0) BSF_TRY(prof_mark(c, 0, side));
         BSF_TRY(launch_hex6_preint(dtype == BSF_U8, image, (int)C, (int)H, (int)W, h, dt + ch.first, n, ch.cols,
-                                   c->h6_win, (unsigned*)c->h6_flag, st, o.boundary == BSF_BOUNDARY_REFLECT));
-        BSF_TRY(prof_mark(c, 1, st));
+                                   win_k, flag_k, side, o.boundary == BSF_BOUNDARY_REFLECT));
+        BSF_TRY(prof_mark(c, 1, side));
+        BSF_TRY(cudaEventRecord(c->h6_ev_pre[k], side));
+        BSF_TRY(cudaStreamWaitEvent(st, c->h6_ev_pre[k], 0));
+        BSF_TRY(prof_mark(c, 3, st));
         BSF_TRY(launch_hex6_stencil((const double*)c->h6_scales, (int)C, (int)H, (int)W, tl[ch.first].w,
-                                    tl[ch.first].hh, h, dt + ch.first, n, c->h6_win, (const unsigned*)c->h6_flag, out,
+                                    tl[ch.first].hh, h, dt + ch.first, n, win_k, (const unsigned*)flag_k, out,
                                     c->d_status, st));
+        BSF_TRY(cudaEventRecord(c->h6_ev_st[k], st));
         BSF_TRY(prof_mark(c, 2, st));
-        if (i + 1 < chunks.size()) BSF_TRY(prof_mark(c, 0, st));
     }
     return BSF_OK;
 }
@@ -594,7 +628,7 @@ bsf_status bsf_query_workspace(bsf_ctx* c, int dtype, int64_t B, int64_t C, int6
         const double win = (double)tiles * C * t.ncol * t.nrow * 16.0;
         total += (size_t)B * 6 * HW * sizeof(double) + (size_t)tiles * 2 * sizeof(unsigned) +
                  (size_t)tiles * (sizeof(hex6_tile) + C * sizeof(unsigned)) +
-                 (size_t)std::min(win, (double)((size_t)8 << 30));
+                 2 * (size_t)std::min(win, (double)((size_t)8 << 30));  // two window buffers
     }
     *bytes = total;
     return BSF_OK;
