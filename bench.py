@@ -404,7 +404,7 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     ctx = api.context(dev)
     opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=smax,
-                         hex_spacing=args.hex_spacing)
+                         hex_spacing=args.hex_spacing, map_lut=args.map_lut)
     stream = torch.cuda.current_stream(dev)
     sptr = int(stream.cuda_stream)
 
@@ -600,6 +600,7 @@ def run_ours(args):
                    f"{WORKLOAD_TEXT[args.workload]} (resized to {H}x{W})",
                    "workload_id": args.workload, **({"hex_spacing": args.hex_spacing} if N == 6 else {}),
                    **({"sigma_max": args.sigma_max} if args.sigma_max is not None else {}),
+                   **({"map": "table"} if args.map_lut else {}),
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))},
@@ -818,6 +819,8 @@ def main():
     ap.add_argument("--pool-side", type=int, default=4096)
     ap.add_argument("--hex-spacing", type=float, default=0.5, help="N=6: lattice spacing h (1, 0.5, 0.25, 0.125)")
     ap.add_argument("--sigma-max", type=float, default=None, help="batched workloads: cap the size field at this sigma")
+    ap.add_argument("--map-lut", action="store_true",
+                    help="N=6: read the scale map from its table (an approximation) instead of solving it per pixel")
     args = ap.parse_args()
     from paper_1003_2022_gb300 import synth as _synth
     heavy = _synth.WORKLOADS[args.workload]["N"] == 6

@@ -144,6 +144,19 @@ typedef struct {
                          bsf_filter_noalloc (N = 4 and 6); bsf_preintegrate / bsf_apply take no
                          options and use zero; bsf_filter_backward returns BSF_EUNSUPPORTED for
                          reflect. */
+    int map_lut;      /* N = 6 only, kinds COV and SRT: 0 (default) solves the map of Sec. 3.2.2
+                         for every pixel; 1 reads it from a table.  The map is homogeneous
+                         (p(s C) = s p(C)) and invariant under rotations by pi/6 up to a shift of
+                         the direction index, so the table holds p / T (T = sum p = 12 tr C) on a
+                         513 x 513 grid over 2 theta in [0, pi/3] and e / e_c in [0, 1]
+                         (e = (rho - 1) / (rho + 1), e_c the elongation clamp).  A lookup
+                         interpolates bilinearly and projects the result onto the covariance
+                         constraint, so each kernel keeps its target covariance; only the kurtosis
+                         optimum is approximated (p moves by at most 1e-3 T, at the kinks where a
+                         width leaves its bound).  Pixels where eps binds (eps above rel_bound
+                         times T), rel_bound = 0 and invalid input take the solver.  The table
+                         (8.4 MB of device memory, kept by the context) is built on the first call
+                         for each (eta, rel_bound), which then waits on its stream once. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */

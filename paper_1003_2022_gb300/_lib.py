@@ -59,6 +59,7 @@ class bsf_opts(ctypes.Structure):
         ("hex_spacing", ctypes.c_float),
         ("rel_bound", ctypes.c_float),
         ("boundary", ctypes.c_int),
+        ("map_lut", ctypes.c_int),
     ]
 
 

@@ -41,8 +41,9 @@ def _stream_ptr(stream) -> int:
 
 
 def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False,
-              iterations=1, hex_spacing=0.5, rel_bound=1e-3, boundary="zero") -> L.bsf_opts:
+              iterations=1, hex_spacing=0.5, rel_bound=1e-3, boundary="zero", map_lut=False) -> L.bsf_opts:
     o = L.default_opts()
+    o.map_lut = 1 if map_lut else 0
     o.boundary = {"zero": L.BSF_BOUNDARY_ZERO, "reflect": L.BSF_BOUNDARY_REFLECT}[boundary]
     o.iterations = int(iterations)
     o.hex_spacing = float(hex_spacing)
@@ -69,7 +70,8 @@ def _as4d(image: torch.Tensor) -> torch.Tensor:
 def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int = 4, precision: str = "exact",
            halo: int = 0, max_scale: float = 0.0, eps: float = 1e-3, eta: float = 1e-3, strict: bool = False,
            out: torch.Tensor | None = None, stream=None, iterations: int = 1,
-           hex_spacing: float = 0.5, rel_bound: float = 1e-3, boundary: str = "zero") -> torch.Tensor:
+           hex_spacing: float = 0.5, rel_bound: float = 1e-3, boundary: str = "zero",
+           map_lut: bool = False) -> torch.Tensor:
     """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k).
 
     N = 4 or 6 directions; N = 6 runs on the hexagonal lattice of spacing
@@ -77,7 +79,9 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
     iterations = m > 1 applies the iterated box spline of Sec. 3.3 (m passes
     with the widths a / sqrt(m)).  rel_bound: the six-directional map's lower
     bound p_k >= max(eps, rel_bound * sum p) (see bsf_opts).  boundary: "zero"
-    (f = 0 outside the image) or "reflect" (half-sample symmetric extension)."""
+    (f = 0 outside the image) or "reflect" (half-sample symmetric extension).
+    map_lut: N = 6 only, read the map from its table instead of solving it per
+    pixel (an approximation; see bsf_opts.map_lut)."""
     img = _as4d(image)
     if not img.is_cuda:
         raise ValueError("image must be a CUDA tensor")
@@ -95,7 +99,8 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
     if out is None:
         out = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device)
     dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
-    opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations, hex_spacing, rel_bound, boundary)
+    opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations, hex_spacing, rel_bound, boundary,
+                     map_lut)
     rc = L.bsf_filter(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), _KINDS[kind],
                       opts, out.data_ptr(), _stream_ptr(stream))
     L.check(rc, "bsf_filter")
@@ -103,7 +108,7 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
 
 
 def scales_from_cov(params: torch.Tensor, kind: str = "srt", N: int = 4, eps: float = 1e-3, eta: float = 1e-3,
-                    stream=None, rel_bound: float = 1e-3):
+                    stream=None, rel_bound: float = 1e-3, map_lut: bool = False):
     """Per-pixel optimal scale vectors (Sec. 3.2.2): (3, ...) planes -> ((N, ...), flags uint8)."""
     prm = params.contiguous()
     if prm.dtype != torch.float32 or not prm.is_cuda or prm.shape[0] != 3:
@@ -111,7 +116,7 @@ def scales_from_cov(params: torch.Tensor, kind: str = "srt", N: int = 4, eps: fl
     npix = prm[0].numel()
     scales = torch.empty((N,) + tuple(prm.shape[1:]), dtype=torch.float32, device=prm.device)
     flags = torch.empty(tuple(prm.shape[1:]), dtype=torch.uint8, device=prm.device)
-    opts = make_opts(eps=eps, eta=eta, rel_bound=rel_bound)
+    opts = make_opts(eps=eps, eta=eta, rel_bound=rel_bound, map_lut=map_lut)
     rc = L.bsf_scales_from_cov(context(prm.device), prm.data_ptr(), _KINDS[kind], npix, N, opts,
                                scales.data_ptr(), flags.data_ptr(), _stream_ptr(stream))
     L.check(rc, "bsf_scales_from_cov")

@@ -56,6 +56,9 @@ struct bsf_ctx {
     // the windows of chunk i + 1 are pre-integrated on a side stream into the second of two
     // buffers while the stencil of chunk i runs on the caller's stream
     cudaStream_t h6_side = nullptr;
+    // the map's table (opts.map_lut), built for one (eta, rel) pair at a time
+    void* h6_lut = nullptr;
+    double h6_lut_eta = -1.0, h6_lut_rel = -1.0;
     cudaEvent_t h6_ev_tiles = nullptr, h6_ev_pre[2] = {nullptr, nullptr}, h6_ev_st[2] = {nullptr, nullptr};
     bool profiling;
     size_t prof_used;                                // event sets recorded since begin
@@ -140,6 +143,7 @@ void bsf_default_opts(bsf_opts* o) {
     o->hex_spacing = 0.5f;
     o->rel_bound = 1e-3f;
     o->boundary = BSF_BOUNDARY_ZERO;
+    o->map_lut = 0;
 }
 
 const char* bsf_status_string(bsf_status s) {
@@ -209,7 +213,7 @@ bsf_status bsf_destroy(bsf_ctx* c) {
     if (c->hbuf) cudaFree(c->hbuf);
     if (c->iter) cudaFree(c->iter);
     if (c->stbuf) cudaFree(c->stbuf);
-    for (void* p6 : {c->h6_scales, c->h6_ext, c->h6_tiles, c->h6_win, c->h6_flag})
+    for (void* p6 : {c->h6_scales, c->h6_ext, c->h6_tiles, c->h6_win, c->h6_flag, c->h6_lut})
         if (p6) cudaFree(p6);
     if (c->d_status) cudaFree(c->d_status);
     for (auto& h : c->hs) {
@@ -282,6 +286,24 @@ bsf_status bsf_get_device_status(bsf_ctx* c, void* stream, int* status) {
     return BSF_OK;
 }
 
+// the map's table for opts (null unless opts.map_lut); built on st and waited for once per
+// (eta, rel), so that later calls on any stream see it complete.  The caller holds c->mu.
+static cudaError_t map6_table(bsf_ctx* c, const bsf_opts& o, cudaStream_t st, const float** lut) {
+    *lut = nullptr;
+    if (!o.map_lut) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!c->h6_lut && (e = cudaMalloc(&c->h6_lut, lut6_bytes())) != cudaSuccess) return e;
+    if (c->h6_lut_eta != (double)o.eta || c->h6_lut_rel != (double)o.rel_bound) {
+        c->h6_lut_eta = c->h6_lut_rel = -1.0;
+        if ((e = launch_lut6_build(o.eta, o.rel_bound, (float*)c->h6_lut, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        c->h6_lut_eta = o.eta;
+        c->h6_lut_rel = o.rel_bound;
+    }
+    *lut = (const float*)c->h6_lut;
+    return cudaSuccess;
+}
+
 bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_t npix, int N, const bsf_opts* opts,
                                float* scales, uint8_t* flags, void* stream) {
     if (!c || !params || !scales || npix < 0) return BSF_EINVAL;
@@ -292,9 +314,13 @@ bsf_status bsf_scales_from_cov(bsf_ctx* c, const float* params, int kind, int64_
     if (opts) o = *opts;
     if (N == 6 && !(o.rel_bound >= 0.f && o.rel_bound < 1.f / 6.f)) return BSF_EINVAL;
     BSF_TRY(cudaSetDevice(c->device));
-    if (N == 6)
+    if (N == 6) {
+        std::lock_guard<std::mutex> lock(c->mu);
+        const float* lut = nullptr;
+        BSF_TRY(map6_table(c, o, (cudaStream_t)stream, &lut));
         BSF_TRY(launch_map6_out(params, kind, (long long)npix, o.eps, o.eta, o.rel_bound, scales, flags,
-                                 (cudaStream_t)stream));
+                                 (cudaStream_t)stream, lut));
+    }
     else
         BSF_TRY(launch_map4(params, kind, (long long)npix, o.eps, o.eta, scales, flags, (cudaStream_t)stream));
     return BSF_OK;
@@ -461,8 +487,10 @@ static bsf_status filter6(bsf_ctx* c, const void* image, int dtype, int64_t B, i
     BSF_TRY(grow(&c->h6_ext, &c->h6_ext_bytes, ext_bytes));
     BSF_TRY(cudaMemsetAsync(c->h6_ext, 0, ext_bytes, st));
     BSF_TRY(prof_mark(c, 0, st));
+    const float* lut = nullptr;
+    if (kind != BSF_PARAM_SCALES) BSF_TRY(map6_table(c, o, st, &lut));
     BSF_TRY(launch_map6(params, kind, (int)B, (int)H, (int)W, fine, o.eps, o.eta, o.rel_bound, ascale, (double*)c->h6_scales,
-                        (unsigned*)c->h6_ext, c->d_status, st));
+                        (unsigned*)c->h6_ext, c->d_status, st, lut));
     std::vector<unsigned> ext((size_t)B * nfine * 2);
     BSF_TRY(cudaMemcpyAsync(ext.data(), c->h6_ext, ext_bytes, cudaMemcpyDeviceToHost, st));
     BSF_TRY(cudaStreamSynchronize(st));

@@ -118,12 +118,16 @@ int hex6_max_cols();
 // BSF_EINVAL: an extent not finite or above 1e5 px, or a window too wide.
 int hex6_plan(int64_t B, int64_t C, int64_t H, int64_t W, double h, const unsigned* ext, size_t budget,
               std::vector<hex6_tile>& tiles, std::vector<hex6_chunk>& chunks);
-// rel: the lower bound p_k >= max(eps, rel * sum p) of the six-directional map (opts.rel_bound)
+// rel: the lower bound p_k >= max(eps, rel * sum p) of the six-directional map (opts.rel_bound).
+// lut: null, or the table of launch_lut6_build for the same (eta, rel) (opts.map_lut)
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double rel, double ascale, double* scales, unsigned* tile_ext, unsigned* status,
-                        cudaStream_t st);
+                        cudaStream_t st, const float* lut);
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, double rel,
-                            float* scales, uint8_t* flags, cudaStream_t st);
+                            float* scales, uint8_t* flags, cudaStream_t st, const float* lut);
+// the six-directional map at sigma = 1 on a (ln rho, theta) grid: lut6_bytes() bytes of device memory
+size_t lut6_bytes();
+cudaError_t launch_lut6_build(double eta, double rel, float* table, cudaStream_t st);
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
                                int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st,
                                int reflect = 0);

@@ -759,11 +759,143 @@ __device__ __forceinline__ double sin_k(int k) {
     return t[k];
 }
 
+// ---- the map as a table (optional fast mode, opts.map_lut) ----
+// With the relative bound (R19) the problem is homogeneous: p(s C) = s p(C)
+// (the paper's observation (O1), Sec. 3.2.2), so p / T depends only on the
+// normalised traceless part z = (Zc, Zs) / T = e (cos 2 theta, sin 2 theta),
+// e = (rho - 1) / (rho + 1).  The six directions are invariant under a rotation
+// by pi/6 that shifts their indices (the six-directional form of (O2)), so
+// p_k(2 theta) = p_{k-r}(2 theta - r pi/3).  The table holds p / T on a polar
+// grid of that sector: 2 theta' in [0, pi/3] and u = e / e_c(theta') in [0, 1],
+// e_c the elongation clamp, so that clamped pixels lie on the grid's last line.
+// A lookup interpolates bilinearly, rotates, scales by T and then projects onto
+// the covariance constraint (the least-norm change of p that restores
+// sum p = T, sum p cos 2 theta_k = Zc, sum p sin 2 theta_k = Zs), so every
+// table kernel keeps its target covariance; the interpolation touches only the
+// kurtosis optimum.  Pixels the table cannot serve (eps binds, invalid input)
+// take the exact solver.
+constexpr int LUT6_NU = 512;  // cells along u = e / e_c
+constexpr int LUT6_NP = 512;  // cells along 2 theta' in [0, pi/3]
+
+// e_c: the largest e the clamp of map6_solve keeps at the orientation (c2, s2) = (cos, sin) 2 theta
+template <typename T>
+__device__ __forceinline__ T map6_ecap(T c2, T s2, T eta, T rel) {
+    const T R3 = (T)0.86602540378443864676;
+    const T cpsi = fmax(fabs(R3 * c2 + (T)0.5 * s2), fmax(fabs(s2), fabs((T)0.5 * s2 - R3 * c2)));
+    const T r = ((T)1 - (T)6 * rel) * R3 / cpsi;
+    const T rc = ((T)1 - eta) * ((T)1 + r) / ((T)1 - r);
+    return (rc - (T)1) / (rc + (T)1);
+}
+
+__global__ void k_lut6_build(double eta, double rel, float* __restrict__ table) {
+    const int n = (LUT6_NU + 1) * (LUT6_NP + 1);
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int i = id / (LUT6_NP + 1), j = id % (LUT6_NP + 1);
+    double s2, c2;
+    sincos((double)j / LUT6_NP * 1.04719755119659774615, &s2, &c2);
+    const double e = (double)i / LUT6_NU * map6_ecap(c2, s2, eta, rel);
+    map6_p P = map6_active_set(1.0, e * c2, e * s2, rel);
+    if (!P.ok) {
+        P = map6_active_set(1.0, e * c2, e * s2, 0.0);
+        for (int k = 0; k < 6; ++k) P.p[k] = fmax(P.p[k], rel);
+    }
+    float* t = table + (size_t)id * 8;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = (float)P.p[k];
+    t[6] = t[7] = 0.f;
+}
+
+// the table's scales for one pixel; false when the exact solver must run
+__device__ bool lut6_lookup(const float* __restrict__ table, int kind, float v0, float v1, float v2, double eps,
+                            double eta, double rel, double a[6], int& flag) {
+    // validity as the exact solver decides it (eigenvalues in FP64: the determinant of an
+    // elongated covariance cancels); the rest in FP32
+    double dmax, dmin;
+    float T, Zc, Zs;
+    if (kind == BSF_PARAM_SRT) {
+        dmax = (double)v0 * (double)v0;
+        dmin = dmax / (double)v1;
+        if (!(fabsf(v2) < 64.f)) return false;
+        float sn, cs;
+        sincosf(2.f * v2, &sn, &cs);
+        const float d = (float)(12.0 * (dmax - dmin));
+        T = (float)(12.0 * (dmax + dmin));
+        Zc = d * cs;
+        Zs = d * sn;
+    } else {
+        const double a0 = v0, a1 = v1, a2 = v2;
+        dmax = 0.5 * (a0 + a2 + sqrt((a0 - a2) * (a0 - a2) + 4.0 * a1 * a1));
+        dmin = (a0 * a2 - a1 * a1) / dmax;
+        T = 12.f * (v0 + v2);
+        Zc = 12.f * (v0 - v2);
+        Zs = 24.f * v1;
+    }
+    if (!(isfinite(dmax) && isfinite(dmin)) || !(dmin > 0.0) || !(dmax >= dmin) || rel <= 0.0) return false;
+    if (rel * 12.0 * (dmax + dmin) < eps) return false;  // eps binds: not homogeneous
+    const float zn = sqrtf(Zc * Zc + Zs * Zs);
+    const float c2 = zn > 0.f ? Zc / zn : 1.f, s2 = zn > 0.f ? Zs / zn : 0.f;
+    const float ec = map6_ecap(c2, s2, (float)eta, (float)rel);
+    float e = zn / T;
+    flag = 0;
+    if (e > ec) {
+        Zc *= ec / e;
+        Zs *= ec / e;
+        e = ec;
+        flag = 1;
+    }
+    const float SEC = 1.04719755119659774615f;
+    float phi = atan2f(s2, c2);
+    if (phi < 0.f) phi += 6.28318530717958648f;
+    int r = (int)(phi / SEC);
+    r = r < 0 ? 0 : (r > 5 ? 5 : r);
+    const float php = fminf(fmaxf(phi - (float)r * SEC, 0.f), SEC);
+    const float u = fminf(e / ec, 1.f) * LUT6_NU, w = php / SEC * LUT6_NP;
+    const int iu = min((int)u, LUT6_NU - 1), iw = min((int)w, LUT6_NP - 1);
+    const float fu = u - (float)iu, fw = w - (float)iw;
+    const float4* t00 = reinterpret_cast<const float4*>(table + ((size_t)iu * (LUT6_NP + 1) + iw) * 8);
+    const float4* t01 = t00 + 2;
+    const float4* t10 = t00 + 2 * (LUT6_NP + 1);
+    const float4* t11 = t10 + 2;
+    float v[6];
+    {
+        const float4 a0 = t00[0], a1 = t00[1], b0 = t01[0], b1 = t01[1];
+        const float4 c0 = t10[0], c1 = t10[1], d0 = t11[0], d1 = t11[1];
+        const float w00 = (1.f - fu) * (1.f - fw), w01 = (1.f - fu) * fw, w10 = fu * (1.f - fw), w11 = fu * fw;
+        v[0] = w00 * a0.x + w01 * b0.x + w10 * c0.x + w11 * d0.x;
+        v[1] = w00 * a0.y + w01 * b0.y + w10 * c0.y + w11 * d0.y;
+        v[2] = w00 * a0.z + w01 * b0.z + w10 * c0.z + w11 * d0.z;
+        v[3] = w00 * a0.w + w01 * b0.w + w10 * c0.w + w11 * d0.w;
+        v[4] = w00 * a1.x + w01 * b1.x + w10 * c1.x + w11 * d1.x;
+        v[5] = w00 * a1.y + w01 * b1.y + w10 * c1.y + w11 * d1.y;
+    }
+    float p[6], sT = 0.f, sC = 0.f, sS = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int src = (k - r + 6) % 6;
+        float vk = v[0];
+#pragma unroll
+        for (int m = 1; m < 6; ++m) vk = (src == m) ? v[m] : vk;
+        p[k] = T * vk;
+        sT += p[k];
+        sC += p[k] * MAP6_C2F[k];
+        sS += p[k] * MAP6_S2F[k];
+    }
+    const float dT = T - sT, dC = Zc - sC, dS = Zs - sS, lb = (float)rel * T;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float pk = fmaxf(p[k] + (dT + 2.f * (dC * MAP6_C2F[k] + dS * MAP6_S2F[k])) * (1.f / 6.f), lb);
+        a[k] = (double)sqrtf(pk);
+    }
+    return true;
+}
+
 // per pixel: scales (FP64, six planes per batch entry) and the largest
 // footprint half-extents of each tile
 __global__ void k_map6(const float* __restrict__ params, int kind, long long HW, int B, int W, int tile, int tiles_x,
                        int ntile, double eps, double eta, double rel, double ascale, double* __restrict__ scales,
-                       unsigned* __restrict__ tile_ext, unsigned* __restrict__ status) {
+                       unsigned* __restrict__ tile_ext, unsigned* __restrict__ status,
+                       const float* __restrict__ lut) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= HW * B) return;
     const long long b = gid / HW, p = gid - b * HW;
@@ -779,9 +911,13 @@ __global__ void k_map6(const float* __restrict__ params, int kind, long long HW,
         if (flag) raise_status(status, BSF_EBADSCALE);
     } else {
         const float* q = params + b * 3 * HW + p;
-        const map6_result R = map6_solve(kind, q[0], q[HW], q[2 * HW], eps, eta, rel);
-        for (int k = 0; k < 6; ++k) a[k] = R.a[k] * ascale;
-        flag = R.flag;
+        if (lut != nullptr && lut6_lookup(lut, kind, q[0], q[HW], q[2 * HW], eps, eta, rel, a, flag)) {
+            for (int k = 0; k < 6; ++k) a[k] *= ascale;
+        } else {
+            const map6_result R = map6_solve(kind, q[0], q[HW], q[2 * HW], eps, eta, rel);
+            for (int k = 0; k < 6; ++k) a[k] = R.a[k] * ascale;
+            flag = R.flag;
+        }
         if (flag & 1) raise_status(status, BSF_EINFEASIBLE);
         if (flag & 4) raise_status(status, BSF_EBADSCALE);
     }
@@ -800,12 +936,20 @@ __global__ void k_map6(const float* __restrict__ params, int kind, long long HW,
 
 // the scales of bsf_scales_from_cov for N = 6 (float32, six planes, flags)
 __global__ void k_map6_out(const float* __restrict__ params, int kind, long long npix, double eps, double eta,
-                           double rel, float* __restrict__ scales, uint8_t* __restrict__ flags) {
+                           double rel, float* __restrict__ scales, uint8_t* __restrict__ flags,
+                           const float* __restrict__ lut) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    const map6_result R = map6_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta, rel);
-    for (int k = 0; k < 6; ++k) scales[k * npix + p] = (float)R.a[k];
-    if (flags) flags[p] = (uint8_t)R.flag;
+    double a[6];
+    int flag = 0;
+    if (lut == nullptr ||
+        !lut6_lookup(lut, kind, params[p], params[npix + p], params[2 * npix + p], eps, eta, rel, a, flag)) {
+        const map6_result R = map6_solve(kind, params[p], params[npix + p], params[2 * npix + p], eps, eta, rel);
+        for (int k = 0; k < 6; ++k) a[k] = R.a[k];
+        flag = R.flag;
+    }
+    for (int k = 0; k < 6; ++k) scales[k * npix + p] = (float)a[k];
+    if (flags) flags[p] = (uint8_t)flag;
 }
 
 constexpr int PRE_THREADS = HEX6_PRE_THREADS;
@@ -1320,20 +1464,29 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_hex6_stencil(const double* __
 }  // namespace
 
 
+size_t lut6_bytes() { return (size_t)(LUT6_NU + 1) * (LUT6_NP + 1) * 8 * sizeof(float); }
+
+cudaError_t launch_lut6_build(double eta, double rel, float* table, cudaStream_t st) {
+    const int n = (LUT6_NU + 1) * (LUT6_NP + 1);
+    k_lut6_build<<<(n + 127) / 128, 128, 0, st>>>(eta, rel, table);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_map6(const float* params, int kind, int B, int H, int W, int tile, double eps, double eta,
                         double rel, double ascale, double* scales, unsigned* tile_ext, unsigned* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float* lut) {
     const long long HW = (long long)H * W, n = HW * B;
     const int tiles_x = (W + tile - 1) / tile, tiles_y = (H + tile - 1) / tile;
     k_map6<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(params, kind, HW, B, W, tile, tiles_x, tiles_x * tiles_y, eps,
-                                                        eta, rel, ascale, scales, tile_ext, status);
+                                                        eta, rel, ascale, scales, tile_ext, status, lut);
     return cudaGetLastError();
 }
 
 cudaError_t launch_map6_out(const float* params, int kind, long long npix, double eps, double eta, double rel,
-                            float* scales, uint8_t* flags, cudaStream_t st) {
+                            float* scales, uint8_t* flags, cudaStream_t st, const float* lut) {
     if (npix == 0) return cudaSuccess;
-    k_map6_out<<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(params, kind, npix, eps, eta, rel, scales, flags);
+    k_map6_out<<<(unsigned)((npix + 127) / 128), 128, 0, st>>>(params, kind, npix, eps, eta, rel, scales, flags,
+                                                               lut);
     return cudaGetLastError();
 }
 

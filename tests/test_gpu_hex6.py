@@ -323,3 +323,93 @@ def test_reflect_boundary():
     assert _nerr(got.ravel()[idx], ref) < TOL
     got0, _ = _run(f, p, "srt")
     assert _nerr(got0.ravel()[idx], ref) > 1e-4  # borders differ with the zero boundary
+
+
+def _srt_sweep(n, seed, rho_hi=60.0):
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(0.5, 40.0, n)
+    r = np.exp(rng.uniform(0.0, math.log(rho_hi), n))
+    t = rng.uniform(-math.pi, 2 * math.pi, n)
+    t[:6] = np.arange(6) * math.pi / 6  # on the rotation steps
+    return np.stack([s, r, t]).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["srt", "cov"])
+def test_map_table_scales(kind, accuracy_record):
+    """The map read from its table (opts.map_lut) against the oracle's KKT map
+    over sigma in [0.5, 40], rho in [1, 60] and every orientation.  The table
+    kernels keep the target covariance (the moments sum p, sum p cos 2 theta_k,
+    sum p sin 2 theta_k of p = a^2 equal those of the oracle's p, to 2e-5 of
+    the trace T); the interpolation moves p by at most 1e-3 T (bilinear error
+    at the kinks where a width leaves its bound), recorded with the relative
+    error of the widths.  Flags follow the solver's (a clamp decided in FP32
+    may differ at the bound itself)."""
+    dev = _cuda()
+    P = _srt_sweep(4000, 91)
+    if kind == "cov":
+        s, r, t = P.astype(np.float64)
+        l1, l2 = s * s, s * s / r
+        c, sn = np.cos(t), np.sin(t)
+        P = np.stack([l1 * c * c + l2 * sn * sn, (l1 - l2) * c * sn, l1 * sn * sn + l2 * c * c]).astype(np.float32)
+    ki = 2 if kind == "srt" else 1
+    sc, fl = api.scales_from_cov(torch.from_numpy(P).to(dev), kind=kind, N=6, map_lut=True)
+    sc, fl = sc.cpu().numpy().astype(np.float64), fl.cpu().numpy()
+    ref, rfl = n6.map6(P.astype(np.float64), ki)
+    assert np.all((rfl & 4) == 0)
+    p, q = sc ** 2, ref ** 2
+    T = q.sum(0)
+    c2 = np.cos(2 * n6.directions(6))[:, None]
+    s2 = np.sin(2 * n6.directions(6))[:, None]
+    mom = np.maximum.reduce([np.abs(p.sum(0) - T), np.abs((c2 * (p - q)).sum(0)),
+                             np.abs((s2 * (p - q)).sum(0))]) / T
+    dpt = (np.abs(p - q) / T).max(0)
+    rel = np.abs(sc - ref) / ref
+    accuracy_record[f"n6_map_table_{kind}"] = {
+        "pixels": int(P.shape[1]), "max_dp_over_T": float(dpt.max()), "median_dp_over_T": float(np.median(dpt)),
+        "max_moment_error_over_T": float(mom.max()), "max_rel_width": float(rel.max()),
+        "p99_rel_width": float(np.quantile(rel, 0.99)), "median_rel_width": float(np.median(rel))}
+    print(f"map table ({kind}): max |dp|/T {dpt.max():.3e} (median {np.median(dpt):.3e}), moments {mom.max():.3e}, "
+          f"widths: max rel {rel.max():.3e}, p99 {np.quantile(rel, 0.99):.3e}, median {np.median(rel):.3e}")
+    assert mom.max() < 2e-5, mom.max()
+    assert dpt.max() < 1e-3, dpt.max()
+    assert (fl != rfl).mean() < 1e-3
+
+
+def test_map_table_fallback_pixels_take_the_solver():
+    """Pixels the table does not serve (kernels so small that eps binds, invalid
+    input) and every pixel with rel_bound = 0 get the solver's scales bit for bit."""
+    dev = _cuda()
+    s = np.array([0.01, 0.02, 0.005, np.inf, 2.0, 2.0, 3.0], np.float32)
+    r = np.array([1.5, 3.0, 1.0, 2.0, 0.0, 2.0, 2.0], np.float32)
+    t = np.array([0.3, 1.0, 0.0, 0.0, 0.0, np.nan, 0.5], np.float32)
+    P = torch.from_numpy(np.stack([s, r, t])).to(dev)
+    a0, f0 = api.scales_from_cov(P, kind="srt", N=6)
+    a1, f1 = api.scales_from_cov(P, kind="srt", N=6, map_lut=True)
+    assert torch.equal(f0, f1)
+    assert torch.equal(torch.nan_to_num(a0[:, :6], nan=-1.0), torch.nan_to_num(a1[:, :6], nan=-1.0))
+    Q = torch.from_numpy(_srt_sweep(500, 92)).to(dev)
+    b0, g0 = api.scales_from_cov(Q, kind="srt", N=6, rel_bound=0.0)
+    b1, g1 = api.scales_from_cov(Q, kind="srt", N=6, rel_bound=0.0, map_lut=True)
+    assert torch.equal(g0, g1) and torch.equal(b0, b1)
+
+
+def test_map_table_filter_uses_the_table_scales(accuracy_record):
+    """The filter with map_lut against the definition at the table's own scales
+    (read back through bsf_scales_from_cov with map_lut, within the path's 1e-5
+    bar), and its distance to the filter at the solver's scales, recorded."""
+    H, W = 96, 104
+    f = synth.image(H, W, seed=93, dtype="f32")
+    p = synth.srt_field(H, W, seed=93, sigma=(1.5, 6.0), rho=(1.0, 8.0))
+    got, st = _run(f, p, "srt", map_lut=True)
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    dev = _cuda()
+    sc, _ = api.scales_from_cov(torch.from_numpy(p).to(dev), kind="srt", N=6, map_lut=True)
+    A = sc.cpu().numpy().astype(np.float64)
+    idx = _sample(H, W, 30, seed=93)
+    ref = n6.direct6_hex(f.astype(np.float64), A, idx, 0.5)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+    exact, _ = _run(f, p, "srt")
+    d = _nerr(got.ravel()[idx], exact.ravel()[idx])
+    accuracy_record["n6_map_table_filter"] = {"pixels": int(idx.size), "max_normwise_vs_solver_scales": d}
+    print(f"filter with the map table vs the solver's scales: max normwise difference {d:.3e}")
+    assert d < 1e-3
