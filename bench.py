@@ -404,7 +404,7 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     ctx = api.context(dev)
     opts = api.make_opts("exact" if args.precision == "exact" else "fp64", max_scale=smax,
-                         hex_spacing=args.hex_spacing, map_lut=args.map_lut)
+                         hex_spacing=args.hex_spacing, map_lut=args.map_lut, staging=args.staging)
     stream = torch.cuda.current_stream(dev)
     sptr = int(stream.cuda_stream)
 
@@ -601,6 +601,7 @@ def run_ours(args):
                    "workload_id": args.workload, **({"hex_spacing": args.hex_spacing} if N == 6 else {}),
                    **({"sigma_max": args.sigma_max} if args.sigma_max is not None else {}),
                    **({"map": "table"} if args.map_lut else {}),
+                   **({"stencil_staging": "tma"} if args.staging == "tma" else {}),
                    "precision": args.precision, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))},
@@ -819,6 +820,8 @@ def main():
     ap.add_argument("--pool-side", type=int, default=4096)
     ap.add_argument("--hex-spacing", type=float, default=0.5, help="N=6: lattice spacing h (1, 0.5, 0.25, 0.125)")
     ap.add_argument("--sigma-max", type=float, default=None, help="batched workloads: cap the size field at this sigma")
+    ap.add_argument("--staging", choices=["l1", "tma"], default="l1",
+                    help="N=4 u8: the stencil reads its buffer through L1 or from TMA-staged shared-memory boxes")
     ap.add_argument("--map-lut", action="store_true",
                     help="N=6: read the scale map from its table (an approximation) instead of solving it per pixel")
     args = ap.parse_args()

@@ -111,6 +111,9 @@ typedef int bsf_status;
                              scales rounded to a per-pixel dyadic grid; one final FP32 rounding */
 #define BSF_PREC_FP64 1   /* all-FP64: Algorithm 1 computed literally in double precision */
 
+#define BSF_STAGING_L1 0
+#define BSF_STAGING_TMA 1
+
 typedef struct bsf_ctx bsf_ctx;
 
 typedef struct {
@@ -157,6 +160,12 @@ typedef struct {
                          times T), rel_bound = 0 and invalid input take the solver.  The table
                          (8.4 MB of device memory, kept by the context) is built on the first call
                          for each (eta, rel_bound), which then waits on its stream once. */
+    int staging;      /* N = 4, exact 64-bit form (u8 images): how the stencil reads the
+                         pre-integrated buffer.  BSF_STAGING_L1 (default): nine loads per tap
+                         through the L1 cache.  BSF_STAGING_TMA: per CTA of 32 x 8 pixels and per
+                         tap, the box of cells the tile reads is copied to shared memory by the
+                         tensor-copy engine first (taps whose box exceeds 40 x 16 elements read
+                         through L1).  Both give the same bits; other forms ignore the field. */
 } bsf_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -34,6 +34,8 @@ BSF_PARAM_SRT = 2
 
 BSF_BOUNDARY_ZERO = 0
 BSF_BOUNDARY_REFLECT = 1
+BSF_STAGING_L1 = 0
+BSF_STAGING_TMA = 1
 
 BSF_PREC_EXACT = 0
 BSF_PREC_FP64 = 1
@@ -60,6 +62,7 @@ class bsf_opts(ctypes.Structure):
         ("rel_bound", ctypes.c_float),
         ("boundary", ctypes.c_int),
         ("map_lut", ctypes.c_int),
+        ("staging", ctypes.c_int),
     ]
 
 

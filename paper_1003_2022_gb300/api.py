@@ -41,9 +41,11 @@ def _stream_ptr(stream) -> int:
 
 
 def make_opts(precision="exact", halo=0, max_scale=0.0, eps=1e-3, eta=1e-3, strict=False,
-              iterations=1, hex_spacing=0.5, rel_bound=1e-3, boundary="zero", map_lut=False) -> L.bsf_opts:
+              iterations=1, hex_spacing=0.5, rel_bound=1e-3, boundary="zero", map_lut=False,
+              staging="l1") -> L.bsf_opts:
     o = L.default_opts()
     o.map_lut = 1 if map_lut else 0
+    o.staging = {"l1": L.BSF_STAGING_L1, "tma": L.BSF_STAGING_TMA}[staging]
     o.boundary = {"zero": L.BSF_BOUNDARY_ZERO, "reflect": L.BSF_BOUNDARY_REFLECT}[boundary]
     o.iterations = int(iterations)
     o.hex_spacing = float(hex_spacing)
@@ -71,7 +73,7 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
            halo: int = 0, max_scale: float = 0.0, eps: float = 1e-3, eta: float = 1e-3, strict: bool = False,
            out: torch.Tensor | None = None, stream=None, iterations: int = 1,
            hex_spacing: float = 0.5, rel_bound: float = 1e-3, boundary: str = "zero",
-           map_lut: bool = False) -> torch.Tensor:
+           map_lut: bool = False, staging: str = "l1") -> torch.Tensor:
     """Space-variant elliptical box-spline filter fbar[n] = sum_k f[k] beta_{a(n)}(n-k).
 
     N = 4 or 6 directions; N = 6 runs on the hexagonal lattice of spacing
@@ -81,7 +83,8 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
     bound p_k >= max(eps, rel_bound * sum p) (see bsf_opts).  boundary: "zero"
     (f = 0 outside the image) or "reflect" (half-sample symmetric extension).
     map_lut: N = 6 only, read the map from its table instead of solving it per
-    pixel (an approximation; see bsf_opts.map_lut)."""
+    pixel (an approximation; see bsf_opts.map_lut).  staging: "l1" or "tma",
+    how the four-directional exact stencil reads its buffer (same results)."""
     img = _as4d(image)
     if not img.is_cuda:
         raise ValueError("image must be a CUDA tensor")
@@ -100,7 +103,7 @@ def filter(image: torch.Tensor, params: torch.Tensor, kind: str = "srt", N: int 
         out = torch.empty((B, C, H, W), dtype=torch.float32, device=img.device)
     dtype = L.BSF_U8 if img.dtype == torch.uint8 else L.BSF_F32
     opts = make_opts(precision, halo, max_scale, eps, eta, strict, iterations, hex_spacing, rel_bound, boundary,
-                     map_lut)
+                     map_lut, staging)
     rc = L.bsf_filter(context(img.device), img.data_ptr(), dtype, B, C, H, W, N, prm.data_ptr(), _KINDS[kind],
                       opts, out.data_ptr(), _stream_ptr(stream))
     L.check(rc, "bsf_filter")

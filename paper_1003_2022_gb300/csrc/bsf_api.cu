@@ -144,6 +144,7 @@ void bsf_default_opts(bsf_opts* o) {
     o->rel_bound = 1e-3f;
     o->boundary = BSF_BOUNDARY_ZERO;
     o->map_lut = 0;
+    o->staging = BSF_STAGING_L1;
 }
 
 const char* bsf_status_string(bsf_status s) {
@@ -398,7 +399,8 @@ static bsf_status n4_layout_of(int dtype, int64_t B, int64_t C, int64_t H, int64
     const int nstrip = Wfull <= maxw ? 1 : (int)((W + (maxw - 2 * P) - 1) / (maxw - 2 * P));
     if (nstrip > 1 && maxw - 2 * P < 64) return BSF_EINVAL;
     const int Ws = (int)((W + nstrip - 1) / nstrip);
-    const int Hp = (int)H + 2 * P, Wp = (nstrip == 1 ? (int)W : Ws) + 2 * P, pitch = Wp;
+    // rows padded to an even number of elements: 16-byte aligned rows for the staged stencil's tensor map
+    const int Hp = (int)H + 2 * P, Wp = (nstrip == 1 ? (int)W : Ws) + 2 * P, pitch = (Wp + 1) & ~1;
     const size_t per_img = (size_t)Hp * pitch * elem_bytes(mode);
     // images per launch: whole batch entries, bounded by a 16 GiB buffer budget
     const size_t budget = (size_t)16 << 30;
@@ -459,6 +461,8 @@ static bsf_status filter_pass(bsf_ctx* c, const void* image, int dtype, int64_t 
             a.ascale = ascale;
             a.out = out + (size_t)(b0 * C) * HW;
             a.status = c->d_status;
+            a.staging = o.staging;
+            a.polls = bsf_wait_limit();
             BSF_TRY(prof_mark(c, 1, st));
             BSF_TRY(launch_stencil4(mode, a, st));
             BSF_TRY(prof_mark(c, 2, st));

@@ -64,6 +64,8 @@ struct stencil_args {
     float ascale = 1.f;    // widths multiplier (1/sqrt(m) in a pass of the m-fold iterated filter)
     float* out;
     unsigned* status;
+    int staging = 0;       // opts.staging: BSF_STAGING_TMA selects the TMA-staged form (64-bit exact mode)
+    unsigned polls = 0;    // bound of its waits (0: the default)
 };
 
 cudaError_t launch_stencil4(int mode, const stencil_args& a, cudaStream_t st);
