@@ -51,9 +51,10 @@ STENCIL_INT_OPS_PER_PX = 16 * 124
 # product (88), two words per product sum and accumulator (28), 32 for
 # position, truncation, bounds and addresses: 260 per tap
 STENCIL_INT_OPS_PER_PX_U128 = 16 * 260
-# six directions: 64 taps x 24 lattice points x 15 coefficients x 5 twenty-bit limbs,
-# one int32 multiply-add each
-HEX6_IMAD_PER_PX = 64 * 24 * 15 * 5
+# six directions: the exact coefficient sums on the tensor cores.  Per round a warp's
+# 24 mma.sync.m16n8k16 (3 words x 4 bytes x 2 k-steps; 16 x 8 x 16 multiply-adds each)
+# cover 8 taps: 3 x 4096 FLOP per tap, 64 taps per pixel
+HEX6_TC_FLOP_PER_PX = 64 * 3 * 2 * 16 * 8 * 16
 # the method's work per output pixel as the hot-path table counts it: N = 4, 16 taps x
 # (partition select + 7 ZP weights + 7 multiply-adds) ~ 1.0k operations; N = 6, 64 taps,
 # 2.5k-4k operations (the midpoint is used)
@@ -530,14 +531,15 @@ def run_ours(args):
                                         and args.precision == "exact") else None
         alg_bytes = int((12 + 4 + 8 * (1 if u8 else 2)) * px_per_launch)
     else:
-        impl_ops = HEX6_IMAD_PER_PX
         kname = "k_hex6_stencil"
-        impl = {"what": "int32 multiply-adds of the exact coefficient sums: 64 taps x 24 lattice points x 15 "
-                        "coefficients x 5 twenty-bit limbs",
-                "ops_per_px": impl_ops, "achieved_tops": impl_ops * px_per_launch / (st_ms / 1e3) / 1e12,
-                "peak": 152 * 64 * 2.070e9 / 1e12,
-                "peak_note": "int32 multiply-add rate, 152 SMs x 64 per clock x 2070 MHz (derived)"}
-        impl["frac"] = impl["achieved_tops"] / impl["peak"]
+        tc_peak = float(peaks.get("bf16_tflops", 1887.8))
+        impl = {"what": "tensor-core FLOP of the exact coefficient sums (FP16 bytes x FP16 coefficients, "
+                        "FP32 sums, mma.sync.m16n8k16): 64 taps x 3 mma of 4096 FLOP",
+                "flop_per_px": HEX6_TC_FLOP_PER_PX,
+                "achieved_tflops": HEX6_TC_FLOP_PER_PX * px_per_launch / (st_ms / 1e3) / 1e12,
+                "peak": tc_peak,
+                "peak_note": "measured dense bf16 (burst) of this GPU; FP16 runs at the bf16 rate"}
+        impl["frac"] = impl["achieved_tflops"] / impl["peak"]
         traffic = None
         alg_bytes = int((12 + 4 + 16) * px_per_launch)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
