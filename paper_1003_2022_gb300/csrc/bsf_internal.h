@@ -95,8 +95,9 @@ cudaError_t launch_adaptive_cov(const float* J, long long HW, int B, float s0sq,
 // where the footprints are small; groups of 2 x 1, 4 x 1 or 4 x 2 64-tiles where
 // they are large); channel c of the tile's image has its window at
 // off + c * ncol * nrow elements (exact 128-bit running sums).
-constexpr int HEX6_PRE_THREADS = 512;  // largest block of the pre-integration
-constexpr int HEX6_PRE_CPT = 8;        // window columns per pre-integration thread
+constexpr int HEX6_PRE_THREADS = 832;  // largest block of the pre-integration
+constexpr int HEX6_PRE_CPT = 4;        // window columns per pre-integration thread
+constexpr int HEX6_PRE_PAD = 8;        // one padding element per this many columns of a state row
 struct hex6_tile {
     long long off;   // 16-byte elements from the chunk's window base
     int i_left;      // lattice column i of storage column 0 in row 0

@@ -966,10 +966,13 @@ constexpr int MU_FRAC_BITS = 24;  // fixed point of the transferred masses
 // the four sums whose rows shift by one to three columns (the neighbouring
 // threads read them), in registers for the two that do not shift.
 // Shared-memory index of window column c: one padding element after every
-// PRE_CPT, so that the 32 lanes of a warp, which own columns PRE_CPT apart,
-// touch every bank once per 128 bytes (without it, a 16-byte state access of
-// a warp is a 32-way bank conflict).
-__device__ __forceinline__ int pidx(int c) { return c + c / PRE_CPT; }
+// eight columns, so that the lanes of a warp, which own columns PRE_CPT = 4
+// apart, spread a 16-byte state access over all banks (each quarter-warp
+// touches eight distinct 16-byte bank groups; without the padding, eight lanes
+// share two of them).  Four columns per thread rather than eight halve the
+// registers of the per-column states and double the warps per window: on the
+// batch's largest windows one CTA per SM then holds 26 warps instead of 13.
+__device__ __forceinline__ int pidx(int c) { return c + c / HEX6_PRE_PAD; }
 
 // The stencil reads the window values as three 32-bit limbs of g + 2^95, so
 // every value must lie in [-2^95, 2^95).  The kernel checks that and that no
@@ -1493,7 +1496,7 @@ cudaError_t launch_map6_out(const float* params, int kind, long long npix, doubl
 cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int W, double h, const hex6_tile* tiles,
                                int ntiles, int ncol_max, void* scratch, unsigned* wflag, cudaStream_t st,
                                int reflect) {
-    const size_t smem = (4 * (size_t)(ncol_max + ncol_max / PRE_CPT + 1) + 32) * sizeof(u128);
+    const size_t smem = (4 * (size_t)(ncol_max + ncol_max / HEX6_PRE_PAD + 1) + 32) * sizeof(u128);
     // as many threads as the widest window of the chunk needs (PRE_CPT columns each, whole
     // warps): narrow windows take small blocks, several of them per SM
     if (ncol_max < 1 || ncol_max > PRE_THREADS * PRE_CPT) return cudaErrorInvalidValue;
@@ -1502,7 +1505,8 @@ cudaError_t launch_hex6_preint(int dtype_u8, const void* img, int C, int H, int 
     // the attribute is the kernel's largest shared-memory size (set on every launch, the
     // same value each time: launches from several host threads never lower it for another);
     // each launch still asks only for its chunk's size
-    const int smem_cap = (int)((4 * (size_t)(hex6_max_cols() + hex6_max_cols() / PRE_CPT + 1) + 32) * sizeof(u128));
+    const int smem_cap =
+        (int)((4 * (size_t)(hex6_max_cols() + hex6_max_cols() / HEX6_PRE_PAD + 1) + 32) * sizeof(u128));
     if ((int)smem > smem_cap) return cudaErrorInvalidValue;
     if (dtype_u8) {
         cudaFuncSetAttribute(k_hex6_preint<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap);

@@ -47,7 +47,7 @@ void hex6_window(int tx0, int ty0, int tw, int th_, int H, int W, double ex, dou
 // warp totals in 227 KB of shared memory
 int hex6_max_cols() {
     return std::min(HEX6_PRE_THREADS * HEX6_PRE_CPT,
-                    (232448 - 32 * 16) / (4 * 16) * HEX6_PRE_CPT / (HEX6_PRE_CPT + 1) - 8);
+                    (232448 - 32 * 16) / (4 * 16) * HEX6_PRE_PAD / (HEX6_PRE_PAD + 1) - 8);
 }
 
 // tile records and chunks from the largest footprint half-extents of every
