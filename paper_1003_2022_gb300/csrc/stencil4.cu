@@ -540,13 +540,10 @@ static cudaError_t launch_tma(const stencil_args& a, cudaStream_t st) {
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    static bool attr = false;  // set once; the same value every time
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_stencil4_tma<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // the attribute is per device: set on every launch (a cheap host call, always the same value)
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_stencil4_tma<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
+    if (e != cudaSuccess) return e;
     dim3 blk(32, TMA_ROWS), grd((ws + 31) / 32, (a.H + TMA_ROWS - 1) / TMA_ROWS, a.nimg);
     k_stencil4_tma<KIND><<<grd, blk, TMA_SMEM, st>>>(map, (const unsigned long long*)a.buf, a.buf_stride, a.Hp, a.Wp,
                                                      a.pitch, a.P, a.H, a.W, a.C, a.col0, min(a.col0 + ws, a.W),
