@@ -183,16 +183,23 @@ def test_batched_rgb_4096_workload_six_directions(accuracy_record):
     """The paper-shaped batch with N = 6 (4 x 3 x 4096 x 4096, sigma 2-48, rho
     1-6) in one call, against the oracle's definition on the transferred image
     at sampled pixels of every (image, channel).  The method error of the
-    transfer (against the definition on the pixel comb) is recorded beside it."""
+    transfer (against the definition on the pixel comb) is recorded beside it.
+    The same call with the map read from its table (opts.map_lut) is held to
+    the same bar against the same references (the oracle's exact map)."""
     from oracle import n6
     dev = _cuda()
     imgs, prm = synth.batch_inputs("b4c3_4096_f32_n6")
     B, C, H, W = imgs.shape
-    out = api.filter(torch.from_numpy(imgs).to(dev), torch.from_numpy(prm).to(dev), kind="srt", N=6)
+    img_d, prm_d = torch.from_numpy(imgs).to(dev), torch.from_numpy(prm).to(dev)
+    out = api.filter(img_d, prm_d, kind="srt", N=6)
     st = api.device_status(dev)
     assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
     out = out.cpu().numpy()
-    gots, refs, mg, mr = [], [], [], []
+    out_lut = api.filter(img_d, prm_d, kind="srt", N=6, map_lut=True)
+    assert api.device_status(dev) & ~(1 << L.BSF_EINFEASIBLE) == 0
+    out_lut = out_lut.cpu().numpy()
+    del img_d, prm_d
+    gots, refs, mg, mr, lut = [], [], [], [], []
     for b in range(B):
         for c in range(C):
             for p in _samples(H, W, 1, seed=300 + 10 * b + c)[:2]:
@@ -200,10 +207,14 @@ def test_batched_rgb_4096_workload_six_directions(accuracy_record):
                 a, _ = n6.map6(prm[b][:, y, x].reshape(3, 1).astype(np.float64), 2)
                 refs.append(_direct6_on_crop(imgs[b, c], a[:, 0], y, x))
                 gots.append(out[b, c, y, x])
+                lut.append(out_lut[b, c, y, x])
                 if c == 0 and len(mr) < 4:
                     mg.append(refs[-1])
                     mr.append(_direct6_on_crop(imgs[b, c], a[:, 0], y, x, definition=True))
     fig = _figures(np.array(gots), np.array(refs))
     accuracy_record["b4c3_4096_f32_n6/exact_hex"] = fig
     accuracy_record["b4c3_4096_f32_n6/method_error_vs_pixel_comb"] = _figures(np.array(mg), np.array(mr))
+    fig_lut = _figures(np.array(lut), np.array(refs))
+    accuracy_record["b4c3_4096_f32_n6/exact_hex_map_table"] = fig_lut
     assert fig["max_norm"] < TOL
+    assert fig_lut["max_norm"] < TOL
