@@ -119,3 +119,30 @@ def test_query_workspace_host_only(lib):
     with pytest.raises(lib.BsfError) as e:
         lib.bsf_query_workspace(None, lib.BSF_U8, 1, 1, 64, 64, 5, lib.BSF_PARAM_SRT, o)
     assert e.value.code == lib.BSF_EUNSUPPORTED
+
+
+def test_opts_layout_matches_the_header(lib, tmp_path):
+    """The ctypes bsf_opts has the C struct's size and field offsets (compiled
+    from include/bsf.h with the host compiler), and the defaults of the
+    optional modes are off."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("needs a C compiler")
+    fields = [f[0] for f in lib.bsf_opts._fields_]
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'    printf("{n} %zu\\n", offsetof(bsf_opts, {n}));' for n in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bsf.h"\nint main(void) {\n'
+                   '    printf("sizeof %zu\\n", sizeof(bsf_opts));\n' + body + "\n    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.split("\n") if line)
+    assert int(out["sizeof"]) == ctypes.sizeof(lib.bsf_opts)
+    for n in fields:
+        assert int(out[n]) == getattr(lib.bsf_opts, n).offset, n
+    o = lib.default_opts()
+    assert o.map_lut == 0 and o.staging == lib.BSF_STAGING_L1 and o.boundary == lib.BSF_BOUNDARY_ZERO
