@@ -461,10 +461,12 @@ static void launch_band(const scan_plan& p, const InT* img, long long img_stride
                         cudaStream_t st, int reflect) {
     typedef typename mode_traits<MODE>::T T;
     dim3 grid(p.nb, nimg);
-    // one fixed cap (a row of at most 4096 16-byte elements), so that launches from several host
-    // threads never lower it for one another; each launch still asks for its own size
+    // Any dynamic shared memory opts in to one fixed cap (a row of at most 4096 16-byte elements):
+    // the kernel's static shared memory (up to 3 KB) counts against the 48 KB default too, and a
+    // fixed value keeps launches from several host threads from lowering it for one another; each
+    // launch still asks for its own size
     constexpr int kBandSmemCap = 4096 * 16;
-    if (p.smem > 48 * 1024)
+    if (p.smem > 0)
         cudaFuncSetAttribute(k_band<MODE, InT, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemCap);
     k_band<MODE, InT, CPT><<<grid, p.threads, p.smem, st>>>(img, img_stride, H, W, col0, P, Hp, Wp, pitch, p.band_h, p.nb,
                                                         (const T*)carry, (T*)local, (T*)G, G_stride, reflect);

@@ -72,7 +72,8 @@ def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: floa
     the library's scratch.  N = 4: pre-integrated buffers (8 B/elem for uint8,
     16 B for float32) and scan carries.  N = 6: FP64 scales (48 B/px) and the
     lattice windows of the 64-pixel tiles (spacing 0.5 px, 16 B per lattice
-    point), at most 8 GiB of them at a time."""
+    point), at most 8 GiB of them per chunk, in two buffers (the windows of the
+    next chunk are pre-integrated while the current chunk's stencil runs)."""
     io = C * H * W * image_itemsize + 3 * H * W * 4 + C * H * W * 4
     if N == 6:
         # half-extent of a footprint: sum_k a_k |cos theta_k| / 2 <= sqrt(3 sum_k a_k^2) / 2
@@ -82,7 +83,7 @@ def footprint_bytes(C: int, H: int, W: int, image_itemsize: int, max_sigma: floa
         R = 64 + 2 * 4.25 * max_sigma + 10
         tiles = math.ceil(H / 64) * math.ceil(W / 64)
         win = min(8 << 30, int(tiles * C * 16 * 5.46 * R * 2.31 * R))
-        return io + 48 * H * W + win
+        return io + 48 * H * W + 2 * win
     P = halo_for_sigma(max_sigma)
     Hp, Wp = H + 2 * P, W + 2 * P
     elem = 8 if image_itemsize == 1 else 16

@@ -326,6 +326,28 @@ def test_unsupported_n_and_bad_args():
     assert rc == L.BSF_EINVAL
 
 
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_every_band_width_class_runs(dtype):
+    """Image widths across every shape class of the band sweep (columns per
+    thread 1-8, thread counts up to each class's bound, one strip or several),
+    including padded widths in (2816, 3072] where the 128-bit form's row of
+    dynamic shared memory reaches 48 KB and, with the kernel's static shared
+    memory, needs the opt-in attribute: every call succeeds and matches the
+    oracle at sampled pixels."""
+    H = 10
+    rng = np.random.default_rng(17)
+    for W in (1, 7, 255, 257, 511, 1025, 1500, 2047, 2049, 2500, 2790, 2850, 2900, 3000, 3030, 3100, 4000,
+              4100):
+        f = synth.image(H, W, seed=W, dtype=dtype)
+        p = synth.srt_field(H, W, seed=W, sigma=(1.0, 4.0), rho=(1.0, 4.0))
+        out, st = _run(f, p, "srt", max_scale=4.0)
+        assert st & ~(1 << L.BSF_EINFEASIBLE) == 0, W
+        a, _ = O.map4(p.astype(np.float64), O.KIND_SRT)
+        idx = np.unique(np.concatenate([rng.integers(0, H * W, 12), [0, W - 1, H * W - 1]]))
+        ref = O.direct4(f.astype(np.float64), a, idx)
+        assert _nerr(out.ravel()[idx], ref) < TOL, W
+
+
 @pytest.mark.parametrize("dtype,W", [("f32", 3300), ("u8", 4200)])
 def test_wide_images_are_filtered_in_strips(dtype, W):
     """Rows wider than one band CTA holds (float32: 3072 buffer columns, uint8:
