@@ -660,7 +660,8 @@ bsf_status bsf_query_workspace(bsf_ctx* c, int dtype, int64_t B, int64_t C, int6
         const double win = (double)tiles * C * t.ncol * t.nrow * 16.0;
         total += (size_t)B * 6 * HW * sizeof(double) + (size_t)tiles * 2 * sizeof(unsigned) +
                  (size_t)tiles * (sizeof(hex6_tile) + C * sizeof(unsigned)) +
-                 2 * (size_t)std::min(win, (double)((size_t)8 << 30));  // two window buffers
+                 2 * (size_t)std::min(win, (double)((size_t)8 << 30)) +  // two window buffers
+                 (o.map_lut ? lut6_bytes() : 0);                           // the map's table
     }
     *bytes = total;
     return BSF_OK;
