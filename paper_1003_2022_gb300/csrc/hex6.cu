@@ -1020,6 +1020,14 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
         const double kyd = floor(pyd);
         const int ky0 = (int)kyd;
         const float dy0 = (float)(kyd - pyd);  // (pixel row ky0) - (lattice row), in (-1, 0]
+        // the image row the lattice rows two to three ahead first need (their columns lie about
+        // 1.5 h px per row further left), fetched into L1 now: one line per thread, no registers
+        if (c0 < ncol) {
+            const int kyp = ky0 + 2;
+            const int kxp = (int)floorf(hf * ((float)(c0 + tl.i_left - 2 * r) + 0.5f * (float)j)) - 2;
+            if (kyp >= 0 && kyp < H && kxp < W)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(f + (size_t)kyp * W + (kxp > 0 ? kxp : 0)));
+        }
         u128 run = 0;
 #pragma unroll
         for (int e = 0; e < PRE_CPT; ++e) {
