@@ -198,7 +198,7 @@ __device__ __forceinline__ bool spd_solve(int d, const R A[3][3], const R b[3], 
 // the bound multipliers, and the most negative one (below -mult_tol * |g|)
 // leaves the working set.  R = float for the first pass, double for the last.
 template <class R>
-__device__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int& nw, int max_it, R step_tol,
+__device__ __forceinline__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int& nw, int max_it, R step_tol,
                             R mult_tol, R armijo_rel) {
     for (int it = 0; it < max_it; ++it) {
         R p[6];
@@ -310,18 +310,26 @@ __device__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int&
         if (d == 0 || dec <= R(0) || smax <= step_tol * T) {
             // converged on the face: bound multipliers from g = sum_{k in W} lambda_k z_k
             if (nw == 0) return;
+            // (fixed trip counts with guards: every array index is known at compile time, so the
+            // arrays stay in registers)
             R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[3] = {0, 0, 0}, lam[3] = {0, 0, 0};
             int idx[3] = {0, 0, 0}, a = 0;
 #pragma unroll
             for (int k = 0; k < 6; ++k)
                 if ((wmask >> k) & 1) {
-                    if (a < 3) idx[a] = k;
+                    idx[0] = a == 0 ? k : idx[0];
+                    idx[1] = a == 1 ? k : idx[1];
+                    idx[2] = a == 2 ? k : idx[2];
                     ++a;
                 }
-            for (int i = 0; i < nw; ++i) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= nw) break;
                 const int ki = idx[i];
                 rhs[i] = m6c<R>::z(ki, 0) * g[0] + m6c<R>::z(ki, 1) * g[1] + m6c<R>::z(ki, 2) * g[2];
-                for (int j2 = 0; j2 < nw; ++j2) {
+#pragma unroll
+                for (int j2 = 0; j2 < 3; ++j2) {
+                    if (j2 >= nw) break;
                     const int kj = idx[j2];
                     G[i][j2] = m6c<R>::z(ki, 0) * m6c<R>::z(kj, 0) + m6c<R>::z(ki, 1) * m6c<R>::z(kj, 1) +
                                m6c<R>::z(ki, 2) * m6c<R>::z(kj, 2);
@@ -331,8 +339,9 @@ __device__ void map6_newton(const R pbar[6], R lb, R T, R t[3], int& wmask, int&
             int worst = -1;
             const R gs = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
             R lw = -mult_tol * (gs + R(1e-30));
-            for (int i = 0; i < nw; ++i)
-                if (lam[i] < lw) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (i < nw && lam[i] < lw) {
                     lw = lam[i];
                     worst = idx[i];
                 }
@@ -410,7 +419,7 @@ __device__ __forceinline__ dflt m6_dz(int k, int l) {
 // gradient's accuracy (an FP32 Hessian only slows the convergence to a factor of
 // about 1e-7 per step).  Three steps from the FP32 solution reach the rounding level
 // of the double-float gradient.  Returns p in double.
-__device__ void map6_polish(const double pbar_d[6], double lb, const double t_d[3], int wmask, int nw,
+__device__ __forceinline__ void map6_polish(const double pbar_d[6], double lb, const double t_d[3], int wmask, int nw,
                             double p_out[6]) {
     dflt pbar[6], t[3];
 #pragma unroll
@@ -562,7 +571,7 @@ struct map6_p {
 // reproduces the covariance.  (The result is returned by value: the scales
 // must not travel through a pointer to the caller's local array, which the
 // device build did not write back reliably.)
-__device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
+__device__ __forceinline__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
     const double PI3 = 1.04719755119659774615;
     map6_p res;
     res.ok = true;
@@ -640,21 +649,34 @@ __device__ map6_p map6_active_set(double T, double Zc, double Zs, double lb) {
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             if ((wmask >> k) & 1) {
-                if (a < 3) idx[a] = k;
+                idx[0] = a == 0 ? k : idx[0];
+                idx[1] = a == 1 ? k : idx[1];
+                idx[2] = a == 2 ? k : idx[2];
                 ++a;
             }
         double pc[6];
         p_of_t(pbar, t, pc);
-        for (int i = 0; i < nw; ++i) {
-            rhs[i] = lb - pc[idx[i]];
-            for (int j = 0; j < nw; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i >= nw) break;
+            double pci = pc[0];
+#pragma unroll
+            for (int k = 1; k < 6; ++k) pci = idx[i] == k ? pc[k] : pci;
+            rhs[i] = lb - pci;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j >= nw) break;
                 G[i][j] = MAP6_Z[idx[i]][0] * MAP6_Z[idx[j]][0] + MAP6_Z[idx[i]][1] * MAP6_Z[idx[j]][1] +
                           MAP6_Z[idx[i]][2] * MAP6_Z[idx[j]][2];
+            }
         }
         if (spd_solve(nw, G, rhs, mu))
-            for (int i = 0; i < nw; ++i)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= nw) break;
 #pragma unroll
                 for (int l = 0; l < 3; ++l) t[l] += mu[i] * MAP6_Z[idx[i]][l];
+            }
     }
     map6_polish(pbar, lb, t, wmask, nw, p);
 #pragma unroll
