@@ -35,6 +35,7 @@
 #include "bsf_common.cuh"
 #include "bsf_internal.h"
 #include "hex6_tables.h"
+#include "map4.cuh"  // map4_sincos64: FP64 sin and cos from the Taylor series
 
 namespace {
 
@@ -577,14 +578,18 @@ __device__ __forceinline__ map6_p map6_active_set(double T, double Zc, double Zs
     res.ok = true;
     double* p = res.p;
     double pbar[6];
+    // (divisions by constants as multiplications: an FP64 division costs a dozen FP64 operations on
+    // this GPU's FP64 pipe, which the map is bound by; the results move by an ulp at most)
+    constexpr double I3 = 1.0 / 3.0, I6 = 1.0 / 6.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * MAP6_C2[k] + Zs * MAP6_S2[k])) / 6.0;
+    for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * MAP6_C2[k] + Zs * MAP6_S2[k])) * I6;
     const double den = T - 6.0 * lb;
     if (!(den > 0.0)) {
         res.ok = false;
         return res;
     }
-    const double zr = Zc / den, zi = Zs / den;
+    const double iden = 1.0 / den;
+    const double zr = Zc * iden, zi = Zs * iden;
     // the sector [k pi/3, (k+1) pi/3) holding the angle of (zr, zi): the one whose bisector
     // k pi/3 + pi/6 (30, 90, 150, 210, 270, 330 degrees) has the largest projection
     int ka = 0;
@@ -603,8 +608,9 @@ __device__ __forceinline__ map6_p map6_active_set(double T, double Zc, double Zs
     (void)PI3;
     const int kb = (ka + 1) % 6;
     const double dt = MAP6_C2[ka] * MAP6_S2[kb] - MAP6_S2[ka] * MAP6_C2[kb];
-    const double la = (zr * MAP6_S2[kb] - zi * MAP6_C2[kb]) / dt;
-    const double lbb = (MAP6_C2[ka] * zi - MAP6_S2[ka] * zr) / dt;
+    const double idt = 1.0 / dt;
+    const double la = (zr * MAP6_S2[kb] - zi * MAP6_C2[kb]) * idt;
+    const double lbb = (MAP6_C2[ka] * zi - MAP6_S2[ka] * zr) * idt;
     double l0 = 1.0 - la - lbb;
     if (l0 < -1e-12) {
         res.ok = false;
@@ -616,11 +622,11 @@ __device__ __forceinline__ map6_p map6_active_set(double T, double Zc, double Zs
     int wmask = 0, nw = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double ps = lb + den * (l0 / 6.0 + (k == ka ? la : 0.0) + (k == kb ? lbb : 0.0));
+        const double ps = lb + den * (l0 * I6 + (k == ka ? la : 0.0) + (k == kb ? lbb : 0.0));
         const double dps = ps - pbar[k];
-        t[0] += MAP6_Z[k][0] * dps / 3.0;
-        t[1] += MAP6_Z[k][1] * dps / 3.0;
-        t[2] += MAP6_Z[k][2] * dps / 6.0;
+        t[0] += MAP6_Z[k][0] * dps * I3;
+        t[1] += MAP6_Z[k][1] * dps * I3;
+        t[2] += MAP6_Z[k][2] * dps * I6;
         if (ps <= lb + tiny) {
             wmask |= 1 << k;
             ++nw;
@@ -705,14 +711,18 @@ __device__ map6_result map6_solve(int kind, float v0f, float v1f, float v2f, dou
     if (kind == BSF_PARAM_SRT) {
         lmax = v0 * v0;
         lmin = lmax / v1;
-        sincos(fmod(2.0 * v2, 6.283185307179586476925), &s2, &c2);
+        // 2 theta reduced by pi/2 inside the series routine (exact enough for |2 theta| < 64; larger
+        // angles are taken modulo 2 pi first)
+        const double x2 = 2.0 * v2;
+        map4_sincos64(fabs(x2) < 64.0 ? x2 : fmod(x2, 6.283185307179586476925), s2, c2);
         if (!(v2 == v2) || fabs(v2) > 1e30) c2 = s2 = BSF_QNAN64;
     } else {
         const double D = sqrt((v0 - v2) * (v0 - v2) + 4.0 * v1 * v1);
         lmax = 0.5 * (v0 + v2 + D);
         lmin = (v0 * v2 - v1 * v1) / lmax;
-        c2 = D > 0.0 ? (v0 - v2) / D : 1.0;
-        s2 = D > 0.0 ? 2.0 * v1 / D : 0.0;
+        const double iD = D > 0.0 ? 1.0 / D : 0.0;
+        c2 = D > 0.0 ? (v0 - v2) * iD : 1.0;
+        s2 = D > 0.0 ? 2.0 * v1 * iD : 0.0;
     }
     if (!(isfinite(lmax) && isfinite(lmin) && isfinite(c2) && isfinite(s2)) || !(lmin > 0.0) || !(lmax >= lmin)) {
         for (int k = 0; k < 6; ++k) R.a[k] = BSF_QNAN64;

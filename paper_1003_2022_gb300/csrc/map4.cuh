@@ -62,7 +62,7 @@ __device__ __forceinline__ void map4_sincos64(double x, double& sn, double& cs) 
 // component of p is small compared with the largest: there FP32 loses it to
 // cancellation (it is a difference of terms of the size of the covariance),
 // and the filter is sensitive to it because two widths are tiny.
-__device__ __noinline__ void map4_refine64(int kind, float v0, float v1, float v2, float eps, float eta, bool clamp,
+static __device__ __noinline__ void map4_refine64(int kind, float v0, float v1, float v2, float eps, float eta, bool clamp,
                                            float w32, float* pk) {
     double c1, c2, c3;
     if (kind == BSF_PARAM_COV && !clamp) {
