@@ -115,26 +115,59 @@ __device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
     e += c.lo;
     return df_norm(s, e);
 }
-// a 128-bit integer as a double-float (to about 48 bits): its top 62 bits as a
-// 64-bit integer v (the bits below are dropped: at most 2^-62 of |v|), then the
-// nearest FP32 value of v and of the exact remainder, both scaled back
+// Integer -> float conversions without 64-bit conversion instructions: those run on
+// the FP64 pipe (1/64 of the FP32 rate on this GPU) and, at 16 coefficients per tap,
+// kept it 80 % busy in the stencil.  A 23-bit integer becomes a float exactly through
+// its bit pattern: the float 2^23 (or 1.5 * 2^23 for a signed one) with the integer
+// added to its mantissa, minus the same constant.
+__device__ __forceinline__ float exact_f32_u23(unsigned c) {  // c < 2^23
+    return __int_as_float(0x4B000000 | (int)c) - 8388608.0f;
+}
+__device__ __forceinline__ float exact_f32_s22(int c) {  // -2^22 <= c < 2^22
+    return __int_as_float(0x4B400000 + c) - 12582912.0f;
+}
+// a 128-bit integer as a double-float (to about 48 bits): |a| normalised to 62 bits
+// (v = a 2^(62 - n), n its bit length), v cut into 23 + 23 + 17 bits converted exactly,
+// the two high parts added exactly (two-sum), the low one rounded into the low part, and
+// the scale 2^(n - 62) applied (exact)
 __device__ __forceinline__ dflt df_of_i128(i128 a) {
     const long long hw = (long long)(a >> 64);
     const unsigned long long lw = (unsigned long long)a;
-    // bit length of |a| (one less for negative a: enough to choose the shift)
+    // bit length of |a| (one less for negative a: enough to place the top bit)
     const unsigned long long mh = (unsigned long long)(hw ^ (hw >> 63));
     const unsigned long long ml = lw ^ (unsigned long long)(hw >> 63);
     const int n = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
-    const int sh = n > 62 ? n - 62 : 0;
-    const long long v = (long long)(a >> sh);
-    const float hi = __ll2float_rn(v);
-    const float lo = __ll2float_rn(v - __float2ll_rn(hi));
-    const float sc = __int_as_float((127 + sh) << 23);  // 2^sh, exact
-    return df_norm(hi * sc, lo * sc);
+    // for n <= 62 the value is its low 64 bits (two's complement)
+    const long long v = n > 62 ? (long long)(a >> (n - 62)) : (long long)(lw << (62 - n));
+    const float f2 = exact_f32_s22((int)(v >> 40)) * 1099511627776.0f;               // * 2^40
+    const float f1 = exact_f32_u23((unsigned)(v >> 17) & 0x7FFFFFu) * 131072.0f;      // * 2^17
+    const float f0 = exact_f32_u23((unsigned)v & 0x1FFFFu);
+    const float s = f2 + f1;
+    const float bb = s - f2;
+    const float e = ((f2 - (s - bb)) + (f1 - bb)) + f0;
+    const float sc = __int_as_float((127 + n - 62) << 23);  // 2^(n - 62), exact
+    return df_norm(s * sc, e * sc);
 }
-// the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact)
+// round-to-nearest-even of a float to a 64-bit integer (as __float2ll_rn, saturating at
+// 2^63; NaN saturates too) with FP32 additions and integer operations only: below 2^23
+// adding and subtracting 2^23 with the sign of x rounds to an integer (the sum lies where
+// the spacing of floats is 1), above it every float is one; the integer is then read from
+// the exponent and mantissa bits
+__device__ __forceinline__ long long f32_to_i64_rn(float x) {
+    const float t = copysignf(8388608.0f, x);
+    const float r = fabsf(x) < 8388608.0f ? (x + t) - t : x;
+    const unsigned b = __float_as_uint(r);
+    const int ef = (int)((b >> 23) & 0xFFu);
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int e = ef - 150;  // |r| = m 2^e for a normal r
+    long long v = e >= 0 ? (e < 40 ? m << e : 0x7FFFFFFFFFFFFFFFLL) : (e > -24 ? m >> (-e) : 0LL);
+    if (ef == 0) v = 0;  // zero (subnormals round to zero above)
+    return (b >> 31) ? -v : v;
+}
+// the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact):
+// two 24-bit halves, each converted as a 32-bit integer (exact below 2^24)
 __device__ __forceinline__ dflt df_of_frac48(long long x) {
-    return {(float)(x >> 24) * 5.9604644775390625e-8f, (float)(x & 0xFFFFFF) * 3.552713678800501e-15f};
+    return {(float)(int)(x >> 24) * 5.9604644775390625e-8f, (float)(int)(x & 0xFFFFFF) * 3.552713678800501e-15f};
 }
 
 // ||K||^2 for six directions: sum_{k,m} p_k^2 p_m^2 cos^2(theta_k - theta_m)
@@ -1094,7 +1127,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
                     }
                 }
             }
-            run += (u128)(i128)__float2ll_rn(mu * qscale);  // saturates: at most 2^63 in magnitude
+            run += (u128)(i128)f32_to_i64_rn(mu * qscale);  // saturates: at most 2^63 in magnitude
             qbits = max(qbits, __float_as_uint(fabsf(mu)));
             y[e] = run;
         }
