@@ -36,12 +36,29 @@ template <> struct mode_traits<MODE_F64> {
     static constexpr int FRAC_BITS = 0;
 };
 
+// Round-to-nearest-even of a float to a 64-bit integer (as __float2ll_rn, saturating at
+// 2^63; NaN saturates too) with FP32 additions and integer operations only: below 2^23
+// adding and subtracting 2^23 with the sign of x rounds to an integer (the sum lies where
+// the spacing of floats is 1), above it every float is one; the integer is then read from
+// the exponent and mantissa bits
+__device__ __forceinline__ long long f32_to_i64_rn(float x) {
+    const float t = copysignf(8388608.0f, x);
+    const float r = fabsf(x) < 8388608.0f ? (x + t) - t : x;
+    const unsigned b = __float_as_uint(r);
+    const int ef = (int)((b >> 23) & 0xFFu);
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int e = ef - 150;  // |r| = m 2^e for a normal r
+    long long v = e >= 0 ? (e < 40 ? m << e : 0x7FFFFFFFFFFFFFFFLL) : (e > -24 ? m >> (-e) : 0LL);
+    if (ef == 0) v = 0;  // zero (subnormals round to zero above)
+    return (b >> 31) ? -v : v;
+}
+// (64-bit integer <-> float conversions run on the FP64 pipe, 1/64 of the FP32 rate on this GPU.)
+
 // Image sample -> accumulator element.
 __device__ __forceinline__ unsigned long long to_acc_u64(uint8_t v) { return (unsigned long long)v; }
 __device__ __forceinline__ u128 to_acc_u128(float v) {
-    // round(v * 2^32) as a signed 64-bit integer, sign-extended to 128 bits
-    long long q = __double2ll_rn((double)v * 4294967296.0);
-    return (u128)(i128)q;
+    // round(v * 2^32) as a signed 64-bit integer (the scaling is exact in FP32), sign-extended to 128 bits
+    return (u128)(i128)f32_to_i64_rn(v * 4294967296.0f);
 }
 
 template <int MODE, class InT> __device__ __forceinline__ typename mode_traits<MODE>::T load_sample(InT v);

@@ -148,22 +148,6 @@ __device__ __forceinline__ dflt df_of_i128(i128 a) {
     const float sc = __int_as_float((127 + n - 62) << 23);  // 2^(n - 62), exact
     return df_norm(s * sc, e * sc);
 }
-// round-to-nearest-even of a float to a 64-bit integer (as __float2ll_rn, saturating at
-// 2^63; NaN saturates too) with FP32 additions and integer operations only: below 2^23
-// adding and subtracting 2^23 with the sign of x rounds to an integer (the sum lies where
-// the spacing of floats is 1), above it every float is one; the integer is then read from
-// the exponent and mantissa bits
-__device__ __forceinline__ long long f32_to_i64_rn(float x) {
-    const float t = copysignf(8388608.0f, x);
-    const float r = fabsf(x) < 8388608.0f ? (x + t) - t : x;
-    const unsigned b = __float_as_uint(r);
-    const int ef = (int)((b >> 23) & 0xFFu);
-    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int e = ef - 150;  // |r| = m 2^e for a normal r
-    long long v = e >= 0 ? (e < 40 ? m << e : 0x7FFFFFFFFFFFFFFFLL) : (e > -24 ? m >> (-e) : 0LL);
-    if (ef == 0) v = 0;  // zero (subnormals round to zero above)
-    return (b >> 31) ? -v : v;
-}
 // the fraction (48 bits, x / 2^48) of a lattice coordinate as a double-float (exact):
 // two 24-bit halves, each converted as a 32-bit integer (exact below 2^24)
 __device__ __forceinline__ dflt df_of_frac48(long long x) {
