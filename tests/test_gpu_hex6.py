@@ -413,3 +413,23 @@ def test_map_table_filter_uses_the_table_scales(accuracy_record):
     accuracy_record["n6_map_table_filter"] = {"pixels": int(idx.size), "max_normwise_vs_solver_scales": d}
     print(f"filter with the map table vs the solver's scales: max normwise difference {d:.3e}")
     assert d < 1e-3
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e5])
+def test_signed_images_of_large_magnitude(scale):
+    """Images of both signs (U[-1, 1) times 1 or 1e5): window sums and
+    coefficients of either sign and up to about 2^80, which the stencil turns
+    into double-floats without 64-bit conversion instructions; against the
+    definition on the transferred image."""
+    H, W = 72, 88
+    f = ((synth.image(H, W, seed=61, dtype="f32") * 2.0 - 1.0) * scale).astype(np.float32)
+    p = synth.srt_field(H, W, seed=61, sigma=(2.0, 12.0), rho=(1.0, 5.0))
+    got, st = _run(f, p, "srt")
+    assert st & ~(1 << L.BSF_EINFEASIBLE) == 0
+    idx = _sample(H, W, 30, seed=61)
+    a, _ = n6.map6(p.reshape(3, -1)[:, idx].astype(np.float64), 2)
+    A = np.zeros((6, H * W))
+    A[:, idx] = a
+    ref = n6.direct6_hex(f.astype(np.float64), A.reshape(6, H, W), idx, 0.5)
+    assert _nerr(got.ravel()[idx], ref) < TOL
+

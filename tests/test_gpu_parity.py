@@ -55,6 +55,24 @@ def test_preintegrate_f32_fixed_point_bitexact(H, W, P):
         assert np.array_equal(buf[..., 1], np.where(ref < 0, -1, 0))
 
 
+def test_preintegrate_f32_signed_values_and_rounding_ties():
+    """The float32 fixed point round(f 2^32) on values of both signs and every
+    magnitude the form accepts (|f| < 2^31), including exact ties (odd
+    multiples of 2^-33, rounded to even) and values above 2^23 / 2^32 (already
+    integers after the scaling): the sums equal the oracle's integer recursion
+    bit for bit."""
+    dev = _cuda()
+    H, W, P = 37, 41, 9
+    rng = np.random.default_rng(29)
+    f = (rng.uniform(-1.0, 1.0, (H, W)) * 10.0 ** rng.integers(-12, 9, (H, W))).astype(np.float32)
+    ties = ((rng.integers(-2 ** 20, 2 ** 20, 60) * 2 + 1) * 2.0 ** -33).astype(np.float32)
+    f.ravel()[:60] = ties
+    f.ravel()[60:64] = np.array([2.0 ** 30, -2.0 ** 30, 2.0 ** -20, -(2.0 ** -40)], np.float32)
+    buf = api.preintegrate(torch.from_numpy(f).to(dev), halo=P).cpu().numpy()
+    fi = np.rint(f.astype(np.float64) * 2.0 ** 32).astype(np.int64)
+    assert np.array_equal(buf[..., 0], O.preint4_i64(fi, P))
+
+
 @pytest.mark.parametrize("dtype", ["u8", "f32"])
 def test_preintegrate_fp64_form(dtype):
     dev = _cuda()
