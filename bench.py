@@ -538,7 +538,7 @@ def run_ours(args):
                 "flop_per_px": HEX6_TC_FLOP_PER_PX,
                 "achieved_tflops": HEX6_TC_FLOP_PER_PX * px_per_launch / (st_ms / 1e3) / 1e12,
                 "peak": tc_peak,
-                "peak_note": "measured dense bf16 (burst) of this GPU; FP16 runs at the bf16 rate"}
+                "peak_note": "measured dense bf16 (burst) of the GB300; FP16 runs at the bf16 rate"}
         impl["frac"] = impl["achieved_tflops"] / impl["peak"]
         traffic = None
         alg_bytes = int((12 + 4 + 16) * px_per_launch)

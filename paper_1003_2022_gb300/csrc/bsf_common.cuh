@@ -52,7 +52,7 @@ __device__ __forceinline__ long long f32_to_i64_rn(float x) {
     if (ef == 0) v = 0;  // zero (subnormals round to zero above)
     return (b >> 31) ? -v : v;
 }
-// (64-bit integer <-> float conversions run on the FP64 pipe, 1/64 of the FP32 rate on this GPU.)
+// (64-bit integer <-> float conversions run on the FP64 pipe, 1/64 of the FP32 rate on GB300.)
 
 // Image sample -> accumulator element.
 __device__ __forceinline__ unsigned long long to_acc_u64(uint8_t v) { return (unsigned long long)v; }

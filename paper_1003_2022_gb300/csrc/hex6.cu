@@ -116,7 +116,7 @@ __device__ __forceinline__ dflt df_fma(dflt a, dflt b, dflt c) {
     return df_norm(s, e);
 }
 // Integer -> float conversions without 64-bit conversion instructions: those run on
-// the FP64 pipe (1/64 of the FP32 rate on this GPU) and, at 16 coefficients per tap,
+// the FP64 pipe (1/64 of the FP32 rate on GB300) and, at 16 coefficients per tap,
 // kept it 80 % busy in the stencil.  A 23-bit integer becomes a float exactly through
 // its bit pattern: the float 2^23 (or 1.5 * 2^23 for a signed one) with the integer
 // added to its mantissa, minus the same constant.
@@ -596,7 +596,7 @@ __device__ __forceinline__ map6_p map6_active_set(double T, double Zc, double Zs
     double* p = res.p;
     double pbar[6];
     // (divisions by constants as multiplications: an FP64 division costs a dozen FP64 operations on
-    // this GPU's FP64 pipe, which the map is bound by; the results move by an ulp at most)
+    // GB300's FP64 pipe, which the map is bound by; the results move by an ulp at most)
     constexpr double I3 = 1.0 / 3.0, I6 = 1.0 / 6.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) pbar[k] = (T + 2.0 * (Zc * MAP6_C2[k] + Zs * MAP6_S2[k])) * I6;
