@@ -1062,13 +1062,23 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
 #pragma unroll
     for (int e = 0; e < PRE_CPT; ++e) s90a[e] = s150[e] = 0;
     unsigned qbits = 0, big = 0;  // largest |mass| (FP32 bits; NaN above all); OR of |stored value| >> 95
+    // the pixel row below each lattice row and the offset to it, in FP64 (the lattice row height
+    // h sqrt3/2 is irrational): computed once per block by one thread, for row r + 1 while row r
+    // runs (GB300's FP64 pipe takes about 64 cycles per warp instruction)
+    __shared__ int row_ky0;
+    __shared__ float row_dy0;
+    auto row_pos = [&](int r) {
+        const double pyd = hy * (double)(tl.j0w + r);
+        const double kyd = floor(pyd);
+        row_ky0 = (int)kyd;
+        row_dy0 = (float)(kyd - pyd);  // (pixel row ky0) - (lattice row), in (-1, 0]
+    };
+    if (tid == 0) row_pos(0);
     __syncthreads();
     for (int r = 0; r < nrow; ++r) {
         const int j = tl.j0w + r;
-        const double pyd = hy * (double)j;
-        const double kyd = floor(pyd);
-        const int ky0 = (int)kyd;
-        const float dy0 = (float)(kyd - pyd);  // (pixel row ky0) - (lattice row), in (-1, 0]
+        const int ky0 = row_ky0;
+        const float dy0 = row_dy0;
         // the image row the lattice rows two to three ahead first need (their columns lie about
         // 1.5 h px per row further left), fetched into L1 now: one line per thread, no registers
         if (c0 < ncol) {
@@ -1124,6 +1134,9 @@ __global__ void __launch_bounds__(PRE_THREADS) k_hex6_preint(const InT* __restri
         }
         if (lane == 31) wt[warp] = v;
         __syncthreads();
+        // every thread has read this row's position: the next row's can be written (read after
+        // the row's last barrier)
+        if (tid == 0 && r + 1 < nrow) row_pos(r + 1);
         // every warp scans the warp totals itself (no second barrier)
         u128 wsum = lane < nwarp ? wt[lane] : (u128)0;
 #pragma unroll
